@@ -1,0 +1,214 @@
+"""Fast-diagonalization preconditioner: exact (Alg. 3), approximate eigenpairs (App. B),
+exponential sums (Prop. 1, eq. estimate_prec_rel) and the low-rank application (Alg. 4).
+
+Oracle module (test infrastructure only).  Dense matrices, direct sums for the sine transforms.
+
+Readings (listed in the design doc):
+  * App. B, U1: the columns of V1 U1 are the B-spline coefficients of the interpolant in V_h,1 of
+    the L2-normalised sines sqrt(2) sin(j pi x) at the points x_i (one factor sqrt(2)).
+  * App. B, V2: V2 = M^{-1} N with N a basis of null(V1^T), which makes span(V2) the
+    M-orthogonal complement of V_h,1; U2, Lambda2 solve the projected pencil with U2^T (V2^T M V2) U2 = I.
+  * lambda_min / lambda_max (eq. estimate_prec_rel) are sums over the three directions of the
+    extreme entries of Lambda~_i, outliers of Lambda2 included.
+  * Exponential sums: the paper takes (omega_j, alpha_j) from Hackbusch's tables, which are not
+    available.  This oracle uses the sinc-quadrature sums of 1/lambda = int_R exp(s - lambda e^s) ds
+    (trapezoidal rule, step h, nodes s_k = s0 + k h), with (h, s0, R) chosen by a search so that
+    E_R(M) <= eps_prec / M on a dense log grid of [1, M]; R_P is the smallest such R found.
+    The search is not a best approximation, so R_P >= the paper's Table 1 values: parity unpinned
+    for R_P itself; the bound E_R(M_P) M_P <= eps_prec is pinned.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+from . import bspline, tucker
+
+
+# ---------------------------------------------------------------------------------------------
+# Exact FD (Alg. 3)
+# ---------------------------------------------------------------------------------------------
+def exact_eig(n: int, p: int):
+    """Generalized eigendecomposition K U = M U Lambda, U^T M U = I (eq. factorizations)."""
+    n_el = n - p + 2
+    K = bspline.stiffness(n_el, p)
+    M = bspline.mass(n_el, p)
+    lam, U = scipy.linalg.eigh(K, M)
+    return lam, U
+
+
+def exact_fd_apply_full(n: int, p: int, s: np.ndarray) -> np.ndarray:
+    """v = P^{-1} s for the exact FD preconditioner (eq. factorized_FD), full vectors, tiny n."""
+    lam, U = exact_eig(n, p)
+    S = tucker.unvec(s, (n, n, n))
+    T = S
+    for m in range(3):
+        T = tucker.mode_product(T, U.T, m)
+    D = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+    T = T / D
+    for m in range(3):
+        T = tucker.mode_product(T, U, m)
+    return tucker.vec(T)
+
+
+# ---------------------------------------------------------------------------------------------
+# Approximate eigenpairs (App. B)
+# ---------------------------------------------------------------------------------------------
+def split_dims(n_el: int, p: int):
+    """(n1, n2) of the splitting V_h = V_h,1 (+) V_h,2 (App. B)."""
+    if p % 2 == 1:
+        return n_el - 1, p - 1
+    return n_el, p - 2
+
+
+def interpolation_points(n_el: int, p: int) -> np.ndarray:
+    """Breakpoints except 0 and 1 (odd p) or span midpoints (even p) (App. B)."""
+    if p % 2 == 1:
+        return np.arange(1, n_el) / n_el
+    return (np.arange(1, n_el + 1) - 0.5) / n_el
+
+
+def _nullspace(A: np.ndarray) -> np.ndarray:
+    if A.shape[0] == 0:
+        return np.eye(A.shape[1])
+    return scipy.linalg.null_space(A)
+
+
+def v1_basis(n_el: int, p: int) -> np.ndarray:
+    """V1 (n x n1): columns Phi0 | Phi | Phi1 spanning V_h,1 (eq. Phi0, eq. Phi1)."""
+    n = n_el + p - 2
+    n1, n2 = split_dims(n_el, p)
+    nc = n2 // 2                              # constraints per end: even derivatives 2k <= p-1
+    V1 = np.zeros((n, n1))
+    col = 0
+    if n2 > 0:
+        ders = [2 * k for k in range(1, nc + 1)]
+        D0 = np.array([bspline.dirichlet_basis(n_el, p, np.array([0.0]), d)[:n2, 0] for d in ders])
+        D1 = np.array([bspline.dirichlet_basis(n_el, p, np.array([1.0]), d)[n1:, 0] for d in ders])
+        Z0 = _nullspace(D0)                   # n2 x nc
+        Z1 = _nullspace(D1)
+        V1[:n2, :Z0.shape[1]] = Z0
+        col = Z0.shape[1]
+    for i in range(n2, n1):
+        V1[i, col] = 1.0
+        col += 1
+    if n2 > 0:
+        V1[n1:, col:col + Z1.shape[1]] = Z1
+        col += Z1.shape[1]
+    assert col == n1
+    return V1
+
+
+def approx_eig(n: int, p: int):
+    """U~ (n x n) and Lambda~ (n) of App. B, built from their definitions with dense matrices."""
+    n_el = n - p + 2
+    n1, n2 = split_dims(n_el, p)
+    M = bspline.mass(n_el, p)
+    K = bspline.stiffness(n_el, p)
+    V1 = v1_basis(n_el, p)
+    x = interpolation_points(n_el, p)
+    E = bspline.dirichlet_basis(n_el, p, x, 0).T          # E[l, a] = b_a(x_l)
+    Cint = E @ V1                                          # Cint[l, i] = v_i(x_l)
+    j = np.arange(1, n1 + 1)
+    Udft = np.sqrt(2.0) * np.sin(np.pi * np.outer(x, j))   # Udft[l, j] = sqrt(2) sin(j pi x_l)
+    U1 = np.linalg.solve(Cint, Udft)                       # interpolation: Cint c = f(x)
+    lam1 = (j * np.pi) ** 2
+    parts = [V1 @ U1]
+    lams = [lam1]
+    if n2 > 0:
+        N = _nullspace(V1.T)                               # n x n2
+        V2 = np.linalg.solve(M, N)
+        lam2, U2 = scipy.linalg.eigh(V2.T @ K @ V2, V2.T @ M @ V2)
+        parts.append(V2 @ U2)
+        lams.append(lam2)
+    return np.concatenate(parts, axis=1), np.concatenate(lams)
+
+
+def mp_value(n: int, p: int) -> float:
+    """M_P = lambda_max / lambda_min (eq. estimate_prec_rel) for the same n, p in all directions."""
+    _, lam = approx_eig(n, p)
+    return (3.0 * lam.max()) / (3.0 * lam.min())
+
+
+def mp_value_fast(n_el: int, p: int) -> float:
+    """M_P from Lambda1 = (j pi)^2 and the small pencil on V_h,2 only (no dense U1)."""
+    n = n_el + p - 2
+    n1, n2 = split_dims(n_el, p)
+    lam = [np.pi ** 2, (n1 * np.pi) ** 2]
+    if n2 > 0:
+        M = bspline.mass(n_el, p)
+        K = bspline.stiffness(n_el, p)
+        V1 = v1_basis(n_el, p)
+        N = _nullspace(V1.T)
+        V2 = np.linalg.solve(M, N)
+        lam2 = scipy.linalg.eigh(V2.T @ K @ V2, V2.T @ M @ V2, eigvals_only=True)
+        lam += list(lam2)
+    return max(lam) / min(lam)
+
+
+# ---------------------------------------------------------------------------------------------
+# Exponential sums (Prop. 1)
+# ---------------------------------------------------------------------------------------------
+def expsum_error(omega, alpha, M: float, npts: int = 4000) -> float:
+    """E_R(M) = sup_{lambda in [1, M]} |1/lambda - sum_j omega_j exp(-alpha_j lambda)| on a log grid."""
+    lam = np.exp(np.linspace(0.0, np.log(M), npts))
+    s = np.exp(-np.outer(lam, alpha)) @ omega
+    return float(np.max(np.abs(1.0 / lam - s)))
+
+
+def sinc_expsum(R: int, h: float, s0: float):
+    """Trapezoidal rule for 1/lambda = int exp(s - lambda e^s) ds with nodes s0 + k h, k < R."""
+    s = s0 + h * np.arange(R)
+    return h * np.exp(s), np.exp(s)
+
+
+def expsum_for(M: float, eps_prec: float, rmax: int = 80):
+    """Smallest R (and its omega, alpha) with E_R(M) <= eps_prec / M found by a grid search of (h, s0)."""
+    target = eps_prec / M
+    for R in range(1, rmax + 1):
+        best = None
+        for h in np.linspace(0.15, 1.6, 30):
+            top = np.log(np.log(1.0 / target) + 2.0) + 0.5
+            for s0 in np.linspace(top - h * (R - 1) - 2.0, top - h * (R - 1) + 1.0, 13):
+                om, al = sinc_expsum(R, h, s0)
+                e = expsum_error(om, al, M, 1500)
+                if best is None or e < best[0]:
+                    best = (e, om, al)
+        if best[0] <= target:
+            om, al = best[1], best[2]
+            if expsum_error(om, al, M) <= target:
+                return R, om, al
+    raise RuntimeError("no exponential sum found")
+
+
+# ---------------------------------------------------------------------------------------------
+# Low-rank FD application (Alg. 4)
+# ---------------------------------------------------------------------------------------------
+class ApproxFD:
+    """Setup of Alg. 4 for n dofs and degree p in every direction."""
+
+    def __init__(self, n: int, p: int, eps_prec: float = 0.1, expsum=None):
+        self.n, self.p = n, p
+        self.U, self.lam = approx_eig(n, p)
+        self.lmin = 3.0 * self.lam.min()
+        self.lmax = 3.0 * self.lam.max()
+        self.MP = self.lmax / self.lmin
+        if expsum is None:
+            self.RP, self.omega, self.alpha = expsum_for(self.MP, eps_prec)
+        else:
+            self.omega, self.alpha = np.asarray(expsum[0]), np.asarray(expsum[1])
+            self.RP = len(self.omega)
+
+    def diag(self, j: int) -> np.ndarray:
+        """Diagonal of D_(i,j), eq. diag_factor."""
+        return np.exp(-self.alpha[j] / self.lmin * self.lam)
+
+    def apply(self, S):
+        """Alg. 4, steps 5-9: core P (x) S (block form) and factors [U~ D_(i,1) U~^T S_i, ..., U~ D_(i,R_P) U~^T S_i]."""
+        core, F = S
+        V = tucker.superdiag_kron(self.omega / self.lmin, core)
+        facs = []
+        for m in range(3):
+            Z = self.U.T @ F[m]
+            facs.append(np.concatenate([self.U @ (self.diag(j)[:, None] * Z) for j in range(self.RP)], axis=1))
+        return V, facs
