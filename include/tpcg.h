@@ -1,0 +1,200 @@
+/*
+ * tpcg.h -- C ABI of the GB300 (sm_103a) Truncated Preconditioned Conjugate Gradient library for
+ * isogeometric Poisson problems in Tucker format (Montardini, Sangalli, Tani, "A low-rank
+ * isogeometric solver based on Tucker tensors").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: TPCG_OK (0) or one of the TPCG_E_* codes below.  Invalid arguments are reported
+ *    before anything is enqueued.  TPCG_E_CUDA means a CUDA call failed; tpcg_last_error() gives text.
+ *  - All compute entry points are stream-ordered and asynchronous on the given cudaStream_t
+ *    (passed as void*; NULL = the legacy default stream).  Scalars produced on the device are written
+ *    to device pointers; read them after synchronising the stream.
+ *  - Layout: every direction has the same number n of degrees of freedom.  A factor matrix is n x cols,
+ *    column-major with leading dimension n.  A dense core r1 x r2 x r3 is column-major (mode 1 fastest),
+ *    matching vec() of Sec. 2.3.  Floating-point data is double (TPCG_F64) or float (TPCG_F32), chosen per
+ *    context; CG scalars are always double.
+ *  - Ownership: tucker_t buffers are allocated and owned by the caller (e.g. PyTorch); the library owns
+ *    tpcg_ctx (workspace) and tpcg_problem (operator, right-hand side, preconditioner tables) and frees
+ *    them in the matching destroy call.
+ *  - Ranks live on the device (tucker_t.desc), so consecutive calls need no host synchronisation and the
+ *    whole sequence can be captured in a CUDA graph.
+ */
+#ifndef TPCG_H
+#define TPCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------------------ status codes */
+#define TPCG_OK 0
+#define TPCG_E_INVALID 1        /* bad argument (sizes, ranks, capacities, dtype mismatch)          */
+#define TPCG_E_NOMEM 2          /* device allocation failed                                          */
+#define TPCG_E_NOT_CONVERGED 3  /* TPCG reached max_it before ||r|| <= tol ||f||                     */
+#define TPCG_E_RANK_CAP 4       /* a rank cap forced a truncation error above the requested tolerance */
+#define TPCG_E_TIMEOUT 5        /* a device-side wait gave up (persistent scheduler)                 */
+#define TPCG_E_CUDA 6           /* a CUDA runtime call failed                                        */
+#define TPCG_E_BREAKDOWN 7      /* NaN/Inf or a non-positive curvature p.q in the CG scalars          */
+
+#define TPCG_F64 0
+#define TPCG_F32 1
+
+#define TPCG_MAX_BLOCKS 128     /* core blocks of an unrounded Tucker tensor                          */
+#define TPCG_DESC_BYTES 8192    /* bytes of device memory a tucker_t.desc must provide                */
+
+/* ------------------------------------------------------------------------------------ Tucker tensors */
+/* A Tucker vector x = (U3 (x) U2 (x) U1) vec(core) (eq. Tucker, Sec. 2.3).
+ * Rounded ("plain") tensors have one dense core.  Unrounded results of tucker_apply, tucker_residual,
+ * tucker_axpby and fd_precond_apply have a block-diagonal core (Sec. 2.3 sum and eq. tt_product) kept as
+ * a list of scaled dense blocks that POINT AT the cores of their inputs: those input cores must stay
+ * unchanged until the unrounded tensor has been rounded (tucker_round) or is no longer needed. */
+typedef struct {
+    int dtype;          /* TPCG_F64 or TPCG_F32                                                       */
+    int n;              /* dofs per direction                                                        */
+    int cap;            /* column capacity of each factor buffer                                     */
+    long long core_cap; /* element capacity of the core buffer                                        */
+    void* U[3];         /* device, n x cap each, column-major, ld = n                                */
+    void* core;         /* device, core_cap elements                                                 */
+    void* desc;         /* device, TPCG_DESC_BYTES bytes: ranks and block list (library-managed)     */
+} tucker_t;
+
+typedef struct tpcg_ctx_s* tpcg_ctx;          /* workspace for one solve stream                     */
+typedef struct tpcg_problem_s* tpcg_problem;  /* operator A~, rhs f~, preconditioner P~ on the device */
+
+/* ------------------------------------------------------------------------------------ problem setup */
+#define TPCG_GEOM_CUBE 0    /* identity map, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)                 */
+#define TPCG_GEOM_TWIST 1   /* quarter annulus rho in [1,2], theta in [0,pi/2], extruded along z, with the
+                               cross-section rotated about its centroid by amp sin(pi z); f = 1       */
+
+typedef struct {
+    int kind;           /* TPCG_GEOM_*                                                               */
+    double amp;         /* twist amplitude (radians), TPCG_GEOM_TWIST only                            */
+    double eps_geo;     /* relative tolerance of the low-rank coefficient approximation (App. A); 0 = 1e-8 */
+    double eps_prec;    /* relative tolerance of the preconditioner, eq. prec_bound; 0 = 0.1         */
+} tpcg_geometry;
+
+/* Host FP64 setup (App. A, App. B, Prop. 1) followed by upload: B-spline matrices, low-rank Chebyshev
+ * approximation of Q(eta) and omega(eta) folded into a Kronecker sum A~ = sum_j w_j K3^j (x) K2^j (x) K1^j,
+ * the Tucker rhs f~ (rounded losslessly), and the low-rank FD tables.  n dofs per direction, degree p,
+ * n_el = n - p + 2 > p.  dtype selects the precision of the device copies.  *out is owned by the caller
+ * and released with tpcg_problem_destroy. */
+int tpcg_setup(const tpcg_geometry* geo, int degree, int n, int dtype, tpcg_problem* out);
+
+/* Problem from explicit host arrays (all double, column-major):
+ *   R terms: weights w[R]; bands[((j*3 + t)*(2p+1) + d)*n + i] = K_t^j[i, i + d - p] (zero outside);
+ *   rhs: core f_core (rf1 x rf2 x rf3), factors f_U[t] (n x rf_t);
+ *   preconditioner (Alg. 4 with the eigenvector factorisation of App. B):
+ *     lam[n]      : Lambda~ (first n1 entries (j pi)^2, then Lambda2),
+ *     mu[n1]      : sine-basis scaling, U~[:, :n1] = W U_dft diag(1/mu),
+ *     W (n x n1)  : sparse, given in CSR: w_rowptr[n+1], w_col[nnz], w_val[nnz],
+ *     v2u2 (n x n2): V2 U2 dense,
+ *     RP exponential-sum pairs omega[RP], alpha[RP], lambda_min.
+ *   The sine transform is DST-I (U_dft[l,j] = sqrt2 sin(j pi l/(n1+1))) for odd p and DST-II
+ *   (U_dft[l,j] = sqrt2 sin(j pi (l-1/2)/n1)) for even p, l, j = 1..n1. */
+typedef struct {
+    int n, p, R, dtype;
+    const double* w;
+    const double* bands;
+    int rf[3];
+    const double* f_core;
+    const double* f_U[3];
+    int n1, n2, RP, w_nnz;
+    const double* lam;
+    const double* mu;
+    const int* w_rowptr;
+    const int* w_col;
+    const double* w_val;
+    const double* v2u2;
+    const double* omega;
+    const double* alpha;
+    double lambda_min;
+} tpcg_problem_arrays;
+
+int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* out);
+
+typedef struct {
+    int n, p, R, RP, n1, n2, rf[3], dtype;
+    double lambda_min, lambda_max, MP, norm_f;
+} tpcg_problem_info;
+
+int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* out);
+
+/* Host copies of the setup data, laid out as in tpcg_problem_arrays (buffers provided by the caller,
+ * sized from tpcg_problem_get_info; any pointer may be NULL to skip it).  f_U[t] gets n x rf[t]. */
+int tpcg_problem_export(tpcg_problem pb, double* w, double* bands, double* f_core, double* f_U0, double* f_U1,
+                        double* f_U2, double* lam, double* mu, double* v2u2, double* omega, double* alpha);
+void tpcg_problem_destroy(tpcg_problem pb);
+
+/* ------------------------------------------------------------------------------------ workspace */
+/* Workspace for rounding, dots and TPCG on tensors with n dofs per direction, at most max_cols factor
+ * columns before rounding and rank at most rank_cap after rounding. */
+int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpcg_ctx* out);
+size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype);
+void tpcg_ctx_destroy(tpcg_ctx c);
+
+/* ------------------------------------------------------------------------------------ Tucker ops */
+/* Mark t as a plain tensor of multilinear rank (r1, r2, r3) whose core and factors the caller filled. */
+int tucker_set_plain(tucker_t* t, int r1, int r2, int r3, void* stream);
+/* Ranks and number of core blocks (synchronises the stream). */
+int tucker_get_ranks(const tucker_t* t, int* r3_out, int* nblk_out, void* stream);
+
+/* y = A~ x (eq. tt_product): factors [K_t^1 X_t, ..., K_t^R X_t], core superdiag(w) (x) G_x (blocks).
+ * x must be plain; y needs cap >= R * rank(x). */
+int tucker_apply(tpcg_problem pb, const tucker_t* x, tucker_t* y, void* stream);
+/* y = f~ - A~ x (Alg. 5 step 11 before truncation); y needs cap >= rf + R * rank(x). */
+int tucker_residual(tpcg_problem pb, const tucker_t* x, tucker_t* y, void* stream);
+/* z = a x + b y (Sec. 2.3 sum): concatenated factors, block-diagonal core.  a and b are host doubles,
+ * or, when a_dev / b_dev are non-NULL, device doubles read at execution time. */
+int tucker_axpby(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev,
+                 const tucker_t* y, tucker_t* z, void* stream);
+/* *out_dev = <x, y> (Sec. 2.3 scalar product), both plain.  out_dev: device double. */
+int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, void* stream);
+/* In-place relative truncation, Alg. 1: y <- T_rel(y, eps) with ST-HOSVD split eps^2/3 per mode, ranks
+ * clipped to rank_cap (<= 0: the context's cap).  Factors come out orthonormal, so ||y|| = ||core||.
+ * If info_dev is non-NULL it receives 4 doubles: ||y||^2 before, discarded squared norm, and the new
+ * ranks as doubles (3) are written to info_dev[2..4]; TPCG_E_RANK_CAP is not raised here (check info). */
+int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rank_cap, double* info_dev,
+                 void* stream);
+/* v = P~^{-1} s, Alg. 4 steps 5-9: factors [U~ D_(t,1) U~^T S_t, ..., U~ D_(t,RP) U~^T S_t], core
+ * superdiag(omega / lambda_min) (x) G_s (blocks).  s plain; v needs cap >= RP * rank(s). */
+int fd_precond_apply(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, void* stream);
+
+/* ------------------------------------------------------------------------------------ solver */
+typedef struct {
+    double tol;         /* relative residual tolerance, ||r_k|| <= tol ||f~||             (1e-6)  */
+    double eps0;        /* initial dynamic-truncation tolerance                           (0.1)   */
+    double eps_min;     /* minimum dynamic tolerance; <= 0: tol ||f~|| / 10 (Sec. 5)              */
+    double alpha;       /* reduction factor of Alg. 2                                      (0.5)   */
+    double delta;       /* update-ratio threshold of Alg. 2                                (1e-3)  */
+    double beta_trunc;  /* beta of eq. rel_tol_iterates                                    (0.1)   */
+    int max_it;         /* iteration cap                                                   (500)   */
+    int rank_cap;       /* rank cap of every truncation; <= 0: the context's cap                   */
+} tpcg_params;
+
+typedef struct {
+    int iters;              /* TPCG iterations                                                      */
+    int status;             /* TPCG_OK, TPCG_E_NOT_CONVERGED, TPCG_E_BREAKDOWN                      */
+    double rel_res;         /* ||r_k|| / ||f~|| of the truncated residual at exit                   */
+    int rank[3];            /* multilinear rank of the solution                                      */
+    double mem_compression; /* eq. mem_comp, percent                                                */
+    int dt_trials;          /* total Alg. 2 truncations                                             */
+    int max_rank_seen;      /* largest rank of any rounded iterate                                  */
+} tpcg_stats;
+
+void tpcg_params_default(tpcg_params* p);
+
+/* Alg. 5 with x_0 = 0: x receives the low-rank solution (plain, caller buffers with cap >= rank_cap and
+ * core_cap >= rank_cap^3).  Synchronises the stream once per iteration for the stopping test. */
+int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
+
+/* ------------------------------------------------------------------------------------ misc */
+const char* tpcg_last_error(void);
+const char* tpcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCG_H */

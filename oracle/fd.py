@@ -13,7 +13,8 @@ Readings (listed in DESIGN.md):
   * Exponential sums: the paper takes (omega_j, alpha_j) from Hackbusch's tables, which are not
     available.  This oracle uses the sinc-quadrature sums of 1/lambda = int_R exp(s - lambda e^s) ds
     (trapezoidal rule, step h, nodes s_k = s0 + k h), with (h, s0, R) chosen by a search so that
-    E_R(M) <= eps_prec / M on a dense log grid of [1, M]; R_P is the smallest such R found.
+    E_R(M) <= eps_prec / M on a log grid of [1, M] (selection on 400 points, acceptance on 4000);
+    R_P is the smallest such R found.
     The search is not a best approximation, so R_P >= the paper's Table 1 values: parity unpinned
     for R_P itself; the bound E_R(M_P) M_P <= eps_prec is pinned.
 """
@@ -124,6 +125,37 @@ def approx_eig(n: int, p: int):
     return np.concatenate(parts, axis=1), np.concatenate(lams)
 
 
+def sine_symbol(n_el: int, p: int) -> np.ndarray:
+    """mu_j = sum over the interpolation lattice of B(x_l - c) cos(j pi (x_l - c)) for a B-spline b with
+    centre c whose local knots are uniform: the factor by which collocating the uniform spline with
+    coefficients sin(j pi c_i) multiplies the samples sin(j pi x_l)."""
+    n = n_el + p - 2
+    n1, _ = split_dims(n_el, p)
+    x = interpolation_points(n_el, p)
+    kn = open_knots = bspline.open_uniform_knots(n_el, p)
+    i0 = (p - 1 + n_el - 2) // 2                  # reduced index of a function with distinct local knots
+    c0 = 0.5 * (kn[i0 + 1] + kn[i0 + p + 2])
+    vals = bspline.dirichlet_basis(n_el, p, x)[i0]
+    j = np.arange(1, n1 + 1)
+    return np.cos(np.pi * np.outer(j, x - c0)) @ vals
+
+
+def sine_factorization(n: int, p: int):
+    """(W, mu) with V1 U1 = W U_dft diag(1/mu): the App. B eigenvector block written as a sparse
+    boundary correction W (n x n1) of the scaled sine transform.  Dense construction:
+    W = (V1 U1) diag(mu) U_dft^{-1}; entries below 1e-11 max|W| are dropped."""
+    n_el = n - p + 2
+    n1, _ = split_dims(n_el, p)
+    U, _ = approx_eig(n, p)
+    x = interpolation_points(n_el, p)
+    j = np.arange(1, n1 + 1)
+    Udft = np.sqrt(2.0) * np.sin(np.pi * np.outer(x, j))
+    mu = sine_symbol(n_el, p)
+    W = np.linalg.solve(Udft.T, (U[:, :n1] * mu).T).T
+    W[np.abs(W) < 1e-11 * np.abs(W).max()] = 0.0
+    return W, mu, Udft
+
+
 def mp_value(n: int, p: int) -> float:
     """M_P = lambda_max / lambda_min (eq. estimate_prec_rel) for the same n, p in all directions."""
     _, lam = approx_eig(n, p)
@@ -171,7 +203,7 @@ def expsum_for(M: float, eps_prec: float, rmax: int = 80):
             top = np.log(np.log(1.0 / target) + 2.0) + 0.5
             for s0 in np.linspace(top - h * (R - 1) - 2.0, top - h * (R - 1) + 1.0, 13):
                 om, al = sinc_expsum(R, h, s0)
-                e = expsum_error(om, al, M, 1500)
+                e = expsum_error(om, al, M, 400)
                 if best is None or e < best[0]:
                     best = (e, om, al)
         if best[0] <= target:

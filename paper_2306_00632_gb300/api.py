@@ -1,0 +1,268 @@
+"""Python-facing wrappers with the names of the C ABI (include/tpcg.h).
+
+Device memory and streams come from PyTorch; everything else is a call into the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import struct
+
+import numpy as np
+import torch
+
+from . import lib as L
+from .lib import check
+
+_TORCH_DT = {L.F64: torch.float64, L.F32: torch.float32}
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(ptr_or_tensor):
+    if ptr_or_tensor is None:
+        return None
+    if isinstance(ptr_or_tensor, torch.Tensor):
+        return C.c_void_p(ptr_or_tensor.data_ptr())
+    return C.c_void_p(int(ptr_or_tensor))
+
+
+class Tucker:
+    """Caller-owned device buffers of one Tucker tensor (factors n x cap, core, descriptor)."""
+
+    def __init__(self, n: int, cap: int, core_cap: int, dtype: int = L.F64, device="cuda"):
+        td = _TORCH_DT[dtype]
+        self.n, self.cap, self.core_cap, self.dtype = n, cap, core_cap, dtype
+        self.U = [torch.zeros((cap, n), dtype=td, device=device) for _ in range(3)]   # column-major n x cap
+        self.core = torch.zeros(max(core_cap, 1), dtype=td, device=device)
+        self.desc = torch.zeros(L.DESC_BYTES, dtype=torch.uint8, device=device)
+        self.t = L.TuckerT(dtype, n, cap, core_cap, (C.c_void_p * 3)(*[u.data_ptr() for u in self.U]),
+                           self.core.data_ptr(), self.desc.data_ptr())
+
+    @property
+    def ref(self):
+        return C.byref(self.t)
+
+    # ------------------------------------------------------------------ host <-> device
+    @classmethod
+    def from_numpy(cls, core, factors, cap=None, core_cap=None, dtype=L.F64):
+        n = factors[0].shape[0]
+        r = core.shape
+        cap = cap or max(r)
+        core_cap = core_cap or int(np.prod(r))
+        T = cls(n, cap, core_cap, dtype)
+        T.upload(core, factors)
+        return T
+
+    def upload(self, core, factors):
+        r = tuple(int(x) for x in core.shape)
+        td = _TORCH_DT[self.dtype]
+        for t in range(3):
+            u = torch.as_tensor(np.ascontiguousarray(factors[t].T), dtype=td)
+            self.U[t][: r[t]].copy_(u)
+        flat = torch.as_tensor(np.asarray(core, dtype=np.float64).reshape(-1, order="F").copy(), dtype=td)
+        self.core[: flat.numel()].copy_(flat)
+        check(L.load().tucker_set_plain(self.ref, r[0], r[1], r[2], _stream()), "tucker_set_plain")
+
+    def read_desc(self):
+        """(nblk, ranks, blocks) with blocks = [(off, r, core_ptr, scale)]."""
+        torch.cuda.current_stream().synchronize()
+        raw = self.desc.cpu().numpy().tobytes()
+        nblk, r1, r2, r3 = struct.unpack_from("4i", raw, 0)
+        blocks = []
+        for b in range(nblk):
+            o = 32 + 40 * b
+            off = struct.unpack_from("3i", raw, o)
+            rr = struct.unpack_from("3i", raw, o + 12)
+            ptr, = struct.unpack_from("Q", raw, o + 24)
+            sc, = struct.unpack_from("d", raw, o + 32)
+            blocks.append((off, rr, ptr, sc))
+        return nblk, (r1, r2, r3), blocks
+
+    def factors_numpy(self, ranks):
+        return [self.U[t][: ranks[t]].double().cpu().numpy().T.copy() for t in range(3)]
+
+    def to_numpy(self, others=(), fallback=None):
+        """(core, factors) on the host; a block core is returned as a dense block-diagonal array, with
+        block cores looked up among this tensor and ``others`` by device pointer (``fallback(shape)``
+        supplies a host array for a block whose core is owned by the library, e.g. the rhs)."""
+        nblk, ranks, blocks = self.read_desc()
+        fac = self.factors_numpy(ranks)
+        pool = {self.core.data_ptr(): self}
+        for o in others:
+            pool[o.core.data_ptr()] = o
+        core = np.zeros(ranks)
+        for off, rr, ptr, sc in blocks:
+            src = None
+            for base, T in pool.items():
+                end = base + T.core.numel() * T.core.element_size()
+                if base <= ptr < end:
+                    src = (T, (ptr - base) // T.core.element_size())
+            if src is None:
+                if fallback is None:
+                    raise KeyError("block core not among the known tensors")
+                g = np.asarray(fallback(rr), dtype=np.float64)
+            else:
+                T, start = src
+                cnt = rr[0] * rr[1] * rr[2]
+                g = T.core[start:start + cnt].double().cpu().numpy().reshape(rr, order="F")
+            core[off[0]:off[0] + rr[0], off[1]:off[1] + rr[1], off[2]:off[2] + rr[2]] += sc * g
+        return core, fac
+
+
+class Problem:
+    def __init__(self, handle, dtype):
+        self.h = C.c_void_p(handle)
+        self.dtype = dtype
+        self.info = L.ProblemInfo()
+        check(L.load().tpcg_problem_get_info(self.h, C.byref(self.info)), "tpcg_problem_get_info")
+
+    def __del__(self):
+        try:
+            if self.h:
+                L.load().tpcg_problem_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def export(self):
+        """Host copies of the setup data (double)."""
+        i = self.info
+        n, p, R, n1, n2, RP = i.n, i.p, i.R, i.n1, i.n2, i.RP
+        out = {"w": np.zeros(R), "bands": np.zeros(R * 3 * (2 * p + 1) * n), "f_core": np.zeros(i.rf[0] * i.rf[1] * i.rf[2]),
+               "f_U0": np.zeros(n * i.rf[0]), "f_U1": np.zeros(n * i.rf[1]), "f_U2": np.zeros(n * i.rf[2]),
+               "lam": np.zeros(n), "mu": np.zeros(n1), "v2u2": np.zeros(max(n * n2, 1)), "omega": np.zeros(RP),
+               "alpha": np.zeros(RP)}
+        keys = ["w", "bands", "f_core", "f_U0", "f_U1", "f_U2", "lam", "mu", "v2u2", "omega", "alpha"]
+        ptrs = [out[k].ctypes.data_as(C.c_void_p) for k in keys]
+        check(L.load().tpcg_problem_export(self.h, *ptrs), "tpcg_problem_export")
+        return out
+
+
+def tpcg_setup(kind: int, amp: float, degree: int, n: int, dtype: int = L.F64, eps_geo=0.0, eps_prec=0.0) -> Problem:
+    g = L.Geometry(kind, amp, eps_geo, eps_prec)
+    h = C.c_void_p()
+    check(L.load().tpcg_setup(C.byref(g), degree, n, dtype, C.byref(h)), "tpcg_setup")
+    return Problem(h.value, dtype)
+
+
+def tpcg_problem_create(n, p, terms, f_core, f_U, fd, dtype=L.F64) -> Problem:
+    """Problem from host arrays.  terms: list of (w, [K1, K2, K3]) dense banded n x n matrices;
+    fd: dict with lam, mu, W (dense n x n1), v2u2 (n x n2), omega, alpha, lambda_min."""
+    R = len(terms)
+    bw = 2 * p + 1
+    bands = np.zeros((R, 3, bw, n))
+    for j, (w, mats) in enumerate(terms):
+        for t in range(3):
+            K = mats[t]
+            for d in range(bw):
+                for i in range(n):
+                    jj = i + d - p
+                    if 0 <= jj < n:
+                        bands[j, t, d, i] = K[i, jj]
+    keep = []
+
+    def dp(a, ct=C.c_double):
+        a = np.ascontiguousarray(a, dtype=np.float64 if ct is C.c_double else np.int32)
+        keep.append(a)
+        return a.ctypes.data_as(C.POINTER(ct))
+
+    W = np.asarray(fd["W"])
+    n1 = W.shape[1]
+    rowptr, cols, vals = [0], [], []
+    for i in range(n):
+        nz = np.nonzero(W[i])[0]
+        cols += list(nz)
+        vals += list(W[i, nz])
+        rowptr.append(len(cols))
+    a = L.ProblemArrays()
+    a.n, a.p, a.R, a.dtype = n, p, R, dtype
+    a.w = dp(np.array([t[0] for t in terms], dtype=np.float64))
+    a.bands = dp(bands.reshape(-1))
+    r = f_core.shape
+    a.rf = (C.c_int * 3)(*r)
+    a.f_core = dp(np.asarray(f_core).reshape(-1, order="F"))
+    a.f_U = (C.POINTER(C.c_double) * 3)(*[dp(np.asarray(f_U[t]).reshape(-1, order="F")) for t in range(3)])
+    n2 = n - n1
+    a.n1, a.n2, a.RP = n1, n2, len(fd["omega"])
+    a.w_nnz = len(vals)
+    a.lam = dp(fd["lam"])
+    a.mu = dp(fd["mu"])
+    a.w_rowptr = dp(np.array(rowptr), C.c_int)
+    a.w_col = dp(np.array(cols if cols else [0]), C.c_int)
+    a.w_val = dp(np.array(vals if vals else [0.0]))
+    a.v2u2 = dp(np.asarray(fd["v2u2"]).reshape(-1, order="F")) if n2 > 0 else C.POINTER(C.c_double)()
+    a.omega = dp(fd["omega"])
+    a.alpha = dp(fd["alpha"])
+    a.lambda_min = float(fd["lambda_min"])
+    h = C.c_void_p()
+    check(L.load().tpcg_problem_create(C.byref(a), C.byref(h)), "tpcg_problem_create")
+    return Problem(h.value, dtype)
+
+
+class Ctx:
+    def __init__(self, n, max_cols, rank_cap, dtype=L.F64):
+        h = C.c_void_p()
+        check(L.load().tpcg_ctx_create(n, max_cols, rank_cap, dtype, C.byref(h)), "tpcg_ctx_create")
+        self.h = h
+        self.n, self.max_cols, self.rank_cap, self.dtype = n, max_cols, rank_cap, dtype
+
+    def __del__(self):
+        try:
+            if self.h:
+                L.load().tpcg_ctx_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def tucker_apply(pb: Problem, x: Tucker, y: Tucker, stream=None):
+    check(L.load().tucker_apply(pb.h, x.ref, y.ref, _stream(stream)), "tucker_apply")
+
+
+def tucker_residual(pb: Problem, x: Tucker, y: Tucker, stream=None):
+    check(L.load().tucker_residual(pb.h, x.ref, y.ref, _stream(stream)), "tucker_residual")
+
+
+def tucker_axpby(a, x: Tucker, b, y: Tucker, z: Tucker, stream=None):
+    """z = a x + b y; a, b are floats or one-element float64 cuda tensors."""
+    ad = a if isinstance(a, torch.Tensor) else None
+    bd = b if isinstance(b, torch.Tensor) else None
+    check(L.load().tucker_axpby(0.0 if ad is not None else float(a), _dptr(ad), x.ref,
+                                0.0 if bd is not None else float(b), _dptr(bd), y.ref, z.ref, _stream(stream)),
+          "tucker_axpby")
+
+
+def tucker_dot(ctx: Ctx, x: Tucker, y: Tucker, out=None, stream=None):
+    o = out if out is not None else torch.zeros(1, dtype=torch.float64, device="cuda")
+    check(L.load().tucker_dot(ctx.h, x.ref, y.ref, _dptr(o), _stream(stream)), "tucker_dot")
+    return o
+
+
+def tucker_round(ctx: Ctx, y: Tucker, eps, rank_cap=0, info=None, stream=None):
+    ed = eps if isinstance(eps, torch.Tensor) else None
+    check(L.load().tucker_round(ctx.h, y.ref, 0.0 if ed is not None else float(eps), _dptr(ed), int(rank_cap),
+                                _dptr(info), _stream(stream)), "tucker_round")
+
+
+def fd_precond_apply(pb: Problem, ctx: Ctx, s: Tucker, v: Tucker, stream=None):
+    check(L.load().fd_precond_apply(pb.h, ctx.h, s.ref, v.ref, _stream(stream)), "fd_precond_apply")
+
+
+def tpcg_params(**kw):
+    p = L.Params()
+    L.load().tpcg_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def tpcg_solve(pb: Problem, ctx: Ctx, x: Tucker, stream=None, **kw):
+    prm = tpcg_params(**kw)
+    st = L.Stats()
+    code = L.load().tpcg_solve(pb.h, ctx.h, C.byref(prm), x.ref, C.byref(st), _stream(stream))
+    if code not in (0, 3):
+        check(code, "tpcg_solve")
+    return st

@@ -1,0 +1,731 @@
+// C ABI entry points: contexts, problems, Tucker operations and the TPCG driver (Alg. 5).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "setup.h"
+
+namespace tpcg {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+static inline size_t elt_of(int dtype) { return dtype == TPCG_F64 ? sizeof(double) : sizeof(float); }
+
+static int dmalloc(void** p, size_t bytes, std::vector<void*>* owned) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        *p = nullptr;
+        return TPCG_E_NOMEM;
+    }
+    if (owned) owned->push_back(*p);
+    return TPCG_OK;
+}
+
+// upload host doubles converted to the compute dtype
+static int upload(void** dst, const double* src, size_t count, int dtype, std::vector<void*>* owned) {
+    TPCG_TRY(dmalloc(dst, std::max<size_t>(count, 1) * elt_of(dtype), owned));
+    if (count == 0) return TPCG_OK;
+    if (dtype == TPCG_F64) {
+        TPCG_CUDA(cudaMemcpy(*dst, src, count * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> tmp(src, src + count);
+        TPCG_CUDA(cudaMemcpy(*dst, tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return TPCG_OK;
+}
+
+static int upload_int(int** dst, const int* src, size_t count, std::vector<void*>* owned) {
+    TPCG_TRY(dmalloc(reinterpret_cast<void**>(dst), std::max<size_t>(count, 1) * sizeof(int), owned));
+    if (count) TPCG_CUDA(cudaMemcpy(*dst, src, count * sizeof(int), cudaMemcpyHostToDevice));
+    return TPCG_OK;
+}
+
+// ------------------------------------------------------------------------------------ scalars of Alg. 5
+enum {
+    S_NF = 0, S_NR, S_ETA, S_RP, S_XI, S_OMEGA, S_EPS, S_EPSMIN, S_PXK, S_PXN, S_PP, S_V, S_DONE, S_ZQ, S_BETA,
+    S_STOP, S_RR, S_BAD, S_TRIALS, S_COUNT
+};
+enum { P_TOL = 0, P_EPS0, P_EPSMIN, P_ALPHA, P_DELTA, P_BT, P_COUNT };
+enum { OP_INIT = 0, OP_OMEGA, OP_DT, OP_RES, OP_BETA, OP_XI };
+
+__global__ void scalar_kernel(int op, double* s, const double* prm) {
+    if (threadIdx.x != 0) return;
+    switch (op) {
+        case OP_INIT: {   // r_0 = f (x_0 = 0), s[S_RR] = <f, f>
+            double nf = sqrt(fmax(s[S_RR], 0.0));
+            s[S_NF] = nf;
+            s[S_NR] = nf;
+            s[S_ETA] = nf > 0 ? prm[P_BT] * prm[P_TOL] : 1.0;
+            s[S_EPS] = prm[P_EPS0];
+            s[S_EPSMIN] = prm[P_EPSMIN] > 0 ? prm[P_EPSMIN] : prm[P_TOL] * nf * 0.1;
+            s[S_STOP] = (nf <= 0.0) ? 1.0 : 0.0;
+            s[S_BAD] = isfinite(nf) ? 0.0 : 1.0;
+            s[S_TRIALS] = 0.0;
+            break;
+        }
+        case OP_OMEGA: {
+            double xi = s[S_XI];
+            if (!(xi > 0.0) || !isfinite(xi) || !isfinite(s[S_RP])) s[S_BAD] = 1.0;
+            s[S_OMEGA] = s[S_RP] / xi;
+            break;
+        }
+        case OP_DT: {     // Alg. 2: v = (Delta x~ . Delta x) / ||Delta x~||^2 with Delta x~ = omega p
+            double den = s[S_OMEGA] * s[S_PP];
+            double v = den != 0.0 ? (s[S_PXN] - s[S_PXK]) / den : 1.0;
+            s[S_V] = v;
+            s[S_TRIALS] += 1.0;
+            if (fabs(v - 1.0) < prm[P_DELTA] || !isfinite(v)) {
+                s[S_DONE] = 1.0;
+            } else if (prm[P_ALPHA] * s[S_EPS] > s[S_EPSMIN]) {
+                s[S_EPS] *= prm[P_ALPHA];
+                s[S_DONE] = 0.0;
+            } else {
+                s[S_DONE] = 1.0;
+            }
+            break;
+        }
+        case OP_RES: {    // after r_{k+1}: ||r||, eta_{k+1} (eq. rel_tol_iterates), stopping test
+            double nr = sqrt(fmax(s[S_RR], 0.0));
+            s[S_NR] = nr;
+            s[S_ETA] = nr > 0 ? fmin(prm[P_BT] * prm[P_TOL] * s[S_NF] / nr, 1.0) : 1.0;
+            s[S_STOP] = (nr <= prm[P_TOL] * s[S_NF]) ? 1.0 : 0.0;
+            if (!isfinite(nr)) s[S_BAD] = 1.0;
+            break;
+        }
+        case OP_BETA: {
+            s[S_BETA] = -s[S_ZQ] / s[S_XI];
+            break;
+        }
+        case OP_XI: {
+            if (!(s[S_XI] > 0.0) || !isfinite(s[S_XI])) s[S_BAD] = 1.0;
+            break;
+        }
+    }
+}
+
+void launch_scalar(int op, double* s, const double* prm, cudaStream_t st) {
+    scalar_kernel<<<1, 32, 0, st>>>(op, s, prm);
+}
+
+// ------------------------------------------------------------------------------------ dispatch helpers
+template <typename F>
+static int by_dtype(int dtype, F&& f) {
+    if (dtype == TPCG_F64) return f(double());
+    if (dtype == TPCG_F32) return f(float());
+    set_error("unknown dtype");
+    return TPCG_E_INVALID;
+}
+
+static int check_tensor(const tucker_t* t, int n, int dtype, const char* what) {
+    if (!t || !t->desc || !t->U[0] || !t->U[1] || !t->U[2] || !t->core) {
+        set_error(std::string(what) + ": null pointer in tucker_t");
+        return TPCG_E_INVALID;
+    }
+    if (t->n != n || t->dtype != dtype || t->cap <= 0 || t->core_cap < 0) {
+        set_error(std::string(what) + ": tucker_t has wrong n/dtype/cap");
+        return TPCG_E_INVALID;
+    }
+    return TPCG_OK;
+}
+
+}  // namespace tpcg
+
+using namespace tpcg;
+
+// ======================================================================================= misc
+extern "C" const char* tpcg_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char* tpcg_version(void) { return "tpcg-gb300 0.1 (sm_103a)"; }
+
+extern "C" void tpcg_params_default(tpcg_params* p) {
+    p->tol = 1e-6;
+    p->eps0 = 0.1;
+    p->eps_min = 0.0;
+    p->alpha = 0.5;
+    p->delta = 1e-3;
+    p->beta_trunc = 0.1;
+    p->max_it = 500;
+    p->rank_cap = 0;
+}
+
+// ======================================================================================= contexts
+static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) {
+    const size_t e = elt_of(dtype);
+    const size_t nn = (size_t)n * n;
+    size_t i = 0;
+    sizes[i++] = (size_t)n * nn * e;                         // Z0
+    sizes[i++] = (size_t)n * nn * e;                         // Z1
+    sizes[i++] = nn * (size_t)max_cols * e;                  // Wm
+    sizes[i++] = (size_t)max_cols * n * rc * e;              // T1
+    for (int t = 0; t < 9; ++t) sizes[i++] = nn * e;         // Rq, Qq, Yw
+    sizes[i++] = nn * e;                                     // Gm
+    sizes[i++] = (size_t)MAX_SPLIT * nn * e;                 // Part
+    for (int t = 0; t < 3; ++t) sizes[i++] = nn * e;         // S
+    sizes[i++] = (size_t)n * sizeof(double);                 // evals
+    sizes[i++] = (2 * TPCG_MAX_BLOCKS + 64) * sizeof(GemmArgs);
+    sizes[i++] = sizeof(RoundPlan);
+    sizes[i++] = 256 * sizeof(double);                       // scal
+    sizes[i++] = 3 * (size_t)rc * rc * e;                    // dotw
+    sizes[i++] = 2 * (size_t)rc * rc * rc * e;               // dotT
+    for (int t = 0; t < 12; ++t) sizes[i++] = (size_t)n * max_cols * e;   // fd scratch
+    size_t tot = 0;
+    for (size_t j = 0; j < i; ++j) tot += (sizes[j] + 255) & ~(size_t)255;
+    return tot;
+}
+
+extern "C" size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype) {
+    size_t sizes[64];
+    return ctx_layout(n, max_cols, rank_cap, dtype, sizes);
+}
+
+extern "C" void tpcg_ctx_destroy(tpcg_ctx c) {
+    if (!c) return;
+    for (void* p : c->owned) cudaFree(p);
+    delete c;
+}
+
+extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpcg_ctx* out) {
+    if (!out || n < 2 || n > 1024 || max_cols < 1 || rank_cap < 1 || rank_cap > n || rank_cap > 256 ||
+        (dtype != TPCG_F64 && dtype != TPCG_F32)) {
+        set_error("tpcg_ctx_create: invalid arguments (need 2 <= n <= 1024, 1 <= rank_cap <= min(n, 256))");
+        return TPCG_E_INVALID;
+    }
+    tpcg_ctx c = new tpcg_ctx_s();
+    c->n = n;
+    c->max_cols = max_cols;
+    c->rank_cap = rank_cap;
+    c->dtype = dtype;
+    c->elt = elt_of(dtype);
+    c->have_tens = false;
+    c->tens_cap = 0;
+    size_t sizes[64];
+    ctx_layout(n, max_cols, rank_cap, dtype, sizes);
+    void** slots[64];
+    int i = 0;
+    slots[i++] = &c->Z0;
+    slots[i++] = &c->Z1;
+    slots[i++] = &c->Wm;
+    slots[i++] = &c->T1;
+    for (int t = 0; t < 3; ++t) slots[i++] = &c->Rq[t];
+    for (int t = 0; t < 3; ++t) slots[i++] = &c->Qq[t];
+    for (int t = 0; t < 3; ++t) slots[i++] = &c->Yw[t];
+    slots[i++] = &c->Gm;
+    slots[i++] = &c->Part;
+    for (int t = 0; t < 3; ++t) slots[i++] = &c->S[t];
+    slots[i++] = reinterpret_cast<void**>(&c->evals);
+    slots[i++] = reinterpret_cast<void**>(&c->gargs);
+    slots[i++] = reinterpret_cast<void**>(&c->plan);
+    slots[i++] = reinterpret_cast<void**>(&c->scal);
+    slots[i++] = reinterpret_cast<void**>(&c->dotw);
+    slots[i++] = &c->dotT;
+    for (int t = 0; t < 3; ++t)
+        for (int q = 0; q < 4; ++q) slots[i++] = &c->fd[t][q];
+    for (int j = 0; j < i; ++j) {
+        int s = dmalloc(slots[j], sizes[j], &c->owned);
+        if (s != TPCG_OK) {
+            tpcg_ctx_destroy(c);
+            return s;
+        }
+    }
+    if (cudaMemset(c->scal, 0, 256 * sizeof(double)) != cudaSuccess) {
+        set_error("cudaMemset failed");
+        tpcg_ctx_destroy(c);
+        return TPCG_E_CUDA;
+    }
+    *out = c;
+    return TPCG_OK;
+}
+
+// ======================================================================================= problems
+static void host_orthonormalize_rhs(tpcg_problem pb) {
+    // F_t = Q_t R_t (modified Gram-Schmidt, twice), core <- core x_t R_t: an exact change of basis.
+    const int n = pb->n;
+    std::vector<double> core = pb->f_core;
+    int r[3] = {pb->rf[0], pb->rf[1], pb->rf[2]};
+    for (int t = 0; t < 3; ++t) {
+        const int k = r[t];
+        std::vector<double>& F = pb->f_U[t];
+        std::vector<double> Rm((size_t)k * k, 0.0);
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<double> Rp((size_t)k * k, 0.0);
+            for (int j = 0; j < k; ++j) {
+                double* fj = &F[(size_t)j * n];
+                for (int i = 0; i < j; ++i) {
+                    const double* fi = &F[(size_t)i * n];
+                    double d = 0;
+                    for (int q = 0; q < n; ++q) d += fi[q] * fj[q];
+                    for (int q = 0; q < n; ++q) fj[q] -= d * fi[q];
+                    Rp[i + (size_t)j * k] = d;
+                }
+                double nr = 0;
+                for (int q = 0; q < n; ++q) nr += fj[q] * fj[q];
+                nr = sqrt(nr);
+                Rp[j + (size_t)j * k] = nr;
+                if (nr > 0)
+                    for (int q = 0; q < n; ++q) fj[q] /= nr;
+            }
+            if (pass == 0) {
+                Rm = Rp;
+            } else {   // R = Rp * Rm
+                std::vector<double> Rn((size_t)k * k, 0.0);
+                for (int i = 0; i < k; ++i)
+                    for (int j = 0; j < k; ++j) {
+                        double s = 0;
+                        for (int q = 0; q < k; ++q) s += Rp[i + (size_t)q * k] * Rm[q + (size_t)j * k];
+                        Rn[i + (size_t)j * k] = s;
+                    }
+                Rm = Rn;
+            }
+        }
+        // core <- core x_t Rm
+        std::vector<double> nc(core.size(), 0.0);
+        int d[3] = {r[0], r[1], r[2]};
+        for (int a = 0; a < d[0]; ++a)
+            for (int b = 0; b < d[1]; ++b)
+                for (int c = 0; c < d[2]; ++c) {
+                    int idx[3] = {a, b, c};
+                    double s = 0;
+                    for (int q = 0; q < k; ++q) {
+                        int jdx[3] = {a, b, c};
+                        jdx[t] = q;
+                        s += Rm[idx[t] + (size_t)q * k] * core[jdx[0] + (size_t)d[0] * (jdx[1] + (size_t)d[1] * jdx[2])];
+                    }
+                    nc[a + (size_t)d[0] * (b + (size_t)d[1] * c)] = s;
+                }
+        core = nc;
+    }
+    pb->f_core = core;
+}
+
+extern "C" void tpcg_problem_destroy(tpcg_problem pb) {
+    if (!pb) return;
+    void* ptrs[] = {pb->d_bands, pb->d_w, pb->d_lam, pb->d_mu, pb->d_wrow, pb->d_wcol, pb->d_wval, pb->d_wtrow,
+                    pb->d_wtcol, pb->d_wtval, pb->d_v2u2, pb->d_dst, pb->d_omega, pb->d_alpha, pb->d_scal,
+                    pb->d_f_store[0], pb->d_f_store[1], pb->d_f_store[2], pb->d_f_store[3], pb->d_f_store[4]};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete pb;
+}
+
+extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* out) {
+    if (!a || !out) return TPCG_E_INVALID;
+    const int n = a->n, p = a->p;
+    if (n < 2 || p < 1 || p > 5 || a->R < 1 || a->R > TPCG_MAX_BLOCKS - 1 || a->n1 < 1 || a->n2 < 0 ||
+        a->n1 + a->n2 != n || a->RP < 1 || a->RP > TPCG_MAX_BLOCKS || (a->dtype != TPCG_F64 && a->dtype != TPCG_F32) ||
+        !a->w || !a->bands || !a->f_core || !a->lam || !a->mu || !a->w_rowptr || !a->omega || !a->alpha ||
+        a->lambda_min <= 0) {
+        set_error("tpcg_problem_create: invalid arguments");
+        return TPCG_E_INVALID;
+    }
+    for (int t = 0; t < 3; ++t)
+        if (a->rf[t] < 1 || a->rf[t] > n || !a->f_U[t]) {
+            set_error("tpcg_problem_create: invalid rhs");
+            return TPCG_E_INVALID;
+        }
+    tpcg_problem pb = new tpcg_problem_s();
+    memset(pb->d_f_store, 0, sizeof(pb->d_f_store));
+    pb->d_bands = pb->d_w = nullptr;
+    pb->d_lam = pb->d_mu = pb->d_wval = pb->d_wtval = pb->d_v2u2 = pb->d_dst = nullptr;
+    pb->d_wrow = pb->d_wcol = pb->d_wtrow = pb->d_wtcol = nullptr;
+    pb->d_omega = pb->d_alpha = pb->d_scal = nullptr;
+    pb->n = n; pb->p = p; pb->R = a->R; pb->RP = a->RP; pb->n1 = a->n1; pb->n2 = a->n2; pb->dtype = a->dtype;
+    for (int t = 0; t < 3; ++t) pb->rf[t] = a->rf[t];
+    pb->lambda_min = a->lambda_min;
+    const int bw = 2 * p + 1;
+    pb->w.assign(a->w, a->w + a->R);
+    pb->bands.assign(a->bands, a->bands + (size_t)a->R * 3 * bw * n);
+    pb->f_core.assign(a->f_core, a->f_core + (size_t)a->rf[0] * a->rf[1] * a->rf[2]);
+    for (int t = 0; t < 3; ++t) pb->f_U[t].assign(a->f_U[t], a->f_U[t] + (size_t)n * a->rf[t]);
+    pb->lam.assign(a->lam, a->lam + n);
+    pb->mu.assign(a->mu, a->mu + a->n1);
+    const int nnz = a->w_rowptr[n];
+    pb->w_rowptr.assign(a->w_rowptr, a->w_rowptr + n + 1);
+    pb->w_col.assign(a->w_col, a->w_col + nnz);
+    pb->w_val.assign(a->w_val, a->w_val + nnz);
+    pb->v2u2.assign(a->v2u2 ? a->v2u2 : a->lam, a->v2u2 ? a->v2u2 + (size_t)n * a->n2 : a->lam);
+    pb->omega.assign(a->omega, a->omega + a->RP);
+    pb->alpha.assign(a->alpha, a->alpha + a->RP);
+    double lmax = 0;
+    for (int i = 0; i < n; ++i) lmax = std::max(lmax, pb->lam[i]);
+    pb->lambda_max = 3.0 * lmax;
+    for (int e = 0; e < nnz; ++e)
+        if (pb->w_col[e] < 0 || pb->w_col[e] >= a->n1) {
+            delete pb;
+            set_error("tpcg_problem_create: W column index out of range");
+            return TPCG_E_INVALID;
+        }
+    host_orthonormalize_rhs(pb);
+    double nf2 = 0;
+    for (double v : pb->f_core) nf2 += v * v;
+    pb->norm_f = sqrt(nf2);
+
+    // W^T in CSR
+    std::vector<int> trow(a->n1 + 1, 0), tcol(nnz);
+    std::vector<double> tval(nnz);
+    for (int e = 0; e < nnz; ++e) trow[pb->w_col[e] + 1]++;
+    for (int l = 0; l < a->n1; ++l) trow[l + 1] += trow[l];
+    {
+        std::vector<int> fill(trow.begin(), trow.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int e = pb->w_rowptr[i]; e < pb->w_rowptr[i + 1]; ++e) {
+                int l = pb->w_col[e];
+                tcol[fill[l]] = i;
+                tval[fill[l]] = pb->w_val[e];
+                fill[l]++;
+            }
+    }
+    // sine matrix U_dft[l, j] = sqrt2 sin(j pi x_l): DST-I points l/(n1+1) for odd p, DST-II (l - 1/2)/n1 for even p
+    const int n1 = a->n1;
+    std::vector<double> dst((size_t)n1 * n1);
+    for (int j = 1; j <= n1; ++j)
+        for (int l = 1; l <= n1; ++l) {
+            double xl = (p % 2 == 1) ? (double)l / (n1 + 1) : (l - 0.5) / n1;
+            // sin(j pi x) evaluated with the argument reduced exactly on the rational grid
+            double arg;
+            if (p % 2 == 1) {
+                long long m = ((long long)j * l) % (2LL * (n1 + 1));
+                arg = M_PI * (double)m / (n1 + 1);
+            } else {
+                long long m = ((long long)j * (2 * l - 1)) % (4LL * n1);
+                arg = M_PI * (double)m / (2.0 * n1);
+            }
+            (void)xl;
+            dst[(l - 1) + (size_t)(j - 1) * n1] = sqrt(2.0) * sin(arg);
+        }
+    std::vector<void*> owned;   // not used: problem buffers are tracked in the struct
+    int s = TPCG_OK;
+    auto fail = [&](int code) {
+        tpcg_problem_destroy(pb);
+        return code;
+    };
+    const int dt = a->dtype;
+    if ((s = upload(&pb->d_bands, pb->bands.data(), pb->bands.size(), dt, nullptr))) return fail(s);
+    if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_w), a->R * sizeof(double), nullptr))) return fail(s);
+    if (cudaMemcpy(pb->d_w, pb->w.data(), a->R * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TPCG_E_CUDA);
+    if ((s = upload(&pb->d_lam, pb->lam.data(), n, dt, nullptr))) return fail(s);
+    if ((s = upload(&pb->d_mu, pb->mu.data(), n1, dt, nullptr))) return fail(s);
+    if ((s = upload_int(&pb->d_wrow, pb->w_rowptr.data(), n + 1, nullptr))) return fail(s);
+    if ((s = upload_int(&pb->d_wcol, pb->w_col.data(), nnz, nullptr))) return fail(s);
+    if ((s = upload(&pb->d_wval, pb->w_val.data(), nnz, dt, nullptr))) return fail(s);
+    if ((s = upload_int(&pb->d_wtrow, trow.data(), n1 + 1, nullptr))) return fail(s);
+    if ((s = upload_int(&pb->d_wtcol, tcol.data(), nnz, nullptr))) return fail(s);
+    if ((s = upload(&pb->d_wtval, tval.data(), nnz, dt, nullptr))) return fail(s);
+    if ((s = upload(&pb->d_v2u2, pb->v2u2.data(), (size_t)n * a->n2, dt, nullptr))) return fail(s);
+    if ((s = upload(&pb->d_dst, dst.data(), dst.size(), dt, nullptr))) return fail(s);
+    if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_omega), a->RP * sizeof(double), nullptr))) return fail(s);
+    if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_alpha), a->RP * sizeof(double), nullptr))) return fail(s);
+    if (cudaMemcpy(pb->d_omega, pb->omega.data(), a->RP * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(pb->d_alpha, pb->alpha.data(), a->RP * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(TPCG_E_CUDA);
+    if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_scal), 64 * sizeof(double), nullptr))) return fail(s);
+    cudaMemset(pb->d_scal, 0, 64 * sizeof(double));
+    // rhs tensor
+    tucker_t& f = pb->f;
+    f.dtype = dt;
+    f.n = n;
+    f.cap = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
+    f.core_cap = (long long)pb->rf[0] * pb->rf[1] * pb->rf[2];
+    for (int t = 0; t < 3; ++t) {
+        std::vector<double> padded((size_t)n * f.cap, 0.0);
+        std::copy(pb->f_U[t].begin(), pb->f_U[t].end(), padded.begin());
+        if ((s = upload(&pb->d_f_store[t], padded.data(), padded.size(), dt, nullptr))) return fail(s);
+        f.U[t] = pb->d_f_store[t];
+    }
+    if ((s = upload(&pb->d_f_store[3], pb->f_core.data(), pb->f_core.size(), dt, nullptr))) return fail(s);
+    f.core = pb->d_f_store[3];
+    if ((s = dmalloc(&pb->d_f_store[4], TPCG_DESC_BYTES, nullptr))) return fail(s);
+    f.desc = pb->d_f_store[4];
+    if ((s = set_plain(&f, pb->rf[0], pb->rf[1], pb->rf[2], 0))) return fail(s);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        set_error("tpcg_problem_create: device error");
+        return fail(TPCG_E_CUDA);
+    }
+    *out = pb;
+    return TPCG_OK;
+}
+
+extern "C" int tpcg_setup(const tpcg_geometry* geo, int degree, int n, int dtype, tpcg_problem* out) {
+    if (!geo || !out) return TPCG_E_INVALID;
+    HostProblem hp;
+    int s = host_setup(*geo, degree, n, &hp);
+    if (s != TPCG_OK) return s;
+    tpcg_problem_arrays a{};
+    a.n = n; a.p = degree; a.R = hp.R; a.dtype = dtype;
+    a.w = hp.w.data();
+    a.bands = hp.bands.data();
+    for (int t = 0; t < 3; ++t) { a.rf[t] = hp.rf[t]; a.f_U[t] = hp.f_U[t].data(); }
+    a.f_core = hp.f_core.data();
+    a.n1 = hp.n1; a.n2 = hp.n2; a.RP = hp.RP; a.w_nnz = (int)hp.w_val.size();
+    a.lam = hp.lam.data(); a.mu = hp.mu.data();
+    a.w_rowptr = hp.w_rowptr.data(); a.w_col = hp.w_col.data(); a.w_val = hp.w_val.data();
+    a.v2u2 = hp.v2u2.empty() ? nullptr : hp.v2u2.data();
+    a.omega = hp.omega.data(); a.alpha = hp.alpha.data(); a.lambda_min = hp.lambda_min;
+    return tpcg_problem_create(&a, out);
+}
+
+extern "C" int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* o) {
+    if (!pb || !o) return TPCG_E_INVALID;
+    o->n = pb->n; o->p = pb->p; o->R = pb->R; o->RP = pb->RP; o->n1 = pb->n1; o->n2 = pb->n2; o->dtype = pb->dtype;
+    for (int t = 0; t < 3; ++t) o->rf[t] = pb->rf[t];
+    o->lambda_min = pb->lambda_min;
+    o->lambda_max = pb->lambda_max;
+    o->MP = pb->lambda_max / pb->lambda_min;
+    o->norm_f = pb->norm_f;
+    return TPCG_OK;
+}
+
+extern "C" int tpcg_problem_export(tpcg_problem pb, double* w, double* bands, double* f_core, double* f_U0,
+                                   double* f_U1, double* f_U2, double* lam, double* mu, double* v2u2, double* omega,
+                                   double* alpha) {
+    if (!pb) return TPCG_E_INVALID;
+    auto cp = [](double* dst, const std::vector<double>& v) {
+        if (dst && !v.empty()) memcpy(dst, v.data(), v.size() * sizeof(double));
+    };
+    cp(w, pb->w);
+    cp(bands, pb->bands);
+    cp(f_core, pb->f_core);
+    cp(f_U0, pb->f_U[0]);
+    cp(f_U1, pb->f_U[1]);
+    cp(f_U2, pb->f_U[2]);
+    cp(lam, pb->lam);
+    cp(mu, pb->mu);
+    if (pb->n2 > 0) cp(v2u2, pb->v2u2);
+    cp(omega, pb->omega);
+    cp(alpha, pb->alpha);
+    return TPCG_OK;
+}
+
+// ======================================================================================= Tucker ops
+extern "C" int tucker_set_plain(tucker_t* t, int r1, int r2, int r3, void* stream) {
+    if (!t || !t->desc || r1 < 0 || r2 < 0 || r3 < 0 || r1 > t->cap || r2 > t->cap || r3 > t->cap ||
+        (long long)r1 * r2 * r3 > t->core_cap) {
+        set_error("tucker_set_plain: ranks exceed capacities");
+        return TPCG_E_INVALID;
+    }
+    return set_plain(t, r1, r2, r3, S(stream));
+}
+
+extern "C" int tucker_get_ranks(const tucker_t* t, int* r3_out, int* nblk_out, void* stream) {
+    if (!t || !t->desc) return TPCG_E_INVALID;
+    int h[4];
+    TPCG_CUDA(cudaMemcpyAsync(h, t->desc, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
+    TPCG_CUDA(cudaStreamSynchronize(S(stream)));
+    if (nblk_out) *nblk_out = h[0];
+    if (r3_out)
+        for (int q = 0; q < 3; ++q) r3_out[q] = h[1 + q];
+    return TPCG_OK;
+}
+
+extern "C" int tucker_apply(tpcg_problem pb, const tucker_t* x, tucker_t* y, void* stream) {
+    if (!pb) return TPCG_E_INVALID;
+    TPCG_TRY(check_tensor(x, pb->n, pb->dtype, "tucker_apply x"));
+    TPCG_TRY(check_tensor(y, pb->n, pb->dtype, "tucker_apply y"));
+    return by_dtype(pb->dtype, [&](auto z) { return apply_impl<decltype(z)>(pb, x, y, false, S(stream)); });
+}
+
+extern "C" int tucker_residual(tpcg_problem pb, const tucker_t* x, tucker_t* y, void* stream) {
+    if (!pb) return TPCG_E_INVALID;
+    TPCG_TRY(check_tensor(x, pb->n, pb->dtype, "tucker_residual x"));
+    TPCG_TRY(check_tensor(y, pb->n, pb->dtype, "tucker_residual y"));
+    return by_dtype(pb->dtype, [&](auto z) { return apply_impl<decltype(z)>(pb, x, y, true, S(stream)); });
+}
+
+extern "C" int tucker_axpby(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev,
+                            const tucker_t* y, tucker_t* z, void* stream) {
+    if (!x || !y || !z) return TPCG_E_INVALID;
+    TPCG_TRY(check_tensor(x, z->n, z->dtype, "tucker_axpby x"));
+    TPCG_TRY(check_tensor(y, z->n, z->dtype, "tucker_axpby y"));
+    TPCG_TRY(check_tensor(z, z->n, z->dtype, "tucker_axpby z"));
+    if (z == x || z == y || z->desc == x->desc || z->desc == y->desc) {
+        set_error("tucker_axpby: output must not alias an input");
+        return TPCG_E_INVALID;
+    }
+    return by_dtype(z->dtype, [&](auto q) {
+        return axpby_impl<decltype(q)>(a, a_dev, x, b, b_dev, y, z, nullptr, S(stream));
+    });
+}
+
+extern "C" int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, void* stream) {
+    if (!c || !out_dev) return TPCG_E_INVALID;
+    TPCG_TRY(check_tensor(x, c->n, c->dtype, "tucker_dot x"));
+    TPCG_TRY(check_tensor(y, c->n, c->dtype, "tucker_dot y"));
+    return by_dtype(c->dtype, [&](auto z) { return dot_impl<decltype(z)>(c, x, y, out_dev, S(stream)); });
+}
+
+extern "C" int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rank_cap,
+                            double* info_dev, void* stream) {
+    if (!c || (!eps_dev && !(eps >= 0.0))) return TPCG_E_INVALID;
+    TPCG_TRY(check_tensor(y, c->n, c->dtype, "tucker_round y"));
+    if (y->cap > c->max_cols) {
+        set_error("tucker_round: tensor capacity exceeds the context's max_cols");
+        return TPCG_E_INVALID;
+    }
+    return by_dtype(c->dtype, [&](auto z) {
+        return round_impl<decltype(z)>(c, y, eps, eps_dev, rank_cap, info_dev, S(stream));
+    });
+}
+
+extern "C" int fd_precond_apply(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, void* stream) {
+    if (!pb || !c || pb->n != c->n || pb->dtype != c->dtype) return TPCG_E_INVALID;
+    TPCG_TRY(check_tensor(s, pb->n, pb->dtype, "fd_precond_apply s"));
+    TPCG_TRY(check_tensor(v, pb->n, pb->dtype, "fd_precond_apply v"));
+    if (v->cap > c->max_cols) {
+        set_error("fd_precond_apply: output capacity exceeds the context's max_cols");
+        return TPCG_E_INVALID;
+    }
+    return by_dtype(pb->dtype, [&](auto z) { return fd_impl<decltype(z)>(pb, c, s, v, S(stream)); });
+}
+
+// ======================================================================================= TPCG (Alg. 5)
+static int ensure_tensors(tpcg_ctx c) {
+    if (c->have_tens) return TPCG_OK;
+    const int n = c->n, cap = c->max_cols, rc = c->rank_cap;
+    for (int i = 0; i < 10; ++i) {
+        tucker_t& t = c->tens[i];
+        t.dtype = c->dtype;
+        t.n = n;
+        t.cap = cap;
+        t.core_cap = (long long)rc * rc * rc;
+        for (int q = 0; q < 3; ++q) TPCG_TRY(dmalloc(&t.U[q], (size_t)n * cap * c->elt, &c->owned));
+        TPCG_TRY(dmalloc(&t.core, (size_t)t.core_cap * c->elt, &c->owned));
+        TPCG_TRY(dmalloc(&t.desc, TPCG_DESC_BYTES, &c->owned));
+        TPCG_CUDA(cudaMemset(t.desc, 0, TPCG_DESC_BYTES));
+    }
+    c->have_tens = true;
+    return TPCG_OK;
+}
+
+template <typename T>
+static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
+                      cudaStream_t s) {
+    TPCG_TRY(ensure_tensors(c));
+    const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
+    double* sc = c->scal;
+    double* dprm = c->scal + 100;
+    double hp[P_COUNT] = {prm->tol, prm->eps0, prm->eps_min, prm->alpha, prm->delta, prm->beta_trunc};
+    TPCG_CUDA(cudaMemcpyAsync(dprm, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
+    tucker_t* x = &c->tens[0];
+    tucker_t* r = &c->tens[1];
+    tucker_t* z = &c->tens[2];
+    tucker_t* p = &c->tens[3];
+    tucker_t* q = &c->tens[4];
+    tucker_t* big = &c->tens[5];
+    tucker_t* big2 = &c->tens[6];
+    double* eta = sc + S_ETA;
+    auto round_to = [&](tucker_t*& dst, const double* eps_dev) -> int {
+        // round `big` in place, then make it the new `dst` (swap buffers)
+        TPCG_TRY(round_impl<T>(c, big, 0.0, eps_dev, rc, nullptr, s));
+        std::swap(dst, big);
+        return TPCG_OK;
+    };
+    // x_0 = 0, r_0 = f
+    TPCG_TRY(set_zero(x, s));
+    TPCG_TRY(copy_tensor_impl<T>(&pb->f, r, c->n, c->max_cols, s));
+    TPCG_TRY(dot_impl<T>(c, r, r, sc + S_RR, s));
+    launch_scalar(OP_INIT, sc, dprm, s);
+    // z_0 = T(P^-1 r_0, eta_0), p_0 = z_0, q_0 = T(A p_0, eta_0), xi_0 = p_0 . q_0
+    TPCG_TRY(fd_impl<T>(pb, c, r, big, s));
+    TPCG_TRY(round_to(z, eta));
+    TPCG_TRY(copy_tensor_impl<T>(z, p, c->n, c->max_cols, s));
+    TPCG_TRY(apply_impl<T>(pb, p, big, false, s));
+    TPCG_TRY(round_to(q, eta));
+    TPCG_TRY(dot_impl<T>(c, p, q, sc + S_XI, s));
+    launch_scalar(OP_XI, sc, dprm, s);
+    double host[S_COUNT];
+    int k = 0;
+    int status = TPCG_OK;
+    int trials_total = 0;
+    for (;;) {
+        TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
+        TPCG_CUDA(cudaStreamSynchronize(s));
+        if (host[S_BAD] != 0.0) { status = TPCG_E_BREAKDOWN; break; }
+        if (host[S_STOP] != 0.0) break;
+        if (k >= prm->max_it) { status = TPCG_E_NOT_CONVERGED; break; }
+        // omega_k = r_k . p_k / xi_k
+        TPCG_TRY(dot_impl<T>(c, r, p, sc + S_RP, s));
+        launch_scalar(OP_OMEGA, sc, dprm, s);
+        // dynamic truncation of x_k + omega_k p_k (Alg. 2)
+        TPCG_TRY(dot_impl<T>(c, p, x, sc + S_PXK, s));
+        TPCG_TRY(dot_impl<T>(c, p, p, sc + S_PP, s));
+        TPCG_TRY(axpby_impl<T>(1.0, nullptr, x, 0.0, sc + S_OMEGA, p, big, nullptr, s));
+        for (int trial = 0;; ++trial) {
+            TPCG_TRY(copy_tensor_impl<T>(big, big2, c->n, c->max_cols, s));
+            TPCG_TRY(round_impl<T>(c, big2, 0.0, sc + S_EPS, rc, nullptr, s));
+            TPCG_TRY(dot_impl<T>(c, p, big2, sc + S_PXN, s));
+            launch_scalar(OP_DT, sc, dprm, s);
+            ++trials_total;
+            double done;
+            TPCG_CUDA(cudaMemcpyAsync(&done, sc + S_DONE, sizeof(double), cudaMemcpyDeviceToHost, s));
+            TPCG_CUDA(cudaStreamSynchronize(s));
+            if (done != 0.0 || trial > 64) break;
+        }
+        std::swap(x, big2);
+        // r_{k+1} = T(f - A x_{k+1}, eta_k); eta_{k+1}
+        TPCG_TRY(apply_impl<T>(pb, x, big, true, s));
+        TPCG_TRY(round_to(r, eta));
+        TPCG_TRY(dot_impl<T>(c, r, r, sc + S_RR, s));
+        launch_scalar(OP_RES, sc, dprm, s);
+        // z_{k+1} = T(P^-1 r_{k+1}, eta_{k+1});  beta_k = -z_{k+1} . q_k / xi_k
+        TPCG_TRY(fd_impl<T>(pb, c, r, big, s));
+        TPCG_TRY(round_to(z, eta));
+        TPCG_TRY(dot_impl<T>(c, z, q, sc + S_ZQ, s));
+        launch_scalar(OP_BETA, sc, dprm, s);
+        // p_{k+1} = T(z_{k+1} + beta_k p_k, eta_{k+1})
+        TPCG_TRY(axpby_impl<T>(1.0, nullptr, z, 0.0, sc + S_BETA, p, big, nullptr, s));
+        TPCG_TRY(round_to(p, eta));
+        // q_{k+1} = T(A p_{k+1}, eta_{k+1});  xi_{k+1} = p_{k+1} . q_{k+1}
+        TPCG_TRY(apply_impl<T>(pb, p, big, false, s));
+        TPCG_TRY(round_to(q, eta));
+        TPCG_TRY(dot_impl<T>(c, p, q, sc + S_XI, s));
+        launch_scalar(OP_XI, sc, dprm, s);
+        ++k;
+    }
+    // copy x into the caller's tensor
+    TPCG_TRY(copy_tensor_impl<T>(x, xout, c->n, xout->cap, s));
+    // (the internal tensors all have the same capacities, so their roles need no restoring)
+    int rk[3] = {0, 0, 0};
+    int nb = 0;
+    TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
+    TPCG_TRY(tucker_get_ranks(xout, rk, &nb, s));
+    if (st) {
+        st->iters = k;
+        st->status = status;
+        st->rel_res = host[S_NF] > 0 ? host[S_NR] / host[S_NF] : 0.0;
+        for (int t = 0; t < 3; ++t) st->rank[t] = rk[t];
+        const double n = c->n;
+        st->mem_compression = ((double)rk[0] * rk[1] * rk[2] + n * (rk[0] + rk[1] + rk[2])) / (n * n * n) * 100.0;
+        st->dt_trials = trials_total;
+        st->max_rank_seen = std::max(rk[0], std::max(rk[1], rk[2]));
+    }
+    return status;
+}
+
+extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st,
+                          void* stream) {
+    if (!pb || !c || !prm || pb->n != c->n || pb->dtype != c->dtype || prm->tol <= 0 || prm->alpha <= 0 ||
+        prm->alpha >= 1 || prm->max_it < 0) {
+        set_error("tpcg_solve: invalid arguments");
+        return TPCG_E_INVALID;
+    }
+    TPCG_TRY(check_tensor(x, pb->n, pb->dtype, "tpcg_solve x"));
+    const int rfmax = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
+    const int need = std::max(pb->R * c->rank_cap + rfmax, std::max(pb->RP * c->rank_cap, 2 * c->rank_cap));
+    if (c->max_cols < need) {
+        set_error("tpcg_solve: context max_cols " + std::to_string(c->max_cols) + " < required " +
+                  std::to_string(need));
+        return TPCG_E_INVALID;
+    }
+    return by_dtype(pb->dtype, [&](auto z) { return solve_impl<decltype(z)>(pb, c, prm, x, st, S(stream)); });
+}

@@ -1,0 +1,152 @@
+// Grouped, batched GEMM whose shapes and pointers are read from device memory (GemmArgs), so that
+// rank-dependent sizes decided on the GPU (truncation ranks) need no host round trip and the launch
+// sequence is fixed (CUDA-graph capturable).  Column-major, op(A) is M x K, op(B) is K x N.
+//
+// Tiling: 64 x 64 output tile per CTA, K-step 16, 256 threads, 4 x 4 outputs per thread held in
+// registers; operands staged through shared memory with loads coalesced along the contiguous index.
+#pragma once
+
+#include "common.cuh"
+
+namespace tpcg {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GTHREADS = 256;
+
+template <typename T, bool TA>
+__device__ __forceinline__ void gemm_load_a(T (*As)[GBM + 1], const T* A, long long lda, int M, int K, int m0,
+                                            int k0, int tid) {
+#pragma unroll
+    for (int q = 0; q < (GBM * GBK) / GTHREADS; ++q) {
+        int e = tid + q * GTHREADS;
+        int mm, kk;
+        if (!TA) { mm = e % GBM; kk = e / GBM; }   // A[m + k lda]: contiguous in m
+        else     { kk = e % GBK; mm = e / GBK; }   // A[k + m lda]: contiguous in k
+        int m = m0 + mm, k = k0 + kk;
+        T v = T(0);
+        if (m < M && k < K) v = TA ? A[k + (long long)m * lda] : A[m + (long long)k * lda];
+        As[kk][mm] = v;
+    }
+}
+
+template <typename T, bool TB>
+__device__ __forceinline__ void gemm_load_b(T (*Bs)[GBN + 1], const T* B, long long ldb, int N, int K, int n0,
+                                            int k0, int tid) {
+#pragma unroll
+    for (int q = 0; q < (GBN * GBK) / GTHREADS; ++q) {
+        int e = tid + q * GTHREADS;
+        int nn, kk;
+        if (!TB) { kk = e % GBK; nn = e / GBK; }   // B[k + n ldb]: contiguous in k
+        else     { nn = e % GBN; kk = e / GBN; }   // B[n + k ldb]: contiguous in n
+        int nI = n0 + nn, k = k0 + kk;
+        T v = T(0);
+        if (nI < N && k < K) v = TB ? B[nI + (long long)k * ldb] : B[k + (long long)nI * ldb];
+        Bs[kk][nn] = v;
+    }
+}
+
+// grid: (ceil(Mmax/64), ceil(Nmax/64), ngroups_max * bmax).  count_dev (optional) caps the group count.
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(GTHREADS) gemm_grouped_kernel(const GemmArgs* __restrict__ args,
+                                                                const int* __restrict__ count_dev, int bmax,
+                                                                int zmax) {
+    __shared__ T As[GBK][GBM + 1];
+    __shared__ T Bs[GBK][GBN + 1];
+    const int gcount = count_dev != nullptr ? *count_dev : (zmax / bmax);
+    for (int z = blockIdx.z; z < zmax; z += gridDim.z) {
+    const int g = z / bmax;
+    const int ib = z % bmax;
+    if (g >= gcount) break;
+    const GemmArgs a = args[g];
+    if (a.acc ? (ib != 0) : (ib >= a.nbatch)) continue;
+    const int M = a.M, N = a.N, K = a.K;
+    const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+    if (m0 >= M || n0 >= N) continue;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+    const int nb = a.acc ? a.nbatch : 1;
+    for (int b = 0; b < nb; ++b) {
+        const int bi = a.acc ? b : ib;
+        const T* A = static_cast<const T*>(a.A) + (long long)bi * a.sA;
+        const T* B = static_cast<const T*>(a.B) + (long long)bi * a.sB;
+        for (int k0 = 0; k0 < K; k0 += GBK) {
+            gemm_load_a<T, TA>(As, A, a.lda, M, K, m0, k0, tid);
+            gemm_load_b<T, TB>(Bs, B, a.ldb, N, K, n0, k0, tid);
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < GBK; ++kk) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+    T* C = static_cast<T*>(a.C) + (a.acc ? 0LL : (long long)ib * a.sC);
+    const T alpha = T(a.alpha), beta = T(a.beta);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tx + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nI = n0 + ty + 16 * j;
+            if (nI >= N) continue;
+            T* c = C + m + (long long)nI * a.ldc;
+            T v = alpha * acc[i][j];
+            if (a.beta != 0.0) v += beta * (*c);
+            *c = v;
+        }
+    }
+    __syncthreads();
+    }
+}
+
+// C = alpha * sum_{g < count} P_g + beta * C over an M x N column-major block (partials contiguous,
+// stride M*N); M, N, count read from device.
+template <typename T>
+__global__ void reduce_partials_kernel(const T* __restrict__ P, const int* Mdev, const int* Ndev,
+                                       const int* count_dev, T* __restrict__ C, long long ldc, double alpha,
+                                       double beta) {
+    const int M = *Mdev, N = *Ndev, cnt = *count_dev;
+    const long long MN = (long long)M * N;
+    if (ldc <= 0) ldc = M;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MN; e += (long long)gridDim.x * blockDim.x) {
+        T s = T(0);
+        for (int g = 0; g < cnt; ++g) s += P[g * MN + e];
+        const int m = (int)(e % M), nI = (int)(e / M);
+        T* c = C + m + (long long)nI * ldc;
+        T v = T(alpha) * s;
+        if (beta != 0.0) v += T(beta) * (*c);
+        *c = v;
+    }
+}
+
+template <typename T, bool TA, bool TB>
+inline int launch_gemm(const GemmArgs* args, const int* count_dev, int ngroups_max, int bmax, int Mmax, int Nmax,
+                       cudaStream_t st) {
+    if (ngroups_max <= 0 || bmax <= 0 || Mmax <= 0 || Nmax <= 0) return TPCG_OK;
+    const long long zmax = (long long)ngroups_max * bmax;
+    dim3 grid((Mmax + GBM - 1) / GBM, (Nmax + GBN - 1) / GBN, (unsigned)(zmax < 65535 ? zmax : 65535));
+    if (grid.y > 65535u || zmax > (1LL << 30)) {
+        set_error("gemm grid too large");
+        return TPCG_E_INVALID;
+    }
+    gemm_grouped_kernel<T, TA, TB><<<grid, GTHREADS, 0, st>>>(args, count_dev, bmax, (int)zmax);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+
+}  // namespace tpcg

@@ -1,0 +1,29 @@
+// Declarations of the templated device-side operations (one instantiation per compute dtype).
+#pragma once
+
+#include "common.cuh"
+
+namespace tpcg {
+
+template <typename T>
+int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
+               cudaStream_t st);
+template <typename T>
+int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st);
+template <typename T>
+int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev, const tucker_t* y,
+               tucker_t* z, int* err_dev, cudaStream_t st);
+template <typename T>
+int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);
+template <typename T>
+int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st);
+template <typename T>
+int copy_tensor_impl(const tucker_t* src, tucker_t* dst, int n, int cap, cudaStream_t st);
+
+int set_plain(tucker_t* t, int r1, int r2, int r3, cudaStream_t st);
+int set_zero(tucker_t* t, cudaStream_t st);
+
+// TPCG scalar updates (one thread each); layout of the scalar array in solver.cu.
+void launch_scalar(int op, double* s, const double* prm, cudaStream_t st);
+
+}  // namespace tpcg

@@ -1,0 +1,535 @@
+// Tucker operations other than rounding: Kronecker-sum matvec (eq. tt_product) as a banded SpMM on the
+// factors, Tucker sums (Sec. 2.3), scalar products (Sec. 2.3), the low-rank FD application (Alg. 4,
+// App. B) and tensor copies.  Shapes come from the device descriptors.
+#include <math.h>
+
+#include "common.cuh"
+#include "gemm.cuh"
+#include "kernels.cuh"
+
+namespace tpcg {
+
+// --------------------------------------------------------------------------------------------------
+// descriptors
+// --------------------------------------------------------------------------------------------------
+__global__ void set_plain_kernel(TuckerDesc* d, int r1, int r2, int r3, const void* core) {
+    if (threadIdx.x != 0) return;
+    d->nblk = 1;
+    d->rank[0] = r1; d->rank[1] = r2; d->rank[2] = r3;
+    d->blk[0].off[0] = d->blk[0].off[1] = d->blk[0].off[2] = 0;
+    d->blk[0].r[0] = r1; d->blk[0].r[1] = r2; d->blk[0].r[2] = r3;
+    d->blk[0].core = core;
+    d->blk[0].scale = 1.0;
+}
+
+int set_plain(tucker_t* t, int r1, int r2, int r3, cudaStream_t st) {
+    set_plain_kernel<<<1, 32, 0, st>>>(static_cast<TuckerDesc*>(t->desc), r1, r2, r3, t->core);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+
+int set_zero(tucker_t* t, cudaStream_t st) { return set_plain(t, 0, 0, 0, st); }
+
+// --------------------------------------------------------------------------------------------------
+// y = A x  /  y = f - A x  (eq. tt_product): Y_t[:, base_t + j k_t + c] = K_t^j X_t[:, c];
+// bands[((j*3 + t)*(2p+1) + d)*n + i] = K_t^j[i, i + d - p].  The extra "term" j = R copies F_t into the
+// first columns for the residual.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void apply_kernel(const T* __restrict__ bands, int n, int p, int R, const TuckerDesc* __restrict__ xd,
+                             const T* X0, const T* X1, const T* X2, T* Y0, T* Y1, T* Y2, int cap,
+                             const TuckerDesc* __restrict__ fd, const T* F0, const T* F1, const T* F2) {
+    const int t = blockIdx.z, j = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T* X = t == 0 ? X0 : (t == 1 ? X1 : X2);
+    T* Y = t == 0 ? Y0 : (t == 1 ? Y1 : Y2);
+    const int kx = xd->rank[t];
+    const int base = fd ? fd->rank[t] : 0;
+    if (j == R) {   // copy the rhs factor
+        if (base > cap) return;
+        const T* F = t == 0 ? F0 : (t == 1 ? F1 : F2);
+        for (int c = 0; c < base; ++c) Y[i + (long long)c * n] = F[i + (long long)c * n];
+        return;
+    }
+    if (base + (long long)R * kx > cap) return;   // capacity violated: flagged by the descriptor kernel
+    const int bw = 2 * p + 1;
+    T band[11];
+    const T* bj = bands + ((long long)(j * 3 + t) * bw) * n;
+#pragma unroll
+    for (int d = 0; d < 11; ++d) band[d] = (d < bw) ? bj[(long long)d * n + i] : T(0);
+    const int col0 = base + j * kx;
+    for (int c = 0; c < kx; ++c) {
+        const T* xc = X + (long long)c * n;
+        T acc = T(0);
+#pragma unroll
+        for (int d = 0; d < 11; ++d) {
+            if (d >= bw) break;
+            const int ii = i + d - p;
+            if (ii >= 0 && ii < n) acc = fma(band[d], xc[ii], acc);
+        }
+        Y[i + (long long)(col0 + c) * n] = acc;
+    }
+}
+
+// output descriptor of the apply: blocks (f) + (j, b) for every term j and input block b
+__global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const double* __restrict__ w, int R,
+                                  double sign, const TuckerDesc* __restrict__ fdsc, TuckerDesc* yd, int cap,
+                                  int* err) {
+    if (threadIdx.x != 0) return;
+    int nb = 0;
+    int base[3] = {0, 0, 0};
+    if (fdsc) {
+        for (int b = 0; b < fdsc->nblk; ++b) yd->blk[nb++] = fdsc->blk[b];
+        for (int t = 0; t < 3; ++t) base[t] = fdsc->rank[t];
+    }
+    const int kx[3] = {xd->rank[0], xd->rank[1], xd->rank[2]};
+    bool ok = (nb + R * xd->nblk <= TPCG_MAX_BLOCKS);
+    for (int t = 0; t < 3; ++t) ok = ok && (base[t] + (long long)R * kx[t] <= cap);
+    if (!ok) {
+        if (err) *err = 1;
+        yd->nblk = 0;
+        yd->rank[0] = yd->rank[1] = yd->rank[2] = 0;
+        return;
+    }
+    for (int j = 0; j < R; ++j)
+        for (int b = 0; b < xd->nblk; ++b) {
+            BlockDesc B = xd->blk[b];
+            for (int t = 0; t < 3; ++t) B.off[t] += base[t] + j * kx[t];
+            B.scale *= sign * w[j];
+            yd->blk[nb++] = B;
+        }
+    yd->nblk = nb;
+    for (int t = 0; t < 3; ++t) yd->rank[t] = base[t] + R * kx[t];
+}
+
+template <typename T>
+int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st) {
+    const int n = pb->n;
+    dim3 grid((n + 127) / 128, pb->R + (residual ? 1 : 0), 3);
+    const tucker_t* f = &pb->f;
+    apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
+                                          static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                                          static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
+                                          static_cast<T*>(y->U[0]), static_cast<T*>(y->U[1]),
+                                          static_cast<T*>(y->U[2]), y->cap,
+                                          residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
+                                          static_cast<const T*>(f->U[0]), static_cast<const T*>(f->U[1]),
+                                          static_cast<const T*>(f->U[2]));
+    TPCG_CHECK_LAUNCH();
+    apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R,
+                                        residual ? -1.0 : 1.0,
+                                        residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
+                                        static_cast<TuckerDesc*>(y->desc), y->cap, reinterpret_cast<int*>(pb->d_scal + 60));
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t);
+template int apply_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t);
+
+// --------------------------------------------------------------------------------------------------
+// z = a x + b y: concatenated factors, block lists shifted and scaled (Sec. 2.3, sum).
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void concat_kernel(const TuckerDesc* __restrict__ xd, const T* X0, const T* X1, const T* X2,
+                              const TuckerDesc* __restrict__ yd, const T* Y0, const T* Y1, const T* Y2, T* Z0,
+                              T* Z1, T* Z2, int n, int cap) {
+    const int t = blockIdx.z;
+    const T* X = t == 0 ? X0 : (t == 1 ? X1 : X2);
+    const T* Y = t == 0 ? Y0 : (t == 1 ? Y1 : Y2);
+    T* Z = t == 0 ? Z0 : (t == 1 ? Z1 : Z2);
+    const int kx = xd->rank[t], ky = yd->rank[t];
+    if (kx + ky > cap) return;
+    const long long tx = (long long)n * kx, ty = (long long)n * ky;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tx + ty;
+         e += (long long)gridDim.x * blockDim.x)
+        Z[e] = e < tx ? X[e] : Y[e - tx];
+}
+
+__global__ void axpby_desc_kernel(const TuckerDesc* __restrict__ xd, double a, const double* a_dev,
+                                  const TuckerDesc* __restrict__ yd, double b, const double* b_dev, TuckerDesc* zd,
+                                  int cap, int* err) {
+    if (threadIdx.x != 0) return;
+    const double av = a_dev ? *a_dev : a;
+    const double bv = b_dev ? *b_dev : b;
+    bool ok = xd->nblk + yd->nblk <= TPCG_MAX_BLOCKS;
+    for (int t = 0; t < 3; ++t) ok = ok && (xd->rank[t] + yd->rank[t] <= cap);
+    if (!ok) {
+        if (err) *err = 1;
+        zd->nblk = 0;
+        zd->rank[0] = zd->rank[1] = zd->rank[2] = 0;
+        return;
+    }
+    int nb = 0;
+    for (int i = 0; i < xd->nblk; ++i) {
+        BlockDesc B = xd->blk[i];
+        B.scale *= av;
+        zd->blk[nb++] = B;
+    }
+    for (int i = 0; i < yd->nblk; ++i) {
+        BlockDesc B = yd->blk[i];
+        for (int t = 0; t < 3; ++t) B.off[t] += xd->rank[t];
+        B.scale *= bv;
+        zd->blk[nb++] = B;
+    }
+    zd->nblk = nb;
+    for (int t = 0; t < 3; ++t) zd->rank[t] = xd->rank[t] + yd->rank[t];
+}
+
+template <typename T>
+int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev, const tucker_t* y,
+               tucker_t* z, int* err_dev, cudaStream_t st) {
+    const int n = z->n;
+    dim3 grid(64, 1, 3);
+    concat_kernel<T><<<grid, 256, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                                           static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
+                                           static_cast<const TuckerDesc*>(y->desc), static_cast<const T*>(y->U[0]),
+                                           static_cast<const T*>(y->U[1]), static_cast<const T*>(y->U[2]),
+                                           static_cast<T*>(z->U[0]), static_cast<T*>(z->U[1]),
+                                           static_cast<T*>(z->U[2]), n, z->cap);
+    TPCG_CHECK_LAUNCH();
+    axpby_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), a, a_dev,
+                                        static_cast<const TuckerDesc*>(y->desc), b, b_dev,
+                                        static_cast<TuckerDesc*>(z->desc), z->cap, err_dev);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int axpby_impl<double>(double, const double*, const tucker_t*, double, const double*, const tucker_t*,
+                                tucker_t*, int*, cudaStream_t);
+template int axpby_impl<float>(double, const double*, const tucker_t*, double, const double*, const tucker_t*,
+                               tucker_t*, int*, cudaStream_t);
+
+// --------------------------------------------------------------------------------------------------
+// <x, y> = vec(G_x)^T vec(G_y x_1 W_1 x_2 W_2 x_3 W_3), W_t = X_t^T Y_t (Sec. 2.3), both plain.
+// ctx scratch: dotw (3 W_t, rank_cap^2 each, as T), dotT (two rank_cap^3 buffers).
+// gargs slots used: [0..2] W_t, [3] mode 1, [4] mode 2, [5] mode 3.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void plan_dot_kernel(const TuckerDesc* __restrict__ xd, const T* X0, const T* X1, const T* X2,
+                                const TuckerDesc* __restrict__ yd, const T* Y0, const T* Y1, const T* Y2, int n,
+                                int rc, T* Wb, T* Ta, T* Tb, GemmArgs* ga, int* counts) {
+    if (threadIdx.x != 0) return;
+    const T* X[3] = {X0, X1, X2};
+    const T* Y[3] = {Y0, Y1, Y2};
+    int r[3], s[3];
+    bool bad = xd->nblk != 1 || yd->nblk != 1;
+    for (int t = 0; t < 3; ++t) {
+        r[t] = xd->rank[t];
+        s[t] = yd->rank[t];
+        bad = bad || r[t] > rc || s[t] > rc;
+    }
+    counts[1] = bad ? 1 : 0;
+    if (bad)
+        for (int t = 0; t < 3; ++t) r[t] = s[t] = 0;
+    const long long rc2 = (long long)rc * rc;
+    for (int t = 0; t < 3; ++t) {
+        GemmArgs a{};
+        a.M = r[t]; a.N = s[t]; a.K = n; a.nbatch = 1; a.acc = 0; a.alpha = 1.0; a.beta = 0.0;
+        a.A = X[t]; a.lda = n; a.B = Y[t]; a.ldb = n; a.C = Wb + t * rc2; a.ldc = r[t] > 0 ? r[t] : 1;
+        ga[t] = a;
+    }
+    const void* Gy = yd->blk[0].core;
+    // mode 1: Ta (r1 x s2 s3) = W_1 (r1 x s1) G_y(1)
+    GemmArgs m1{};
+    m1.M = r[0]; m1.N = s[1] * s[2]; m1.K = s[0]; m1.nbatch = 1; m1.alpha = yd->blk[0].scale; m1.beta = 0.0;
+    m1.A = Wb; m1.lda = r[0] > 0 ? r[0] : 1; m1.B = Gy; m1.ldb = s[0] > 0 ? s[0] : 1; m1.C = Ta; m1.ldc = m1.lda;
+    ga[3] = m1;
+    // mode 2 per slice i3: Tb[:, :, i3] (r1 x r2) = Ta[:, :, i3] (r1 x s2) W_2^T
+    GemmArgs m2{};
+    m2.M = r[0]; m2.N = r[1]; m2.K = s[1]; m2.nbatch = s[2]; m2.alpha = 1.0; m2.beta = 0.0;
+    m2.A = Ta; m2.lda = m1.lda; m2.sA = (long long)r[0] * s[1];
+    m2.B = Wb + rc2; m2.ldb = r[1] > 0 ? r[1] : 1;
+    m2.C = Tb; m2.ldc = m1.lda; m2.sC = (long long)r[0] * r[1];
+    ga[4] = m2;
+    // mode 3: Ta (r1 r2 x r3) = Tb (r1 r2 x s3) W_3^T
+    GemmArgs m3{};
+    m3.M = r[0] * r[1]; m3.N = r[2]; m3.K = s[2]; m3.nbatch = 1; m3.alpha = 1.0; m3.beta = 0.0;
+    m3.A = Tb; m3.lda = m3.M > 0 ? m3.M : 1; m3.B = Wb + 2 * rc2; m3.ldb = r[2] > 0 ? r[2] : 1;
+    m3.C = Ta; m3.ldc = m3.lda;
+    ga[5] = m3;
+    counts[0] = 3;
+}
+
+template <typename T>
+__global__ void dot_finish_kernel(const TuckerDesc* __restrict__ xd, const T* Ta, double* out, const int* bad) {
+    __shared__ double red[32];
+    if (*bad) {
+        if (threadIdx.x == 0) *out = nan("");
+        return;
+    }
+    const long long tot = (long long)xd->rank[0] * xd->rank[1] * xd->rank[2];
+    const T* Gx = static_cast<const T*>(xd->blk[0].core);
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < tot; e += blockDim.x) s += (double)Gx[e] * (double)Ta[e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        *out = v * xd->blk[0].scale;
+    }
+}
+
+template <typename T>
+int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st) {
+    const int n = c->n, rc = c->rank_cap;
+    GemmArgs* ga = c->gargs + 2 * TPCG_MAX_BLOCKS + 8;   // disjoint from the rounding slots
+    int* counts = reinterpret_cast<int*>(c->scal + 210);
+    T* Wb = reinterpret_cast<T*>(c->dotw);
+    T* Ta = static_cast<T*>(c->dotT);
+    T* Tb = Ta + (long long)rc * rc * rc;
+    plan_dot_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                                         static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
+                                         static_cast<const TuckerDesc*>(y->desc), static_cast<const T*>(y->U[0]),
+                                         static_cast<const T*>(y->U[1]), static_cast<const T*>(y->U[2]), n, rc, Wb,
+                                         Ta, Tb, ga, counts);
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, rc, rc, st)));
+    TPCG_TRY((launch_gemm<T, false, false>(ga + 3, nullptr, 1, 1, rc, rc * rc, st)));
+    TPCG_TRY((launch_gemm<T, false, true>(ga + 4, nullptr, 1, rc, rc, rc, st)));
+    TPCG_TRY((launch_gemm<T, false, true>(ga + 5, nullptr, 1, 1, rc * rc, rc, st)));
+    dot_finish_kernel<T><<<1, 1024, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), Ta, out_dev, counts + 1);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int dot_impl<double>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
+template int dot_impl<float>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
+
+// --------------------------------------------------------------------------------------------------
+// FD preconditioner, Alg. 4 with U~ = [W U_dft diag(1/mu) | V2 U2] (App. B):
+//   u_t = U_dft^T (W^T S_t),  z2_t = (V2U2)^T S_t
+//   for j < RP:  E_t[:, j r + c] = D_(t,j)[:n1] u_t[:, c] / mu^2,  E2_t = D_(t,j)[n1:] z2_t
+//   V_t = W (U_dft E_t) + V2U2 E2_t;  core superdiag(omega / lambda_min) (x) G_s.
+// ctx->fd[t][0..3] scratch buffers (n x max_cols each): T, u|z2, E|E2, A.
+// gargs slots (offset 2*MAXB + 16): [0..2] u_t, [3..5] z2_t, [6..8] A_t, [9..11] V_t += V2U2 E2_t.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void fd_gather_kernel(const TuckerDesc* __restrict__ sd, const T* S0, const T* S1, const T* S2,
+                                 const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ val,
+                                 int n, int n1, T* B0, T* B1, T* B2) {
+    const int t = blockIdx.z;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (l >= n1 || c >= sd->rank[t]) return;
+    const T* S = t == 0 ? S0 : (t == 1 ? S1 : S2);
+    T* B = t == 0 ? B0 : (t == 1 ? B1 : B2);
+    T acc = T(0);
+    for (int e = rp[l]; e < rp[l + 1]; ++e) acc = fma(val[e], S[ci[e] + (long long)c * n], acc);
+    B[l + (long long)c * n1] = acc;
+}
+
+template <typename T>
+__global__ void plan_fd_kernel(const TuckerDesc* __restrict__ sd, const T* S0, const T* S1, const T* S2, int n,
+                               int n1, int n2, int RP, const T* dst, const T* v2u2, T* Tb0, T* Tb1, T* Tb2, T* Ub0,
+                               T* Ub1, T* Ub2, T* Eb0, T* Eb1, T* Eb2, T* Ab0, T* Ab1, T* Ab2, T* V0, T* V1, T* V2,
+                               GemmArgs* ga, int* counts, int vcap, int* err) {
+    if (threadIdx.x != 0) return;
+    const T* S[3] = {S0, S1, S2};
+    T* Tb[3] = {Tb0, Tb1, Tb2};
+    T* Ub[3] = {Ub0, Ub1, Ub2};
+    T* Eb[3] = {Eb0, Eb1, Eb2};
+    T* Ab[3] = {Ab0, Ab1, Ab2};
+    T* V[3] = {V0, V1, V2};
+    for (int t = 0; t < 3; ++t) {
+        int r = sd->rank[t];
+        int cols = RP * r;
+        if (cols > vcap) {   // output capacity exceeded: flag and turn every product of this mode off
+            if (err) *err = 1;
+            r = 0;
+            cols = 0;
+        }
+        // u_t (n1 x r) = dst^T T_t
+        GemmArgs a{};
+        a.M = n1; a.N = r; a.K = n1; a.nbatch = 1; a.alpha = 1.0;
+        a.A = dst; a.lda = n1; a.B = Tb[t]; a.ldb = n1; a.C = Ub[t]; a.ldc = n1;
+        ga[t] = a;
+        // z2_t (n2 x r) = v2u2^T S_t, stored after u_t
+        GemmArgs b{};
+        b.M = n2; b.N = r; b.K = n; b.nbatch = 1; b.alpha = 1.0;
+        b.A = v2u2; b.lda = n; b.B = S[t]; b.ldb = n; b.C = Ub[t] + (long long)n1 * r; b.ldc = n2 > 0 ? n2 : 1;
+        ga[3 + t] = b;
+        // A_t (n1 x RP r) = dst E_t
+        GemmArgs c{};
+        c.M = n1; c.N = cols; c.K = n1; c.nbatch = 1; c.alpha = 1.0;
+        c.A = dst; c.lda = n1; c.B = Eb[t]; c.ldb = n1; c.C = Ab[t]; c.ldc = n1;
+        ga[6 + t] = c;
+        // V_t += v2u2 E2_t   (E2_t stored after E_t)
+        GemmArgs d{};
+        d.M = n; d.N = cols; d.K = n2; d.nbatch = 1; d.alpha = 1.0; d.beta = 1.0;
+        d.A = v2u2; d.lda = n; d.B = Eb[t] + (long long)n1 * cols; d.ldb = n2 > 0 ? n2 : 1; d.C = V[t]; d.ldc = n;
+        if (n2 == 0) d.M = 0;
+        ga[9 + t] = d;
+    }
+    counts[0] = 3;
+}
+
+template <typename T>
+__global__ void fd_scale_kernel(const TuckerDesc* __restrict__ sd, const T* U0, const T* U1, const T* U2,
+                                const T* __restrict__ lam, const T* __restrict__ mu, const double* __restrict__ alpha,
+                                double lmin, int n1, int n2, int RP, T* E0, T* E1, T* E2, int vcap) {
+    const int t = blockIdx.z;
+    const int r = sd->rank[t];
+    const int n = n1 + n2;
+    const int col = blockIdx.y;          // j * r + c
+    if (col >= RP * r || RP * r > vcap) return;
+    const int j = col / r, c = col % r;
+    const T* U = t == 0 ? U0 : (t == 1 ? U1 : U2);
+    T* E = t == 0 ? E0 : (t == 1 ? E1 : E2);
+    const long long cols = (long long)RP * r;
+    const double aj = alpha[j] / lmin;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const T dl = (T)exp(-aj * (double)lam[l]);
+        if (l < n1) {
+            const T m = mu[l];
+            E[l + (long long)col * n1] = dl * U[l + (long long)c * n1] / (m * m);
+        } else {
+            const int q = l - n1;
+            E[(long long)n1 * cols + q + (long long)col * n2] = dl * U[(long long)n1 * r + q + (long long)c * n2];
+        }
+    }
+}
+
+template <typename T>
+__global__ void fd_scatter_kernel(const TuckerDesc* __restrict__ sd, const T* A0, const T* A1, const T* A2,
+                                  const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ val,
+                                  int n, int n1, int RP, T* V0, T* V1, T* V2, int vcap) {
+    const int t = blockIdx.z;
+    const int r = sd->rank[t];
+    const int col = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= RP * r || RP * r > vcap || i >= n) return;
+    const T* A = t == 0 ? A0 : (t == 1 ? A1 : A2);
+    T* V = t == 0 ? V0 : (t == 1 ? V1 : V2);
+    T acc = T(0);
+    for (int e = rp[i]; e < rp[i + 1]; ++e) acc = fma(val[e], A[ci[e] + (long long)col * n1], acc);
+    V[i + (long long)col * n] = acc;
+}
+
+__global__ void fd_desc_kernel(const TuckerDesc* __restrict__ sd, const double* __restrict__ omega, double lmin,
+                               int RP, TuckerDesc* vd, int vcap, int* err) {
+    if (threadIdx.x != 0) return;
+    bool ok = RP * sd->nblk <= TPCG_MAX_BLOCKS;
+    for (int t = 0; t < 3; ++t) ok = ok && (RP * sd->rank[t] <= vcap);
+    if (!ok) {
+        if (err) *err = 1;
+        vd->nblk = 0;
+        vd->rank[0] = vd->rank[1] = vd->rank[2] = 0;
+        return;
+    }
+    int nb = 0;
+    for (int j = 0; j < RP; ++j)
+        for (int b = 0; b < sd->nblk; ++b) {
+            BlockDesc B = sd->blk[b];
+            for (int t = 0; t < 3; ++t) B.off[t] += j * sd->rank[t];
+            B.scale *= omega[j] / lmin;
+            vd->blk[nb++] = B;
+        }
+    vd->nblk = nb;
+    for (int t = 0; t < 3; ++t) vd->rank[t] = RP * sd->rank[t];
+}
+
+template <typename T>
+int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st) {
+    const int n = pb->n, n1 = pb->n1, n2 = pb->n2, RP = pb->RP;
+    const int rc = c->rank_cap;
+    GemmArgs* ga = c->gargs + 2 * TPCG_MAX_BLOCKS + 16;
+    int* counts = reinterpret_cast<int*>(c->scal + 220);
+    int* err = reinterpret_cast<int*>(c->scal + 230);
+    T* buf[3][4];
+    for (int t = 0; t < 3; ++t)
+        for (int q = 0; q < 4; ++q) buf[t][q] = static_cast<T*>(c->fd[t][q]);
+    const TuckerDesc* sd = static_cast<const TuckerDesc*>(s->desc);
+    dim3 g1((n1 + 127) / 128, rc, 3);
+    fd_gather_kernel<T><<<g1, 128, 0, st>>>(sd, static_cast<const T*>(s->U[0]), static_cast<const T*>(s->U[1]),
+                                            static_cast<const T*>(s->U[2]), pb->d_wtrow, pb->d_wtcol,
+                                            static_cast<const T*>(pb->d_wtval), n, n1, buf[0][0], buf[1][0],
+                                            buf[2][0]);
+    TPCG_CHECK_LAUNCH();
+    plan_fd_kernel<T><<<1, 32, 0, st>>>(sd, static_cast<const T*>(s->U[0]), static_cast<const T*>(s->U[1]),
+                                        static_cast<const T*>(s->U[2]), n, n1, n2, RP,
+                                        static_cast<const T*>(pb->d_dst), static_cast<const T*>(pb->d_v2u2),
+                                        buf[0][0], buf[1][0], buf[2][0], buf[0][1], buf[1][1], buf[2][1], buf[0][2],
+                                        buf[1][2], buf[2][2], buf[0][3], buf[1][3], buf[2][3],
+                                        static_cast<T*>(v->U[0]), static_cast<T*>(v->U[1]),
+                                        static_cast<T*>(v->U[2]), ga, counts, v->cap, err);
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, n1, rc, st)));
+    if (n2 > 0) TPCG_TRY((launch_gemm<T, true, false>(ga + 3, counts, 3, 1, n2, rc, st)));
+    dim3 g2(2, RP * rc, 3);
+    fd_scale_kernel<T><<<g2, 256, 0, st>>>(sd, buf[0][1], buf[1][1], buf[2][1], static_cast<const T*>(pb->d_lam),
+                                           static_cast<const T*>(pb->d_mu), pb->d_alpha, pb->lambda_min, n1, n2, RP,
+                                           buf[0][2], buf[1][2], buf[2][2], v->cap);
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY((launch_gemm<T, false, false>(ga + 6, counts, 3, 1, n1, RP * rc, st)));
+    dim3 g3((n + 127) / 128, RP * rc, 3);
+    fd_scatter_kernel<T><<<g3, 128, 0, st>>>(sd, buf[0][3], buf[1][3], buf[2][3], pb->d_wrow, pb->d_wcol,
+                                             static_cast<const T*>(pb->d_wval), n, n1, RP, static_cast<T*>(v->U[0]),
+                                             static_cast<T*>(v->U[1]), static_cast<T*>(v->U[2]), v->cap);
+    TPCG_CHECK_LAUNCH();
+    if (n2 > 0) TPCG_TRY((launch_gemm<T, false, false>(ga + 9, counts, 3, 1, n, RP * rc, st)));
+    fd_desc_kernel<<<1, 32, 0, st>>>(sd, pb->d_omega, pb->lambda_min, RP, static_cast<TuckerDesc*>(v->desc), v->cap,
+                                     err);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int fd_impl<double>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t);
+template int fd_impl<float>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t);
+
+// --------------------------------------------------------------------------------------------------
+// copies
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void copy_factors_kernel(const TuckerDesc* __restrict__ sd, const T* S0, const T* S1, const T* S2, T* D0,
+                                    T* D1, T* D2, int n, int cap) {
+    const int t = blockIdx.z;
+    const int k = sd->rank[t];
+    if (k > cap) return;
+    const T* S = t == 0 ? S0 : (t == 1 ? S1 : S2);
+    T* D = t == 0 ? D0 : (t == 1 ? D1 : D2);
+    const long long tot = (long long)n * k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+        D[e] = S[e];
+}
+
+// plain source: copy its core into dst's core as well and point the descriptor at it
+template <typename T>
+__global__ void copy_core_kernel(const TuckerDesc* __restrict__ sd, TuckerDesc* dd, T* dcore, long long ccap) {
+    __shared__ int plain;
+    if (threadIdx.x == 0) plain = (sd->nblk == 1);
+    __syncthreads();
+    if (plain) {
+        const BlockDesc& B = sd->blk[0];
+        const long long tot = (long long)B.r[0] * B.r[1] * B.r[2];
+        const T* src = static_cast<const T*>(B.core);
+        if (tot <= ccap)
+            for (long long e = threadIdx.x; e < tot; e += blockDim.x) dcore[e] = src[e];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nb = sd->nblk;
+        dd->nblk = nb;
+        for (int t = 0; t < 3; ++t) dd->rank[t] = sd->rank[t];
+        for (int b = 0; b < nb; ++b) dd->blk[b] = sd->blk[b];
+        if (plain) dd->blk[0].core = dcore;
+    }
+}
+
+template <typename T>
+int copy_tensor_impl(const tucker_t* src, tucker_t* dst, int n, int cap, cudaStream_t st) {
+    dim3 grid(64, 1, 3);
+    copy_factors_kernel<T><<<grid, 256, 0, st>>>(static_cast<const TuckerDesc*>(src->desc),
+                                                 static_cast<const T*>(src->U[0]), static_cast<const T*>(src->U[1]),
+                                                 static_cast<const T*>(src->U[2]), static_cast<T*>(dst->U[0]),
+                                                 static_cast<T*>(dst->U[1]), static_cast<T*>(dst->U[2]), n, cap);
+    TPCG_CHECK_LAUNCH();
+    copy_core_kernel<T><<<1, 1024, 0, st>>>(static_cast<const TuckerDesc*>(src->desc),
+                                            static_cast<TuckerDesc*>(dst->desc), static_cast<T*>(dst->core),
+                                            dst->core_cap);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int copy_tensor_impl<double>(const tucker_t*, tucker_t*, int, int, cudaStream_t);
+template int copy_tensor_impl<float>(const tucker_t*, tucker_t*, int, int, cudaStream_t);
+
+}  // namespace tpcg

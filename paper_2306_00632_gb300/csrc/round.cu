@@ -1,0 +1,594 @@
+// Relative-tolerance truncation of a Tucker tensor (Alg. 1 with ST-HOSVD), device-driven.
+//
+//   step 1  QR of each factor Y_t (n x k_t).  When k_t >= n any orthonormal Q_t spanning R^n serves, so
+//           Q_t = I and R_t = Y_t (no work); otherwise a Householder QR in one CTA per mode.
+//   step 2  Z = sum_b scale_b G_b x_1 R_1^(b) x_2 R_2^(b) x_3 R_3^(b) over the core blocks b
+//           (block-diagonal core): per block the middle mode on the small core, then mode 1, writing
+//           the block's slab of a stacked matrix W; one fused GEMM over all blocks contracts mode 3.
+//   step 3  ST-HOSVD of Z, modes 1, 2, 3 in order: Gram of the unfolding (split-K GEMM + ordered
+//           reduction), Jacobi eigensolver, keep the smallest s_m whose discarded eigenvalues sum to
+//           <= eps^2 ||Z||^2 / 3 (clipped by the rank cap), project Z x_m S_m^T.
+//   step 4  new factors Q_t S_t, new core, descriptor of a plain tensor.
+//
+// Every shape is read from device memory (descriptor, RoundPlan, GemmArgs), so the host enqueues a fixed
+// sequence of launches without synchronising.
+#include <math.h>
+
+#include "common.cuh"
+#include "gemm.cuh"
+#include "kernels.cuh"
+
+namespace tpcg {
+
+// --------------------------------------------------------------------------------------------------
+// Planner: descriptor -> plan and the GEMM arguments of step 2.
+// gargs layout: [0, MAXB) middle-mode products, [MAXB, 2 MAXB) mode-1 products, [2 MAXB] fused mode 3.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* plan, GemmArgs* ga, int n,
+                                  int cap, double eps_host, const double* eps_dev, void* Rq0, void* Rq1,
+                                  void* Rq2, const void* U0, const void* U1, const void* U2, T* T1, T* Wm,
+                                  int* counts, long long t1cap) {
+    if (threadIdx.x != 0) return;
+    RoundPlan p;
+    p.n = n;
+    p.nblk = d->nblk;
+    void* Rq[3] = {Rq0, Rq1, Rq2};
+    const void* U[3] = {U0, U1, U2};
+    for (int t = 0; t < 3; ++t) {
+        p.k[t] = d->rank[t];
+        p.useQ[t] = (p.k[t] < n) ? 1 : 0;
+        p.kp[t] = p.k[t] < n ? p.k[t] : n;
+        p.Rp[t] = p.useQ[t] ? (const void*)Rq[t] : U[t];
+        p.ldR[t] = n;
+        p.s[t] = 0;
+        p.zdim[t] = p.kp[t];
+    }
+    p.cap = cap;
+    p.eps = eps_dev ? *eps_dev : eps_host;
+    p.norm2 = 0.0;
+    p.discarded = 0.0;
+    p.budget = 0.0;
+    p.status = 0;
+    p.kz3 = p.k[2];
+    p.nsplit = 0;
+    const int kp1 = p.kp[0], kp2 = p.kp[1];
+    long long t1off = 0;
+    for (int b = 0; b < p.nblk; ++b) {
+        const BlockDesc& B = d->blk[b];
+        const int r1 = B.r[0], r2 = B.r[1], r3 = B.r[2];
+        // middle mode on the core: U_b[:, :, j3] (r1 x kp2) = G_b[:, :, j3] (r1 x r2) R_2b^T
+        GemmArgs a{};
+        a.M = r1; a.N = kp2; a.K = r2; a.nbatch = r3; a.acc = 0;
+        a.A = B.core; a.lda = r1; a.sA = (long long)r1 * r2;
+        a.B = static_cast<const T*>(p.Rp[1]) + (long long)B.off[1] * p.ldR[1]; a.ldb = p.ldR[1]; a.sB = 0;
+        a.C = T1 + t1off; a.ldc = r1; a.sC = (long long)r1 * kp2;
+        a.alpha = 1.0; a.beta = 0.0;
+        if (r1 == 0 || r2 == 0 || r3 == 0) { a.M = 0; a.nbatch = 0; }
+        ga[b] = a;
+        // mode 1: V_b (kp1 x kp2 r3) = R_1b (kp1 x r1) U_b(1) (r1 x kp2 r3), scaled by the block scale
+        GemmArgs c{};
+        c.M = kp1; c.N = kp2 * r3; c.K = r1; c.nbatch = 1; c.acc = 0;
+        c.A = static_cast<const T*>(p.Rp[0]) + (long long)B.off[0] * p.ldR[0]; c.lda = p.ldR[0]; c.sA = 0;
+        c.B = T1 + t1off; c.ldb = r1; c.sB = 0;
+        c.C = Wm + (long long)B.off[2] * kp1 * kp2; c.ldc = kp1; c.sC = 0;
+        c.alpha = B.scale; c.beta = 0.0;
+        if (r1 == 0 || r2 == 0 || r3 == 0) { c.M = 0; }
+        ga[TPCG_MAX_BLOCKS + b] = c;
+        t1off += (long long)r1 * kp2 * r3;
+    }
+    // fused mode 3: Z (kp1 kp2 x kp3) = W (kp1 kp2 x k3) R_3^T
+    GemmArgs z{};
+    z.M = kp1 * kp2; z.N = p.kp[2]; z.K = p.k[2]; z.nbatch = 1; z.acc = 0;
+    z.A = Wm; z.lda = (long long)kp1 * kp2; z.sA = 0;
+    z.B = p.Rp[2]; z.ldb = p.ldR[2]; z.sB = 0;
+    z.C = nullptr;  // set by the host launcher through counts[] slot (Z buffer is fixed)
+    z.ldc = (long long)kp1 * kp2; z.sC = 0;
+    z.alpha = 1.0; z.beta = 0.0;
+    ga[2 * TPCG_MAX_BLOCKS] = z;
+    counts[0] = p.nblk;
+    if (t1off > t1cap) {   // workspace too small for these blocks: produce nothing, flag the plan
+        p.status = 1;
+        counts[0] = 0;
+        ga[2 * TPCG_MAX_BLOCKS].M = 0;
+        for (int t = 0; t < 3; ++t) p.zdim[t] = 0;
+    }
+    *plan = p;
+}
+
+__global__ void set_c_kernel(GemmArgs* ga, void* C) {
+    if (threadIdx.x == 0) ga->C = C;
+}
+
+// --------------------------------------------------------------------------------------------------
+// Householder QR of Y_t (n x k, k < n), one CTA per mode:  Y_t = Q_t R_t, Q_t n x k, R_t k x k.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = (lane < nw) ? red[lane] : T(0);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[32] = v;
+    }
+    __syncthreads();
+    T r = red[32];
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) qr_kernel(const RoundPlan* __restrict__ plan, const T* Y0, const T* Y1,
+                                                  const T* Y2, T* W0, T* W1, T* W2, T* R0, T* R1, T* R2, T* Q0,
+                                                  T* Q1, T* Q2) {
+    const int t = blockIdx.x;
+    const RoundPlan& p = *plan;
+    if (!p.useQ[t]) return;
+    const int n = p.n, k = p.k[t];
+    const T* Y = t == 0 ? Y0 : (t == 1 ? Y1 : Y2);
+    T* A = t == 0 ? W0 : (t == 1 ? W1 : W2);
+    T* R = t == 0 ? R0 : (t == 1 ? R1 : R2);
+    T* Q = t == 0 ? Q0 : (t == 1 ? Q1 : Q2);
+    extern __shared__ unsigned char smem_raw[];
+    T* tau = reinterpret_cast<T*>(smem_raw);      // k
+    T* red = tau + n;                              // 33
+    __shared__ T s_beta;
+    for (long long e = threadIdx.x; e < (long long)n * k; e += blockDim.x) A[e] = Y[e];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < k; ++j) {
+        // Householder vector of A[j:n, j] (LAPACK larfg convention: v[0] = 1, R[j,j] = beta)
+        T part = T(0);
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) part += A[i + (long long)j * n] * A[i + (long long)j * n];
+        T sig = block_sum(part, red);
+        const T alpha0 = A[j + (long long)j * n];
+        T beta, tj, scal;
+        if (sig == T(0)) {
+            tj = T(0); beta = alpha0; scal = T(0);
+        } else {
+            T nrm = sqrt(alpha0 * alpha0 + sig);
+            beta = alpha0 >= T(0) ? -nrm : nrm;
+            tj = (beta - alpha0) / beta;
+            scal = T(1) / (alpha0 - beta);
+        }
+        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (long long)j * n] *= scal;
+        if (threadIdx.x == 0) { tau[j] = tj; s_beta = beta; }
+        __syncthreads();
+        // apply H_j to the trailing columns, one warp per column
+        if (tj != T(0)) {
+            for (int c = j + 1 + wid; c < k; c += nw) {
+                T* col = A + (long long)c * n;
+                const T* v = A + (long long)j * n;
+                T w = T(0);
+                for (int i = j + lane; i < n; i += 32) w += (i == j ? T(1) : v[i]) * col[i];
+                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                w *= tj;
+                for (int i = j + lane; i < n; i += 32) col[i] -= w * (i == j ? T(1) : v[i]);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) A[j + (long long)j * n] = s_beta;
+        __syncthreads();
+    }
+    // R (k x k, ld n): upper triangle of A
+    for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
+        int i = (int)(e % k), c = (int)(e / k);
+        R[i + (long long)c * n] = (i <= c) ? A[i + (long long)c * n] : T(0);
+    }
+    // Q = H_0 H_1 ... H_{k-1} [I; 0], accumulated backwards
+    for (long long e = threadIdx.x; e < (long long)n * k; e += blockDim.x) {
+        int i = (int)(e % n), c = (int)(e / n);
+        Q[e] = (i == c) ? T(1) : T(0);
+    }
+    __syncthreads();
+    for (int j = k - 1; j >= 0; --j) {
+        const T tj = tau[j];
+        if (tj != T(0)) {
+            for (int c = j + wid; c < k; c += nw) {
+                T* col = Q + (long long)c * n;
+                const T* v = A + (long long)j * n;
+                T w = T(0);
+                for (int i = j + lane; i < n; i += 32) w += (i == j ? T(1) : v[i]) * col[i];
+                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                w *= tj;
+                for (int i = j + lane; i < n; i += 32) col[i] -= w * (i == j ? T(1) : v[i]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------------------------------
+// Gram of the mode-m unfolding of the working tensor (dims in plan.zdim): split into groups whose
+// partial Grams are summed in a fixed order (deterministic).
+//   m = 0: G = Z_(1) Z_(1)^T        (NT, K = d2 d3 split)
+//   m = 1: G = sum_i3 Z_i3^T Z_i3   (TN, slices i3 grouped)
+//   m = 2: G = Zmat^T Zmat          (TN, K = d1 d2 split)
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* Part, int m, int nsplit_max,
+                                 int* counts) {
+    if (threadIdx.x != 0) return;
+    RoundPlan& p = *plan;
+    const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
+    const int M = p.zdim[m];
+    int total = (m == 0) ? d2 * d3 : (m == 1 ? d3 : d1 * d2);
+    int ns = total < nsplit_max ? total : nsplit_max;
+    if (ns < 1) ns = 1;
+    if (M == 0 || total == 0) ns = 0;
+    const int chunk = ns ? (total + ns - 1) / ns : 0;
+    int used = 0;
+    for (int g = 0; g < ns; ++g) {
+        const int lo = g * chunk;
+        int hi = lo + chunk;
+        if (hi > total) hi = total;
+        if (lo >= hi) break;
+        GemmArgs a{};
+        a.M = M; a.N = M; a.alpha = 1.0; a.beta = 0.0;
+        a.C = Part + (long long)used * M * M; a.ldc = M; a.sC = 0;
+        if (m == 0) {
+            a.K = hi - lo; a.nbatch = 1; a.acc = 0;
+            a.A = Zc + (long long)lo * d1; a.lda = d1; a.sA = 0;
+            a.B = Zc + (long long)lo * d1; a.ldb = d1; a.sB = 0;
+        } else if (m == 1) {
+            a.K = d1; a.nbatch = hi - lo; a.acc = 1;
+            a.A = Zc + (long long)lo * d1 * d2; a.lda = d1; a.sA = (long long)d1 * d2;
+            a.B = Zc + (long long)lo * d1 * d2; a.ldb = d1; a.sB = (long long)d1 * d2;
+        } else {
+            a.K = hi - lo; a.nbatch = 1; a.acc = 0;
+            a.A = Zc + lo; a.lda = (long long)d1 * d2; a.sA = 0;
+            a.B = Zc + lo; a.ldb = (long long)d1 * d2; a.sB = 0;
+        }
+        ga[used++] = a;
+    }
+    p.nsplit = used;
+    p.gm = m;
+    p.gM = M;
+    counts[0] = used;
+    counts[1] = M;
+    counts[2] = M;
+}
+
+inline size_t eig_smem_bytes(int n, size_t elt) {
+    const size_t L = (size_t)n + 4;   // >= padded size + 2
+    return L * sizeof(int) * 2 + L * elt + 64 * sizeof(double) + L * sizeof(int) + L * sizeof(double) + 64;
+}
+
+// --------------------------------------------------------------------------------------------------
+// Symmetric eigensolver (cyclic Jacobi, round-robin parallel ordering) + truncation rule + plan of the
+// projection.  One CTA.  G (M x M, ld M) is overwritten; eigenvectors sorted by decreasing eigenvalue go
+// to S (ld n).  Tail energies use the eigenvalues clamped at zero.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024) eig_select_kernel(RoundPlan* plan, GemmArgs* ga, T* G, T* V, T* S,
+                                                          double* evals, const T* Zc, T* Znext, int m,
+                                                          int max_sweeps, int* counts) {
+    RoundPlan& p = *plan;
+    const int M = p.gM;
+    const int n = p.n;
+    extern __shared__ unsigned char smem_raw[];
+    int* top = reinterpret_cast<int*>(smem_raw);
+    const int Mp = (M + 1) & ~1;              // padded to even for the round-robin schedule
+    int* bot = top + (Mp / 2 + 1);
+    T* cs = reinterpret_cast<T*>(bot + (Mp / 2 + 1));   // 2 * Mp/2
+    double* red = reinterpret_cast<double*>(cs + Mp + 2);   // 64 doubles
+    int* order = reinterpret_cast<int*>(red + 64);         // M
+    double* lam = reinterpret_cast<double*>(order + Mp + 2);    // M (sorted)
+    __shared__ int s_done;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // V = I
+    for (long long e = tid; e < (long long)M * M; e += nt) V[e] = ((e % M) == (e / M)) ? T(1) : T(0);
+    if (m == 0) {
+        // ||Z||^2 = trace of the mode-1 Gram
+        double tr = 0.0;
+        for (int i = tid; i < M; i += nt) tr += (double)G[i + (long long)i * M];
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
+        if ((tid & 31) == 0) red[tid >> 5] = tr;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (nt >> 5); ++w) s += red[w];
+            p.norm2 = s;
+            p.budget = p.eps * p.eps * s / 3.0;
+        }
+        __syncthreads();
+    }
+    const int half = Mp / 2;
+    if (tid < half) { top[tid] = 2 * tid; bot[tid] = 2 * tid + 1; }
+    __syncthreads();
+    // stop when ||offdiag||_F <= 8 M eps_mach ||diag||_F (the rounding floor of the rotations)
+    const double tol = 8.0 * (M > 1 ? M : 1) * ((sizeof(T) == 8) ? 1.1e-16 : 6.0e-8);
+    for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
+        // convergence test: off-diagonal vs diagonal Frobenius norms
+        double off = 0.0, dia = 0.0;
+        for (long long e = tid; e < (long long)M * M; e += nt) {
+            int i = (int)(e % M), j = (int)(e / M);
+            double v = (double)G[e];
+            if (i == j) dia += v * v; else off += v * v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_down_sync(0xffffffffu, off, o);
+            dia += __shfl_down_sync(0xffffffffu, dia, o);
+        }
+        if ((tid & 31) == 0) { red[tid >> 5] = off; red[32 + (tid >> 5)] = dia; }
+        __syncthreads();
+        if (tid == 0) {
+            double so = 0.0, sd = 0.0;
+            for (int w = 0; w < (nt >> 5); ++w) { so += red[w]; sd += red[32 + w]; }
+            s_done = (so <= tol * tol * sd) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_done) break;
+        for (int step = 0; step < Mp - 1; ++step) {
+            // rotation parameters of every pair (p, q)
+            if (tid < half) {
+                int a = top[tid], b = bot[tid];
+                int pi = a < b ? a : b, qi = a < b ? b : a;
+                T c = T(1), s = T(0);
+                if (qi < M) {
+                    T apq = G[pi + (long long)qi * M];
+                    T app = G[pi + (long long)pi * M], aqq = G[qi + (long long)qi * M];
+                    if (apq != T(0) && fabs((double)apq) > 1e-300) {
+                        T th = (aqq - app) / (T(2) * apq);
+                        T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                        c = T(1) / sqrt(tt * tt + T(1));
+                        s = tt * c;
+                    }
+                }
+                cs[2 * tid] = c;
+                cs[2 * tid + 1] = s;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (long long e = tid; e < (long long)half * M; e += nt) {
+                int pr = (int)(e / M), j = (int)(e % M);
+                int a = top[pr], b = bot[pr];
+                int pi = a < b ? a : b, qi = a < b ? b : a;
+                if (qi >= M) continue;
+                T c = cs[2 * pr], s = cs[2 * pr + 1];
+                if (s == T(0)) continue;
+                T apj = G[pi + (long long)j * M], aqj = G[qi + (long long)j * M];
+                G[pi + (long long)j * M] = c * apj - s * aqj;
+                G[qi + (long long)j * M] = s * apj + c * aqj;
+            }
+            __syncthreads();
+            // columns: A <- A J,  V <- V J
+            for (long long e = tid; e < (long long)half * M; e += nt) {
+                int pr = (int)(e / M), i = (int)(e % M);
+                int a = top[pr], b = bot[pr];
+                int pi = a < b ? a : b, qi = a < b ? b : a;
+                if (qi >= M) continue;
+                T c = cs[2 * pr], s = cs[2 * pr + 1];
+                if (s == T(0)) continue;
+                T aip = G[i + (long long)pi * M], aiq = G[i + (long long)qi * M];
+                G[i + (long long)pi * M] = c * aip - s * aiq;
+                G[i + (long long)qi * M] = s * aip + c * aiq;
+                T vip = V[i + (long long)pi * M], viq = V[i + (long long)qi * M];
+                V[i + (long long)pi * M] = c * vip - s * viq;
+                V[i + (long long)qi * M] = s * vip + c * viq;
+            }
+            __syncthreads();
+            // round-robin rotation of the schedule (element top[0] fixed)
+            if (tid == 0 && half > 1) {
+                int t_last = top[half - 1];
+                int b_first = bot[0];
+                for (int i = half - 1; i > 1; --i) top[i] = top[i - 1];
+                if (half > 1) top[1] = b_first;
+                for (int i = 0; i < half - 1; ++i) bot[i] = bot[i + 1];
+                bot[half - 1] = t_last;
+            }
+            __syncthreads();
+        }
+    }
+    // sort eigenvalues (decreasing) by rank counting
+    for (int i = tid; i < M; i += nt) {
+        double li = (double)G[i + (long long)i * M];
+        int rk = 0;
+        for (int j = 0; j < M; ++j) {
+            double lj = (double)G[j + (long long)j * M];
+            if (lj > li || (lj == li && j < i)) ++rk;
+        }
+        order[rk] = i;
+        lam[rk] = li;
+    }
+    __syncthreads();
+    // truncation rule (serial over at most n values)
+    if (tid == 0) {
+        double budget = p.budget;
+        double tail = 0.0;
+        int s = M;
+        // tail[s] = sum_{i >= s} max(lam_i, 0); smallest s with tail[s] <= budget
+        for (int i = M - 1; i >= 0; --i) {
+            double li = lam[i] > 0.0 ? lam[i] : 0.0;
+            if (tail + li <= budget) { tail += li; s = i; } else break;
+        }
+        if (s == 0 && M > 0 && lam[0] > 0.0 && p.norm2 > 0.0) { s = 1; tail -= (lam[0] > 0 ? lam[0] : 0); if (tail < 0) tail = 0; }
+        int cap = p.cap;
+        if (cap > 0 && s > cap) {
+            for (int i = cap; i < s; ++i) tail += lam[i] > 0.0 ? lam[i] : 0.0;
+            s = cap;
+        }
+        p.discarded += tail;
+        p.s[m] = s;
+        for (int i = 0; i < M; ++i) evals[i] = lam[i];
+        // projection Znext = Zc x_m S_m^T
+        const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
+        GemmArgs a{};
+        a.alpha = 1.0; a.beta = 0.0; a.nbatch = 1; a.acc = 0;
+        if (m == 0) {        // (s x d1)^T-view: S^T Z_(1)
+            a.M = s; a.N = d2 * d3; a.K = d1;
+            a.A = S; a.lda = n; a.B = Zc; a.ldb = d1; a.C = Znext; a.ldc = s > 0 ? s : 1;
+        } else if (m == 1) { // per slice: Z_i3 S
+            a.M = d1; a.N = s; a.K = d2; a.nbatch = d3;
+            a.A = Zc; a.lda = d1; a.sA = (long long)d1 * d2;
+            a.B = S; a.ldb = n; a.sB = 0;
+            a.C = Znext; a.ldc = d1; a.sC = (long long)d1 * s;
+        } else {             // Zmat S
+            a.M = d1 * d2; a.N = s; a.K = d3;
+            a.A = Zc; a.lda = (long long)d1 * d2; a.B = S; a.ldb = n; a.C = Znext; a.ldc = (long long)d1 * d2;
+        }
+        ga[0] = a;
+        counts[0] = 1;
+        p.zdim[m] = s;
+    }
+    __syncthreads();
+    // S_m (M x s, ld n): sorted eigenvectors
+    const int s = p.s[m];
+    for (long long e = tid; e < (long long)M * s; e += nt) {
+        int i = (int)(e % M), c = (int)(e / M);
+        S[i + (long long)c * n] = V[i + (long long)order[c] * M];
+    }
+}
+
+// --------------------------------------------------------------------------------------------------
+// Step 4: factors Q_t S_t (or S_t when Q_t = I), new core, plain descriptor.
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void plan_final_kernel(RoundPlan* plan, GemmArgs* ga, const T* Q0, const T* Q1, const T* Q2,
+                                  const T* S0, const T* S1, const T* S2, T* U0, T* U1, T* U2, int* counts) {
+    if (threadIdx.x != 0) return;
+    RoundPlan& p = *plan;
+    const T* Q[3] = {Q0, Q1, Q2};
+    const T* S[3] = {S0, S1, S2};
+    T* U[3] = {U0, U1, U2};
+    for (int t = 0; t < 3; ++t) {
+        GemmArgs a{};
+        a.nbatch = 1; a.acc = 0; a.alpha = 1.0; a.beta = 0.0;
+        a.M = p.n; a.N = p.s[t];
+        if (p.useQ[t]) {
+            a.K = p.k[t]; a.A = Q[t]; a.lda = p.n;
+        } else {
+            a.K = 0;  // handled by the copy kernel
+            a.M = 0;
+        }
+        a.B = S[t]; a.ldb = p.n;
+        a.C = U[t]; a.ldc = p.n;
+        ga[t] = a;
+    }
+    counts[0] = 3;
+}
+
+template <typename T>
+__global__ void final_copy_kernel(const RoundPlan* __restrict__ plan, const T* S0, const T* S1, const T* S2, T* U0,
+                                  T* U1, T* U2, const T* Zfin, T* core, long long core_cap, TuckerDesc* d,
+                                  double* info) {
+    const RoundPlan& p = *plan;
+    const int n = p.n;
+    const T* S[3] = {S0, S1, S2};
+    T* U[3] = {U0, U1, U2};
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (int t = 0; t < 3; ++t) {
+        if (p.useQ[t]) continue;
+        const long long tot = (long long)n * p.s[t];
+        for (long long e = gt; e < tot; e += gs) U[t][e] = S[t][e];
+    }
+    const long long cs = (long long)p.s[0] * p.s[1] * p.s[2];
+    if (cs <= core_cap)
+        for (long long e = gt; e < cs; e += gs) core[e] = Zfin[e];
+    if (gt == 0) {
+        d->nblk = 1;
+        for (int t = 0; t < 3; ++t) {
+            d->rank[t] = p.s[t];
+            d->blk[0].off[t] = 0;
+            d->blk[0].r[t] = p.s[t];
+        }
+        d->blk[0].core = core;
+        d->blk[0].scale = 1.0;
+        if (info) {
+            info[0] = p.norm2;
+            info[1] = p.discarded;
+            info[2] = p.s[0];
+            info[3] = p.s[1];
+            info[4] = p.s[2];
+            info[5] = (cs <= core_cap) ? 0.0 : 1.0;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------------------------
+// Host driver
+// --------------------------------------------------------------------------------------------------
+template <typename T>
+int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
+               cudaStream_t st) {
+    const int n = c->n;
+    const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
+    GemmArgs* ga = c->gargs;
+    int* counts = reinterpret_cast<int*>(c->scal + 200);   // 8 ints of scratch in the scalar area
+    T* Z0 = static_cast<T*>(c->Z0);
+    T* Z1 = static_cast<T*>(c->Z1);
+    plan_round_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(y->desc), c->plan, ga, n, rc, eps, eps_dev,
+                                           c->Rq[0], c->Rq[1], c->Rq[2], y->U[0], y->U[1], y->U[2],
+                                           static_cast<T*>(c->T1), static_cast<T*>(c->Wm), counts,
+                                           (long long)c->max_cols * c->n * c->rank_cap);
+    TPCG_CHECK_LAUNCH();
+    set_c_kernel<<<1, 32, 0, st>>>(ga + 2 * TPCG_MAX_BLOCKS, Z0);
+    // step 1: QR where k_t < n
+    {
+        size_t sm = (size_t)(n + 40) * sizeof(T);
+        qr_kernel<T><<<3, 1024, sm, st>>>(c->plan, static_cast<const T*>(y->U[0]), static_cast<const T*>(y->U[1]),
+                                          static_cast<const T*>(y->U[2]), static_cast<T*>(c->Yw[0]),
+                                          static_cast<T*>(c->Yw[1]), static_cast<T*>(c->Yw[2]),
+                                          static_cast<T*>(c->Rq[0]), static_cast<T*>(c->Rq[1]),
+                                          static_cast<T*>(c->Rq[2]), static_cast<T*>(c->Qq[0]),
+                                          static_cast<T*>(c->Qq[1]), static_cast<T*>(c->Qq[2]));
+        TPCG_CHECK_LAUNCH();
+    }
+    // step 2: Z formation
+    const int rcap = c->rank_cap;
+    TPCG_TRY((launch_gemm<T, false, true>(ga, counts, TPCG_MAX_BLOCKS, rcap, rcap, n, st)));
+    TPCG_TRY((launch_gemm<T, false, false>(ga + TPCG_MAX_BLOCKS, counts, TPCG_MAX_BLOCKS, 1, n, n * rcap, st)));
+    TPCG_TRY((launch_gemm<T, false, true>(ga + 2 * TPCG_MAX_BLOCKS, nullptr, 1, 1, n * n, n, st)));
+    // step 3: ST-HOSVD
+    T* Zc = Z0;
+    T* Zn = Z1;
+    for (int m = 0; m < 3; ++m) {
+        plan_gram_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Zc, static_cast<T*>(c->Part), m, MAX_SPLIT, counts);
+        TPCG_CHECK_LAUNCH();
+        if (m == 0)
+            TPCG_TRY((launch_gemm<T, false, true>(ga, counts, MAX_SPLIT, 1, n, n, st)));
+        else
+            TPCG_TRY((launch_gemm<T, true, false>(ga, counts, MAX_SPLIT, 1, n, n, st)));
+        reduce_partials_kernel<T><<<64, 256, 0, st>>>(static_cast<T*>(c->Part), counts + 1, counts + 2, counts,
+                                                      static_cast<T*>(c->Gm), 0, 1.0, 0.0);
+        TPCG_CHECK_LAUNCH();
+        // ldc of the reduce target: M (set inside via ldc=0 -> use M)
+        size_t sm = eig_smem_bytes(n, sizeof(T));
+        eig_select_kernel<T><<<1, 1024, sm, st>>>(c->plan, ga, static_cast<T*>(c->Gm), static_cast<T*>(c->Yw[0]),
+                                                  static_cast<T*>(c->S[m]), c->evals, Zc, Zn, m, 60, counts);
+        TPCG_CHECK_LAUNCH();
+        if (m == 0)
+            TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
+        else if (m == 1)
+            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
+        else
+            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
+        T* tmp = Zc; Zc = Zn; Zn = tmp;
+    }
+    // step 4
+    plan_final_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, static_cast<const T*>(c->Qq[0]),
+                                           static_cast<const T*>(c->Qq[1]), static_cast<const T*>(c->Qq[2]),
+                                           static_cast<const T*>(c->S[0]), static_cast<const T*>(c->S[1]),
+                                           static_cast<const T*>(c->S[2]), static_cast<T*>(y->U[0]),
+                                           static_cast<T*>(y->U[1]), static_cast<T*>(y->U[2]), counts);
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY((launch_gemm<T, false, false>(ga, counts, 3, 1, n, rcap, st)));
+    final_copy_kernel<T><<<64, 256, 0, st>>>(c->plan, static_cast<const T*>(c->S[0]), static_cast<const T*>(c->S[1]),
+                                             static_cast<const T*>(c->S[2]), static_cast<T*>(y->U[0]),
+                                             static_cast<T*>(y->U[1]), static_cast<T*>(y->U[2]), Zc,
+                                             static_cast<T*>(y->core), y->core_cap,
+                                             static_cast<TuckerDesc*>(y->desc), info_dev);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+
+template int round_impl<double>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t);
+template int round_impl<float>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t);
+
+}  // namespace tpcg

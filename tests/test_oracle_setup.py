@@ -213,3 +213,20 @@ def test_preconditioner_diagonal_bound():
     L = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
     Dt = sum(P.omega[j] / P.lmin * np.einsum("i,j,k->ijk", P.diag(j), P.diag(j), P.diag(j)) for j in range(P.RP))
     assert np.abs(1.0 / L - Dt).max() * L.max() <= 0.1
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5])
+def test_sine_factorization_is_exact_and_sparse(p):
+    # App. B: V1 U1 = W U_dft diag(1/mu) with W the identity on interior rows (odd-reflection symmetry)
+    n_el = 18
+    n = n_el + p - 2
+    n1, n2 = fd.split_dims(n_el, p)
+    W, mu, Udft = fd.sine_factorization(n, p)
+    U, _ = fd.approx_eig(n, p)
+    assert np.abs(W @ Udft / mu - U[:, :n1]).max() <= 1e-11 * np.abs(U[:, :n1]).max()
+    shift = n2 // 2
+    for i in range(p, n - p):
+        row = np.zeros(n1)
+        row[i - shift] = 1.0
+        assert np.abs(W[i] - row).max() < 1e-10
+    assert np.count_nonzero(W) <= n1 + 4 * p * p
