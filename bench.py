@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""TPCG benchmark on GB300: solves/sec to relative residual 1e-6 (plus p50/p99 latency) for the
+single deformed-geometry Poisson workload (twisted quarter annulus, p = 3, n = 128 dofs per direction).
+
+One step = one complete TPCG solve (Alg. 5 with Alg. 1, 2, 4; every hot-path kernel) of the resident
+problem.  ``python bench.py --gpus N --steps K --warmup W`` prints one JSON line on rank 0.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a bounded sample).
+Multi-GPU: independent replicas (one solve stream per GPU, no collective), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+N_DOF, DEGREE, SEED = 128, 3, 7
+AMP = synth.amp_from_seed(SEED)
+TOL = 1e-6
+WORKLOAD = f"twisted quarter annulus Poisson, p={DEGREE}, n={N_DOF}/direction, amp={AMP:.4f} (seed {SEED})"
+METRIC = "TPCG solves/sec to rel-residual 1e-6"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--rank-cap", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------- CPU oracle
+def oracle_sample(iters_for_scale: int, n=N_DOF, p=DEGREE, sample_iters=2):
+    """Time `sample_iters` iterations of the oracle's Alg. 5 on the same workload (setup excluded) and
+    scale to solves/sec with the iteration count of a full solve."""
+    from oracle import fd, lowrank, tpcg as otp
+    terms = lowrank.operator_terms("twist", AMP, n, p)
+    f = lowrank.rhs_tucker("twist", AMP, n, p)
+    P = fd.ApproxFD(n, p)
+    t0 = time.perf_counter()
+    _, info = otp.tpcg(terms, f, P.apply, otp.Params(tol=TOL, max_it=sample_iters))
+    dt = time.perf_counter() - t0
+    per_iter = dt / max(info["iters"], 1)
+    iters = max(iters_for_scale, 1)
+    return {"value": 1.0 / (per_iter * iters), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{info['iters']} TPCG iterations of the {n}^3 p={p} twisted-annulus solve in {dt:.1f}s "
+                      f"(setup excluded), scaled to a {iters}-iteration solve"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    K = max(args.steps, 1)
+    vals = []
+    for _ in range(K):
+        vals.append(oracle_sample(30, sample_iters=1)["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tol": TOL},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "1 TPCG iteration per step, scaled to a 30-iteration solve"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2306_00632_gb300 import api, lib
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    L = lib.load()
+    dt = lib.F64 if args.dtype == "f64" else lib.F32
+    pb = api.tpcg_setup(lib.GEOM_TWIST, AMP, DEGREE, N_DOF, dt)
+    info = pb.info
+    rc = min(args.rank_cap, N_DOF)
+    rfm = max(info.rf)
+    max_cols = max(info.R * rc + rfm, info.RP * rc, 2 * rc)
+    ctx = api.Ctx(N_DOF, max_cols, rc, dt)
+    x = api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=dt)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def solve():
+        return api.tpcg_solve(pb, ctx, x, tol=TOL, rank_cap=rc)
+
+    for _ in range(max(args.warmup, 0)):
+        st = solve()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    L.tpcg_profile_reset()
+    L.tpcg_profile_enable(1)
+    launches0 = L.tpcg_launch_count()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    g0.record(stream)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        st = solve()
+        ev[k][1].record(stream)
+        stats.append((st.iters, st.rel_res, st.status, tuple(st.rank)))
+    g1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = L.tpcg_launch_count() - launches0
+    L.tpcg_profile_enable(0)
+    clk = clocks.stop()
+    total_ms = g0.elapsed_time(g1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # per-kernel-class profile of the timed region
+    import ctypes as C
+    prof = {}
+    for name, kind in lib.PROF_KINDS.items():
+        ms, cnt, fl, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        L.tpcg_profile_get(kind, C.byref(ms), C.byref(cnt), C.byref(fl), C.byref(by))
+        prof[name] = {"ms": ms.value, "launches": cnt.value, "flops": fl.value, "bytes": by.value}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    peak_src = "measured" if peaks else "fallback"
+    fp64_peak = bf16 * 1.25 / 2250.0       # nominal FP64 / bf16 dense ratio x measured bf16
+    fp32_peak = bf16 * 75.0 / 2250.0       # nominal FP32 (SIMT) / bf16 ratio x measured bf16
+    kernel_classes = ["zgemm", "zblk", "gram", "eig", "proj", "qr", "apply", "fd"]
+    dom = max(kernel_classes, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    roof = {"kernel": dom, "share_of_step": d["ms"] / max(sum(step_ms), 1e-9)}
+    if dom in ("apply", "fd"):
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                     "frac": ach / hbm, "traffic": None, "peak_source": peak_src})
+    elif dom == "eig":
+        roof.update({"bound": "latency", "achieved": d["ms"] / max(d["launches"], 1), "peak": None,
+                     "unit": "ms/launch", "frac": None, "traffic": None, "peak_source": peak_src})
+    else:
+        pk = fp64_peak if dt == lib.F64 else fp32_peak
+        ach = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                     "traffic": None, "peak_source": f"{peak_src} bf16 x nominal {'FP64' if dt == lib.F64 else 'FP32'}/bf16"})
+
+    value = ws * args.steps / (total_ms * 1e-3)
+    iters = [s[0] for s in stats]
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+           "config": {"workload": WORKLOAD, "tol": TOL, "rank_cap": rc, "R": info.R, "RP": info.RP,
+                      "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps"},
+           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+           "solve": {"iters": iters, "rel_res": [s[1] for s in stats], "status": [s[2] for s in stats],
+                     "rank": list(stats[-1][3])},
+           "gpu_launches": int(launches), "roofline": roof,
+           "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+           "clocks": clk}
+
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = e2e(api, lib, pb, dt, ctx, rc, args)
+    if rank == 0 and not args.no_cpu and ws == 1:
+        try:
+            out["cpu_baseline"] = oracle_sample(int(np.median(iters)))
+        except Exception as e:   # the baseline must not hide the GPU line
+            out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e(api, lib, pb, dt, ctx, rc, args):
+    """Same metric through the public API with host inputs: every step re-creates the problem from pinned
+    host arrays (host -> device copies inside tpcg_problem_create), solves, and reads the solution back."""
+    import torch
+    ex = pb.export()
+    info = pb.info
+    n = info.n
+    ex["v2u2"] = ex["v2u2"][: n * info.n2]
+    h2d = 8 * sum(int(np.asarray(ex[k]).size) for k in ("w", "bands", "f_core", "f_U0", "f_U1", "f_U2", "lam",
+                                                        "mu", "w_val", "v2u2", "omega", "alpha"))
+    h2d += 4 * (int(ex["w_rowptr"].size) + int(ex["w_col"].size))
+    x = api.Tucker(n, cap=rc, core_cap=rc ** 3, dtype=dt)
+    K = max(2, min(args.steps, 3))
+    times = []
+    d2h = 0
+    for k in range(K + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pb2 = api.problem_from_export(ex, info, dtype=dt, pinned=True)
+        st = api.tpcg_solve(pb2, ctx, x, tol=TOL, rank_cap=rc)
+        core, fac = x.to_numpy()
+        torch.cuda.synchronize()
+        if k > 0:
+            times.append(time.perf_counter() - t0)
+        d2h = (core.size + sum(f.size for f in fac)) * (8 if dt == lib.F64 else 4)
+        del pb2
+    return {"value": 1.0 / statistics.median(times), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": K}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -118,6 +118,7 @@ int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* out);
 typedef struct {
     int n, p, R, RP, n1, n2, rf[3], dtype;
     double lambda_min, lambda_max, MP, norm_f;
+    int w_nnz;          /* non-zeros of W */
 } tpcg_problem_info;
 
 int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* out);
@@ -126,6 +127,8 @@ int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* out);
  * sized from tpcg_problem_get_info; any pointer may be NULL to skip it).  f_U[t] gets n x rf[t]. */
 int tpcg_problem_export(tpcg_problem pb, double* w, double* bands, double* f_core, double* f_U0, double* f_U1,
                         double* f_U2, double* lam, double* mu, double* v2u2, double* omega, double* alpha);
+/* W of the sine factorisation in CSR (rowptr n+1, col/val w_nnz); NULL pointers are skipped. */
+int tpcg_problem_export_w(tpcg_problem pb, int* rowptr, int* col, double* val);
 void tpcg_problem_destroy(tpcg_problem pb);
 
 /* ------------------------------------------------------------------------------------ workspace */
@@ -189,6 +192,20 @@ void tpcg_params_default(tpcg_params* p);
 /* Alg. 5 with x_0 = 0: x receives the low-rank solution (plain, caller buffers with cap >= rank_cap and
  * core_cap >= rank_cap^3).  Synchronises the stream once per iteration for the stopping test. */
 int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
+
+/* ------------------------------------------------------------------------------------ profiling */
+/* Kernel classes timed with CUDA events on the launching stream while profiling is on:
+ *   0 fused last-mode GEMM of Alg. 1 step 2 (Z formation)   1 per-block mode products of step 2
+ *   2 mode Grams of ST-HOSVD (split-K GEMM + reduction)       3 eigensolver + truncation rule
+ *   4 ST-HOSVD projections   5 Householder QR   6 banded matvec (apply/residual)   7 FD application
+ *   8 Tucker dot   9 whole tucker_round   10 reserved.
+ * flops/bytes are the algorithmic work of the launches (accumulated on the device from the actual ranks). */
+#define TPCG_PROF_KINDS 16
+int tpcg_profile_enable(int on);
+int tpcg_profile_reset(void);
+int tpcg_profile_get(int kind, double* ms_total, long long* count, double* flops, double* bytes);
+/* Number of kernels this library has launched since load (host counter, no synchronisation). */
+long long tpcg_launch_count(void);
 
 /* ------------------------------------------------------------------------------------ misc */
 const char* tpcg_last_error(void);

@@ -138,6 +138,17 @@ class Problem:
         keys = ["w", "bands", "f_core", "f_U0", "f_U1", "f_U2", "lam", "mu", "v2u2", "omega", "alpha"]
         ptrs = [out[k].ctypes.data_as(C.c_void_p) for k in keys]
         check(L.load().tpcg_problem_export(self.h, *ptrs), "tpcg_problem_export")
+        rowptr = np.zeros(n + 1, dtype=np.int32)
+        col = np.zeros(max(i.w_nnz, 1), dtype=np.int32)
+        val = np.zeros(max(i.w_nnz, 1))
+        check(L.load().tpcg_problem_export_w(self.h, rowptr.ctypes.data_as(C.c_void_p), col.ctypes.data_as(C.c_void_p),
+                                             val.ctypes.data_as(C.c_void_p)), "tpcg_problem_export_w")
+        W = np.zeros((n, n1))
+        for r in range(n):
+            for e in range(rowptr[r], rowptr[r + 1]):
+                W[r, col[e]] = val[e]
+        out["W"] = W
+        out["w_rowptr"], out["w_col"], out["w_val"] = rowptr, col, val
         return out
 
 
@@ -145,6 +156,45 @@ def tpcg_setup(kind: int, amp: float, degree: int, n: int, dtype: int = L.F64, e
     g = L.Geometry(kind, amp, eps_geo, eps_prec)
     h = C.c_void_p()
     check(L.load().tpcg_setup(C.byref(g), degree, n, dtype, C.byref(h)), "tpcg_setup")
+    return Problem(h.value, dtype)
+
+
+def problem_from_export(ex, info, dtype=L.F64, pinned=True) -> Problem:
+    """Re-create a problem from exported host arrays (bands and W in CSR as stored by the library).
+    With ``pinned`` the arrays are first placed in page-locked host memory."""
+    keep = []
+
+    def host(a, np_dt):
+        a = np.ascontiguousarray(a, dtype=np_dt)
+        if pinned:
+            t = torch.from_numpy(a).pin_memory()
+            keep.append(t)
+            return t.data_ptr()
+        keep.append(a)
+        return a.ctypes.data
+
+    n, p, R = info.n, info.p, info.R
+    a = L.ProblemArrays()
+    a.n, a.p, a.R, a.dtype = n, p, R, dtype
+    dptr = lambda arr: C.cast(host(arr, np.float64), C.POINTER(C.c_double))
+    iptr = lambda arr: C.cast(host(arr, np.int32), C.POINTER(C.c_int))
+    a.w = dptr(ex["w"])
+    a.bands = dptr(ex["bands"])
+    a.rf = (C.c_int * 3)(*info.rf)
+    a.f_core = dptr(ex["f_core"])
+    a.f_U = (C.POINTER(C.c_double) * 3)(*[dptr(ex[f"f_U{t}"]) for t in range(3)])
+    a.n1, a.n2, a.RP, a.w_nnz = info.n1, info.n2, info.RP, info.w_nnz
+    a.lam = dptr(ex["lam"])
+    a.mu = dptr(ex["mu"])
+    a.w_rowptr = iptr(ex["w_rowptr"])
+    a.w_col = iptr(ex["w_col"])
+    a.w_val = dptr(ex["w_val"])
+    a.v2u2 = dptr(ex["v2u2"]) if info.n2 > 0 else C.POINTER(C.c_double)()
+    a.omega = dptr(ex["omega"])
+    a.alpha = dptr(ex["alpha"])
+    a.lambda_min = info.lambda_min
+    h = C.c_void_p()
+    check(L.load().tpcg_problem_create(C.byref(a), C.byref(h)), "tpcg_problem_create")
     return Problem(h.value, dtype)
 
 

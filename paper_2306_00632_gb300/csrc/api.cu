@@ -117,6 +117,7 @@ __global__ void scalar_kernel(int op, double* s, const double* prm) {
 
 void launch_scalar(int op, double* s, const double* prm, cudaStream_t st) {
     scalar_kernel<<<1, 32, 0, st>>>(op, s, prm);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 // ------------------------------------------------------------------------------------ dispatch helpers
@@ -179,7 +180,7 @@ static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) 
     sizes[i++] = 3 * (size_t)rc * rc * e;                    // dotw
     sizes[i++] = 2 * (size_t)rc * rc * rc * e;               // dotT
     for (int t = 0; t < 12; ++t) sizes[i++] = (size_t)n * max_cols * e;   // fd scratch
-    size_t tot = 0;
+    size_t tot = eig_work_bytes(n);
     for (size_t j = 0; j < i; ++j) tot += (sizes[j] + 255) & ~(size_t)255;
     return tot;
 }
@@ -233,6 +234,13 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
         for (int q = 0; q < 4; ++q) slots[i++] = &c->fd[t][q];
     for (int j = 0; j < i; ++j) {
         int s = dmalloc(slots[j], sizes[j], &c->owned);
+        if (s != TPCG_OK) {
+            tpcg_ctx_destroy(c);
+            return s;
+        }
+    }
+    {
+        int s = eig_work_alloc(&c->eigw, n, &c->owned);
         if (s != TPCG_OK) {
             tpcg_ctx_destroy(c);
             return s;
@@ -483,6 +491,15 @@ extern "C" int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* o) {
     o->lambda_max = pb->lambda_max;
     o->MP = pb->lambda_max / pb->lambda_min;
     o->norm_f = pb->norm_f;
+    o->w_nnz = (int)pb->w_val.size();
+    return TPCG_OK;
+}
+
+extern "C" int tpcg_problem_export_w(tpcg_problem pb, int* rowptr, int* col, double* val) {
+    if (!pb) return TPCG_E_INVALID;
+    if (rowptr) memcpy(rowptr, pb->w_rowptr.data(), pb->w_rowptr.size() * sizeof(int));
+    if (col && !pb->w_col.empty()) memcpy(col, pb->w_col.data(), pb->w_col.size() * sizeof(int));
+    if (val && !pb->w_val.empty()) memcpy(val, pb->w_val.data(), pb->w_val.size() * sizeof(double));
     return TPCG_OK;
 }
 

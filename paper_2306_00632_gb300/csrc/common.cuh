@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -14,6 +15,15 @@ namespace tpcg {
 
 // ------------------------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
+
+// ------------------------------------------------------------------------------------ profiling
+extern std::atomic<long long> g_launches;
+enum { PK_ZGEMM = 0, PK_ZBLK, PK_GRAM, PK_EIG, PK_PROJ, PK_QR, PK_APPLY, PK_FD, PK_DOT, PK_ROUND, PK_FINAL,
+       PK_COUNT = 16 };
+bool prof_on();
+double* prof_dev();                       // device accumulators [kind*2] flops, [kind*2+1] bytes, or null
+void prof_begin(int kind, cudaStream_t st);
+void prof_end(int kind, cudaStream_t st);
 
 #define TPCG_CUDA(call)                                                                   \
     do {                                                                                  \
@@ -26,6 +36,7 @@ void set_error(const std::string& msg);
 
 #define TPCG_CHECK_LAUNCH()                                                               \
     do {                                                                                  \
+        ::tpcg::g_launches.fetch_add(1, std::memory_order_relaxed);                       \
         cudaError_t e_ = cudaGetLastError();                                              \
         if (e_ != cudaSuccess) {                                                          \
             ::tpcg::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));   \
@@ -101,6 +112,9 @@ struct Buf {
 
 }  // namespace tpcg
 
+namespace tpcg { struct EigWork; }
+#include "eig.cuh"
+
 struct tpcg_ctx_s {
     int n, max_cols, rank_cap, dtype;
     size_t elt;
@@ -122,6 +136,7 @@ struct tpcg_ctx_s {
     double* dotw;        // small Gram matrices for dots: 3 * rank_cap * rank_cap * 2 + core temps
     void* dotT;          // rank_cap^3 * 2 temporaries for dot contractions
     void* fd[3][4];      // n * max_cols each: FD application scratch (gather, transform, scaled, back)
+    tpcg::EigWork eigw;  // eigensolver work area
     // TPCG iterate tensors (allocated on first solve)
     std::vector<void*> owned;
     tucker_t tens[10];

@@ -75,8 +75,13 @@ __global__ void apply_kernel(const T* __restrict__ bands, int n, int p, int R, c
 // output descriptor of the apply: blocks (f) + (j, b) for every term j and input block b
 __global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const double* __restrict__ w, int R,
                                   double sign, const TuckerDesc* __restrict__ fdsc, TuckerDesc* yd, int cap,
-                                  int* err) {
+                                  int* err, double* prof, int n, int p, int elt) {
     if (threadIdx.x != 0) return;
+    if (prof) {   // algorithmic work of the banded products: bands read once, X read, Y written
+        double cols = (double)xd->rank[0] + xd->rank[1] + xd->rank[2];
+        prof[2 * PK_APPLY] += 2.0 * (2 * p + 1) * (double)n * R * cols;
+        prof[2 * PK_APPLY + 1] += (double)elt * ((double)R * 3 * (2 * p + 1) * n + (double)n * cols * (1.0 + R));
+    }
     int nb = 0;
     int base[3] = {0, 0, 0};
     if (fdsc) {
@@ -108,6 +113,7 @@ int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, c
     const int n = pb->n;
     dim3 grid((n + 127) / 128, pb->R + (residual ? 1 : 0), 3);
     const tucker_t* f = &pb->f;
+    prof_begin(PK_APPLY, st);
     apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
                                           static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
                                           static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
@@ -120,8 +126,10 @@ int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, c
     apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R,
                                         residual ? -1.0 : 1.0,
                                         residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
-                                        static_cast<TuckerDesc*>(y->desc), y->cap, reinterpret_cast<int*>(pb->d_scal + 60));
+                                        static_cast<TuckerDesc*>(y->desc), y->cap, reinterpret_cast<int*>(pb->d_scal + 60),
+                                        prof_dev(), n, pb->p, (int)sizeof(T));
     TPCG_CHECK_LAUNCH();
+    prof_end(PK_APPLY, st);
     return TPCG_OK;
 }
 template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t);
@@ -279,6 +287,7 @@ int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, 
     T* Wb = reinterpret_cast<T*>(c->dotw);
     T* Ta = static_cast<T*>(c->dotT);
     T* Tb = Ta + (long long)rc * rc * rc;
+    prof_begin(PK_DOT, st);
     plan_dot_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
                                          static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
                                          static_cast<const TuckerDesc*>(y->desc), static_cast<const T*>(y->U[0]),
@@ -291,6 +300,7 @@ int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, 
     TPCG_TRY((launch_gemm<T, false, true>(ga + 5, nullptr, 1, 1, rc * rc, rc, st)));
     dot_finish_kernel<T><<<1, 1024, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), Ta, out_dev, counts + 1);
     TPCG_CHECK_LAUNCH();
+    prof_end(PK_DOT, st);
     return TPCG_OK;
 }
 template int dot_impl<double>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
@@ -440,6 +450,7 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
     for (int t = 0; t < 3; ++t)
         for (int q = 0; q < 4; ++q) buf[t][q] = static_cast<T*>(c->fd[t][q]);
     const TuckerDesc* sd = static_cast<const TuckerDesc*>(s->desc);
+    prof_begin(PK_FD, st);
     dim3 g1((n1 + 127) / 128, rc, 3);
     fd_gather_kernel<T><<<g1, 128, 0, st>>>(sd, static_cast<const T*>(s->U[0]), static_cast<const T*>(s->U[1]),
                                             static_cast<const T*>(s->U[2]), pb->d_wtrow, pb->d_wtcol,
@@ -471,6 +482,7 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
     fd_desc_kernel<<<1, 32, 0, st>>>(sd, pb->d_omega, pb->lambda_min, RP, static_cast<TuckerDesc*>(v->desc), v->cap,
                                      err);
     TPCG_CHECK_LAUNCH();
+    prof_end(PK_FD, st);
     return TPCG_OK;
 }
 template int fd_impl<double>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t);

@@ -1,0 +1,113 @@
+// Launch counting and per-kernel-class timing (CUDA events on the launching stream) with device-side
+// accumulation of the algorithmic flops/bytes of the launches (ranks live on the device).
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tpcg {
+
+std::atomic<long long> g_launches{0};
+
+namespace {
+struct EvPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+std::mutex g_mu;
+bool g_on = false;
+double* g_dev = nullptr;                // PK_COUNT * 2 doubles: flops, bytes
+std::vector<EvPair> g_pairs;            // recorded (start, stop) pairs
+std::vector<cudaEvent_t> g_free;        // recycled events
+std::vector<int> g_open(PK_COUNT, -1);  // index of the open pair per kind
+long long g_count[PK_COUNT] = {0};
+
+cudaEvent_t get_event() {
+    if (!g_free.empty()) {
+        cudaEvent_t e = g_free.back();
+        g_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+}  // namespace
+
+bool prof_on() { return g_on; }
+double* prof_dev() { return g_on ? g_dev : nullptr; }
+
+void prof_begin(int kind, cudaStream_t st) {
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    EvPair p{get_event(), get_event(), kind};
+    cudaEventRecord(p.a, st);
+    g_open[kind] = (int)g_pairs.size();
+    g_pairs.push_back(p);
+}
+
+void prof_end(int kind, cudaStream_t st) {
+    if (!g_on) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int i = g_open[kind];
+    if (i < 0) return;
+    cudaEventRecord(g_pairs[i].b, st);
+    g_open[kind] = -1;
+    g_count[kind]++;
+}
+
+}  // namespace tpcg
+
+using namespace tpcg;
+
+extern "C" long long tpcg_launch_count(void) { return g_launches.load(); }
+
+extern "C" int tpcg_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (on && !g_dev) {
+        if (cudaMalloc(&g_dev, PK_COUNT * 2 * sizeof(double)) != cudaSuccess) {
+            g_dev = nullptr;
+            set_error("tpcg_profile_enable: cudaMalloc failed");
+            return TPCG_E_NOMEM;
+        }
+        cudaMemset(g_dev, 0, PK_COUNT * 2 * sizeof(double));
+    }
+    g_on = on != 0;
+    return TPCG_OK;
+}
+
+extern "C" int tpcg_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaDeviceSynchronize();
+    for (auto& p : g_pairs) {
+        g_free.push_back(p.a);
+        g_free.push_back(p.b);
+    }
+    g_pairs.clear();
+    for (int k = 0; k < PK_COUNT; ++k) {
+        g_open[k] = -1;
+        g_count[k] = 0;
+    }
+    if (g_dev) cudaMemset(g_dev, 0, PK_COUNT * 2 * sizeof(double));
+    return TPCG_OK;
+}
+
+extern "C" int tpcg_profile_get(int kind, double* ms_total, long long* count, double* flops, double* bytes) {
+    if (kind < 0 || kind >= PK_COUNT) return TPCG_E_INVALID;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaDeviceSynchronize();
+    double ms = 0;
+    for (auto& p : g_pairs) {
+        if (p.kind != kind) continue;
+        float t = 0;
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms += t;
+    }
+    if (ms_total) *ms_total = ms;
+    if (count) *count = g_count[kind];
+    double h[2] = {0, 0};
+    if (g_dev) cudaMemcpy(h, g_dev + 2 * kind, sizeof(h), cudaMemcpyDeviceToHost);
+    if (flops) *flops = h[0];
+    if (bytes) *bytes = h[1];
+    return TPCG_OK;
+}

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "gemm.cuh"
+#include "eig.cuh"
 #include "kernels.cuh"
 
 namespace tpcg {
@@ -28,7 +29,7 @@ template <typename T>
 __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* plan, GemmArgs* ga, int n,
                                   int cap, double eps_host, const double* eps_dev, void* Rq0, void* Rq1,
                                   void* Rq2, const void* U0, const void* U1, const void* U2, T* T1, T* Wm,
-                                  int* counts, long long t1cap) {
+                                  int* counts, long long t1cap, double* prof) {
     if (threadIdx.x != 0) return;
     RoundPlan p;
     p.n = n;
@@ -87,6 +88,18 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
     z.alpha = 1.0; z.beta = 0.0;
     ga[2 * TPCG_MAX_BLOCKS] = z;
     counts[0] = p.nblk;
+    if (prof) {
+        const double e = sizeof(T);
+        const double M3 = (double)kp1 * kp2, K3 = p.k[2], N3 = p.kp[2];
+        prof[2 * PK_ZGEMM] += 2.0 * M3 * N3 * K3;
+        prof[2 * PK_ZGEMM + 1] += e * (M3 * K3 + N3 * K3 + M3 * N3);
+        double fb = 0;
+        for (int b = 0; b < p.nblk; ++b) {
+            const BlockDesc& B = d->blk[b];
+            fb += 2.0 * B.r[0] * kp2 * B.r[2] * B.r[1] + 2.0 * kp1 * kp2 * B.r[2] * B.r[0];
+        }
+        prof[2 * PK_ZBLK] += fb;
+    }
     if (t1off > t1cap) {   // workspace too small for these blocks: produce nothing, flag the plan
         p.status = 1;
         counts[0] = 0;
@@ -211,12 +224,16 @@ __global__ void __launch_bounds__(1024) qr_kernel(const RoundPlan* __restrict__ 
 // --------------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* Part, int m, int nsplit_max,
-                                 int* counts) {
+                                 int* counts, double* prof) {
     if (threadIdx.x != 0) return;
     RoundPlan& p = *plan;
     const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
     const int M = p.zdim[m];
     int total = (m == 0) ? d2 * d3 : (m == 1 ? d3 : d1 * d2);
+    if (prof) {
+        prof[2 * PK_GRAM] += 2.0 * M * M * ((double)d1 * d2 * d3 / (M > 0 ? M : 1));
+        prof[2 * PK_GRAM + 1] += sizeof(T) * ((double)d1 * d2 * d3 + (double)M * M);
+    }
     int ns = total < nsplit_max ? total : nsplit_max;
     if (ns < 1) ns = 1;
     if (M == 0 || total == 0) ns = 0;
@@ -253,196 +270,222 @@ __global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* 
     counts[2] = M;
 }
 
-inline size_t eig_smem_bytes(int n, size_t elt) {
-    const size_t L = (size_t)n + 4;   // >= padded size + 2
-    return L * sizeof(int) * 2 + L * elt + 64 * sizeof(double) + L * sizeof(int) + L * sizeof(double) + 64;
+// --------------------------------------------------------------------------------------------------
+// Truncation rule of ST-HOSVD on mode m and the plan of the projection Z x_m S_m^T.
+// FP64 form: eigenpairs refined in FP64; lambda_i = (X^T A X)_ii / (X^T X)_ii.
+// --------------------------------------------------------------------------------------------------
+__device__ void plan_projection(RoundPlan& p, GemmArgs* ga, const void* S, long long ldS, const void* Zc, void* Znext,
+                                int m, int s) {
+    const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
+    GemmArgs a{};
+    a.alpha = 1.0; a.beta = 0.0; a.nbatch = 1; a.acc = 0;
+    if (m == 0) {        // S^T Z_(1)
+        a.M = s; a.N = d2 * d3; a.K = d1;
+        a.A = S; a.lda = ldS; a.B = Zc; a.ldb = d1 > 0 ? d1 : 1; a.C = Znext; a.ldc = s > 0 ? s : 1;
+    } else if (m == 1) { // per slice: Z_i3 S
+        a.M = d1; a.N = s; a.K = d2; a.nbatch = d3;
+        a.A = Zc; a.lda = d1 > 0 ? d1 : 1; a.sA = (long long)d1 * d2;
+        a.B = S; a.ldb = ldS; a.sB = 0;
+        a.C = Znext; a.ldc = d1 > 0 ? d1 : 1; a.sC = (long long)d1 * s;
+    } else {             // Zmat S
+        a.M = d1 * d2; a.N = s; a.K = d3;
+        a.A = Zc; a.lda = (long long)d1 * d2 > 0 ? (long long)d1 * d2 : 1; a.B = S; a.ldb = ldS; a.C = Znext;
+        a.ldc = a.lda;
+    }
+    ga[0] = a;
 }
 
-// --------------------------------------------------------------------------------------------------
-// Symmetric eigensolver (cyclic Jacobi, round-robin parallel ordering) + truncation rule + plan of the
-// projection.  One CTA.  G (M x M, ld M) is overwritten; eigenvectors sorted by decreasing eigenvalue go
-// to S (ld n).  Tail energies use the eigenvalues clamped at zero.
-// --------------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(1024) eig_select_kernel(RoundPlan* plan, GemmArgs* ga, T* G, T* V, T* S,
-                                                          double* evals, const T* Zc, T* Znext, int m,
-                                                          int max_sweeps, int* counts) {
-    RoundPlan& p = *plan;
+__device__ double gram_trace(const RoundPlan& p, const void* G, bool dbl) {
+    double tr = 0.0;
     const int M = p.gM;
-    const int n = p.n;
-    extern __shared__ unsigned char smem_raw[];
-    int* top = reinterpret_cast<int*>(smem_raw);
-    const int Mp = (M + 1) & ~1;              // padded to even for the round-robin schedule
-    int* bot = top + (Mp / 2 + 1);
-    T* cs = reinterpret_cast<T*>(bot + (Mp / 2 + 1));   // 2 * Mp/2
-    double* red = reinterpret_cast<double*>(cs + Mp + 2);   // 64 doubles
-    int* order = reinterpret_cast<int*>(red + 64);         // M
-    double* lam = reinterpret_cast<double*>(order + Mp + 2);    // M (sorted)
-    __shared__ int s_done;
+    for (int i = 0; i < M; ++i)
+        tr += dbl ? static_cast<const double*>(G)[i + (long long)i * M] : (double)static_cast<const float*>(G)[i + (long long)i * M];
+    return tr;
+}
 
-    const int tid = threadIdx.x, nt = blockDim.x;
-    // V = I
-    for (long long e = tid; e < (long long)M * M; e += nt) V[e] = ((e % M) == (e / M)) ? T(1) : T(0);
-    if (m == 0) {
-        // ||Z||^2 = trace of the mode-1 Gram
-        double tr = 0.0;
-        for (int i = tid; i < M; i += nt) tr += (double)G[i + (long long)i * M];
-        for (int o = 16; o > 0; o >>= 1) tr += __shfl_down_sync(0xffffffffu, tr, o);
-        if ((tid & 31) == 0) red[tid >> 5] = tr;
-        __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < (nt >> 5); ++w) s += red[w];
-            p.norm2 = s;
-            p.budget = p.eps * p.eps * s / 3.0;
-        }
-        __syncthreads();
-    }
-    const int half = Mp / 2;
-    if (tid < half) { top[tid] = 2 * tid; bot[tid] = 2 * tid + 1; }
-    __syncthreads();
-    // stop when ||offdiag||_F <= 8 M eps_mach ||diag||_F (the rounding floor of the rotations)
-    const double tol = 8.0 * (M > 1 ? M : 1) * ((sizeof(T) == 8) ? 1.1e-16 : 6.0e-8);
-    for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
-        // convergence test: off-diagonal vs diagonal Frobenius norms
-        double off = 0.0, dia = 0.0;
-        for (long long e = tid; e < (long long)M * M; e += nt) {
-            int i = (int)(e % M), j = (int)(e / M);
-            double v = (double)G[e];
-            if (i == j) dia += v * v; else off += v * v;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_down_sync(0xffffffffu, off, o);
-            dia += __shfl_down_sync(0xffffffffu, dia, o);
-        }
-        if ((tid & 31) == 0) { red[tid >> 5] = off; red[32 + (tid >> 5)] = dia; }
-        __syncthreads();
-        if (tid == 0) {
-            double so = 0.0, sd = 0.0;
-            for (int w = 0; w < (nt >> 5); ++w) { so += red[w]; sd += red[32 + w]; }
-            s_done = (so <= tol * tol * sd) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_done) break;
-        for (int step = 0; step < Mp - 1; ++step) {
-            // rotation parameters of every pair (p, q)
-            if (tid < half) {
-                int a = top[tid], b = bot[tid];
-                int pi = a < b ? a : b, qi = a < b ? b : a;
-                T c = T(1), s = T(0);
-                if (qi < M) {
-                    T apq = G[pi + (long long)qi * M];
-                    T app = G[pi + (long long)pi * M], aqq = G[qi + (long long)qi * M];
-                    if (apq != T(0) && fabs((double)apq) > 1e-300) {
-                        T th = (aqq - app) / (T(2) * apq);
-                        T tt = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
-                        c = T(1) / sqrt(tt * tt + T(1));
-                        s = tt * c;
-                    }
-                }
-                cs[2 * tid] = c;
-                cs[2 * tid + 1] = s;
-            }
-            __syncthreads();
-            // rows: A <- J^T A
-            for (long long e = tid; e < (long long)half * M; e += nt) {
-                int pr = (int)(e / M), j = (int)(e % M);
-                int a = top[pr], b = bot[pr];
-                int pi = a < b ? a : b, qi = a < b ? b : a;
-                if (qi >= M) continue;
-                T c = cs[2 * pr], s = cs[2 * pr + 1];
-                if (s == T(0)) continue;
-                T apj = G[pi + (long long)j * M], aqj = G[qi + (long long)j * M];
-                G[pi + (long long)j * M] = c * apj - s * aqj;
-                G[qi + (long long)j * M] = s * apj + c * aqj;
-            }
-            __syncthreads();
-            // columns: A <- A J,  V <- V J
-            for (long long e = tid; e < (long long)half * M; e += nt) {
-                int pr = (int)(e / M), i = (int)(e % M);
-                int a = top[pr], b = bot[pr];
-                int pi = a < b ? a : b, qi = a < b ? b : a;
-                if (qi >= M) continue;
-                T c = cs[2 * pr], s = cs[2 * pr + 1];
-                if (s == T(0)) continue;
-                T aip = G[i + (long long)pi * M], aiq = G[i + (long long)qi * M];
-                G[i + (long long)pi * M] = c * aip - s * aiq;
-                G[i + (long long)qi * M] = s * aip + c * aiq;
-                T vip = V[i + (long long)pi * M], viq = V[i + (long long)qi * M];
-                V[i + (long long)pi * M] = c * vip - s * viq;
-                V[i + (long long)qi * M] = s * vip + c * viq;
-            }
-            __syncthreads();
-            // round-robin rotation of the schedule (element top[0] fixed)
-            if (tid == 0 && half > 1) {
-                int t_last = top[half - 1];
-                int b_first = bot[0];
-                for (int i = half - 1; i > 1; --i) top[i] = top[i - 1];
-                if (half > 1) top[1] = b_first;
-                for (int i = 0; i < half - 1; ++i) bot[i] = bot[i + 1];
-                bot[half - 1] = t_last;
-            }
-            __syncthreads();
-        }
-    }
-    // sort eigenvalues (decreasing) by rank counting
-    for (int i = tid; i < M; i += nt) {
-        double li = (double)G[i + (long long)i * M];
+// rank-count sort (decreasing) of M values into order[], one thread per element
+__device__ void sort_desc(const double* v, int M, int* order, double* sorted) {
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double vi = v[i];
         int rk = 0;
         for (int j = 0; j < M; ++j) {
-            double lj = (double)G[j + (long long)j * M];
-            if (lj > li || (lj == li && j < i)) ++rk;
+            const double vj = v[j];
+            if (vj > vi || (vj == vi && j < i)) ++rk;
         }
         order[rk] = i;
-        lam[rk] = li;
+        sorted[rk] = vi;
+    }
+}
+
+// smallest s whose discarded (clamped) values sum to <= budget, then the cap; returns s, adds the tail
+__device__ int choose_rank(const double* sorted, int M, RoundPlan& p) {
+    double tail = 0.0;
+    int s = M;
+    for (int i = M - 1; i >= 0; --i) {
+        const double li = sorted[i] > 0.0 ? sorted[i] : 0.0;
+        if (tail + li <= p.budget) { tail += li; s = i; } else break;
+    }
+    if (s == 0 && M > 0 && sorted[0] > 0.0 && p.norm2 > 0.0) {
+        s = 1;
+        tail -= sorted[0] > 0 ? sorted[0] : 0.0;
+        if (tail < 0) tail = 0;
+    }
+    if (p.cap > 0 && s > p.cap) {
+        for (int i = p.cap; i < s; ++i) tail += sorted[i] > 0.0 ? sorted[i] : 0.0;
+        s = p.cap;
+    }
+    p.discarded += tail;
+    return s;
+}
+
+__global__ void __launch_bounds__(1024) select64_kernel(RoundPlan* plan, GemmArgs* ga, const double* __restrict__ G,
+                                                        const double* __restrict__ X, const double* __restrict__ XtX,
+                                                        const double* __restrict__ Sm, double* lamw, int* order,
+                                                        double* S, double* evals, const double* Zc, double* Znext, int m,
+                                                        int* counts) {
+    RoundPlan& p = *plan;
+    const int M = p.gM, n = p.n;
+    __shared__ int s_s;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const double nn = XtX[i + (long long)i * M];
+        lamw[i] = nn > 0 ? Sm[i + (long long)i * M] / nn : 0.0;
     }
     __syncthreads();
-    // truncation rule (serial over at most n values)
-    if (tid == 0) {
-        double budget = p.budget;
-        double tail = 0.0;
-        int s = M;
-        // tail[s] = sum_{i >= s} max(lam_i, 0); smallest s with tail[s] <= budget
-        for (int i = M - 1; i >= 0; --i) {
-            double li = lam[i] > 0.0 ? lam[i] : 0.0;
-            if (tail + li <= budget) { tail += li; s = i; } else break;
+    sort_desc(lamw, M, order, evals);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (m == 0) {
+            p.norm2 = gram_trace(p, G, true);
+            p.budget = p.eps * p.eps * p.norm2 / 3.0;
         }
-        if (s == 0 && M > 0 && lam[0] > 0.0 && p.norm2 > 0.0) { s = 1; tail -= (lam[0] > 0 ? lam[0] : 0); if (tail < 0) tail = 0; }
-        int cap = p.cap;
-        if (cap > 0 && s > cap) {
-            for (int i = cap; i < s; ++i) tail += lam[i] > 0.0 ? lam[i] : 0.0;
-            s = cap;
-        }
-        p.discarded += tail;
+        const int s = choose_rank(evals, M, p);
         p.s[m] = s;
-        for (int i = 0; i < M; ++i) evals[i] = lam[i];
-        // projection Znext = Zc x_m S_m^T
-        const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
-        GemmArgs a{};
-        a.alpha = 1.0; a.beta = 0.0; a.nbatch = 1; a.acc = 0;
-        if (m == 0) {        // (s x d1)^T-view: S^T Z_(1)
-            a.M = s; a.N = d2 * d3; a.K = d1;
-            a.A = S; a.lda = n; a.B = Zc; a.ldb = d1; a.C = Znext; a.ldc = s > 0 ? s : 1;
-        } else if (m == 1) { // per slice: Z_i3 S
-            a.M = d1; a.N = s; a.K = d2; a.nbatch = d3;
-            a.A = Zc; a.lda = d1; a.sA = (long long)d1 * d2;
-            a.B = S; a.ldb = n; a.sB = 0;
-            a.C = Znext; a.ldc = d1; a.sC = (long long)d1 * s;
-        } else {             // Zmat S
-            a.M = d1 * d2; a.N = s; a.K = d3;
-            a.A = Zc; a.lda = (long long)d1 * d2; a.B = S; a.ldb = n; a.C = Znext; a.ldc = (long long)d1 * d2;
-        }
-        ga[0] = a;
+        s_s = s;
+    }
+    __syncthreads();
+    const int s = s_s;
+    for (long long e = threadIdx.x; e < (long long)M * s; e += blockDim.x) {
+        const int i = (int)(e % M), c = (int)(e / M);
+        const int src = order[c];
+        const double nn = XtX[src + (long long)src * M];
+        S[i + (long long)c * n] = X[i + (long long)src * M] / (nn > 0 ? sqrt(nn) : 1.0);
+    }
+    if (threadIdx.x == 0) {
+        plan_projection(p, ga, S, n, Zc, Znext, m, s);
         counts[0] = 1;
         p.zdim[m] = s;
     }
+}
+
+// FP32 form, part 1: eigenvectors sorted by the FP32 eigenvalues, projection onto all M of them
+__global__ void __launch_bounds__(1024) select32a_kernel(RoundPlan* plan, GemmArgs* ga, const float* __restrict__ G,
+                                                         const float* __restrict__ V, const float* __restrict__ lam32,
+                                                         double* lamw, int* order, double* sorted, float* Vs,
+                                                         const float* Zc, float* Znext, int m, int* counts) {
+    RoundPlan& p = *plan;
+    const int M = p.gM;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) lamw[i] = lam32[i];
     __syncthreads();
-    // S_m (M x s, ld n): sorted eigenvectors
-    const int s = p.s[m];
-    for (long long e = tid; e < (long long)M * s; e += nt) {
-        int i = (int)(e % M), c = (int)(e / M);
-        S[i + (long long)c * n] = V[i + (long long)order[c] * M];
+    sort_desc(lamw, M, order, sorted);
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)M * M; e += blockDim.x) {
+        const int i = (int)(e % M), c = (int)(e / M);
+        Vs[e] = V[i + (long long)order[c] * M];
     }
+    if (threadIdx.x == 0) {
+        if (m == 0) {
+            p.norm2 = gram_trace(p, G, false);
+            p.budget = p.eps * p.eps * p.norm2 / 3.0;
+        }
+        plan_projection(p, ga, Vs, M > 0 ? M : 1, Zc, Znext, m, M);
+        counts[0] = 1;
+    }
+}
+
+// energies of the M mode-m slices of the projected tensor (dims zdim with zdim[m] = M), one CTA per slice
+__global__ void slice_energy_kernel(const RoundPlan* __restrict__ plan, const float* __restrict__ Z, int m,
+                                    double* __restrict__ energy) {
+    const RoundPlan& p = *plan;
+    const int M = p.gM;
+    const int c = blockIdx.x;
+    if (c >= M) return;
+    const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
+    const int D[3] = {m == 0 ? M : d1, m == 1 ? M : d2, m == 2 ? M : d3};
+    const long long L = (long long)D[0] * D[1] * D[2] / (M > 0 ? M : 1);
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < L; e += blockDim.x) {
+        long long idx;
+        if (m == 0) idx = c + (long long)M * e;
+        else if (m == 1) { const long long i1 = e % D[0], i3 = e / D[0]; idx = i1 + (long long)D[0] * (c + (long long)M * i3); }
+        else idx = e + (long long)D[0] * D[1] * c;
+        const double v = Z[idx];
+        s += v * v;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        energy[c] = t;
+    }
+}
+
+// FP32 form, part 2: keep the slices of largest energy, compact S_m
+__global__ void __launch_bounds__(1024) select32b_kernel(RoundPlan* plan, const double* __restrict__ energy, int* order,
+                                                         double* sorted, const float* __restrict__ Vs, float* S,
+                                                         double* evals, int m) {
+    RoundPlan& p = *plan;
+    const int M = p.gM, n = p.n;
+    __shared__ int s_s;
+    sort_desc(energy, M, order, sorted);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int s = choose_rank(sorted, M, p);
+        p.s[m] = s;
+        s_s = s;
+        for (int i = 0; i < M; ++i) evals[i] = sorted[i];
+    }
+    __syncthreads();
+    const int s = s_s;
+    for (long long e = threadIdx.x; e < (long long)M * s; e += blockDim.x) {
+        const int i = (int)(e % M), c = (int)(e / M);
+        S[i + (long long)c * n] = Vs[i + (long long)order[c] * M];
+    }
+}
+
+// gather the kept slices (order[0..s)) of Zfull (mode m of size M) into Zout (mode m of size s)
+__global__ void gather_slices_kernel(RoundPlan* plan, const float* __restrict__ Zfull, const int* __restrict__ order,
+                                     float* __restrict__ Zout, int m) {
+    RoundPlan& p = *plan;
+    const int M = p.gM, s = p.s[m];
+    const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
+    int D[3] = {d1, d2, d3};
+    D[m] = s;
+    int F[3] = {d1, d2, d3};
+    F[m] = M;
+    const long long tot = (long long)D[0] * D[1] * D[2];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+        long long r = e;
+        int id[3];
+        id[0] = (int)(r % D[0]); r /= D[0];
+        id[1] = (int)(r % D[1]); r /= D[1];
+        id[2] = (int)r;
+        id[m] = order[id[m]];
+        Zout[e] = Zfull[id[0] + (long long)F[0] * (id[1] + (long long)F[1] * id[2])];
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {}
+}
+
+__global__ void set_zdim_kernel(RoundPlan* plan, int m) {
+    if (threadIdx.x == 0) plan->zdim[m] = plan->s[m];
+}
+
+// after a projection onto all gM eigenvectors the working tensor has gM slices in mode m
+__global__ void set_gdim_kernel(RoundPlan* plan, int m) {
+    if (threadIdx.x == 0) plan->zdim[m] = plan->gM;
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -519,6 +562,7 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
                cudaStream_t st) {
     const int n = c->n;
     const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
+    prof_begin(PK_ROUND, st);
     GemmArgs* ga = c->gargs;
     int* counts = reinterpret_cast<int*>(c->scal + 200);   // 8 ints of scratch in the scalar area
     T* Z0 = static_cast<T*>(c->Z0);
@@ -526,10 +570,12 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
     plan_round_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(y->desc), c->plan, ga, n, rc, eps, eps_dev,
                                            c->Rq[0], c->Rq[1], c->Rq[2], y->U[0], y->U[1], y->U[2],
                                            static_cast<T*>(c->T1), static_cast<T*>(c->Wm), counts,
-                                           (long long)c->max_cols * c->n * c->rank_cap);
+                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev());
     TPCG_CHECK_LAUNCH();
     set_c_kernel<<<1, 32, 0, st>>>(ga + 2 * TPCG_MAX_BLOCKS, Z0);
+    TPCG_CHECK_LAUNCH();
     // step 1: QR where k_t < n
+    prof_begin(PK_QR, st);
     {
         size_t sm = (size_t)(n + 40) * sizeof(T);
         qr_kernel<T><<<3, 1024, sm, st>>>(c->plan, static_cast<const T*>(y->U[0]), static_cast<const T*>(y->U[1]),
@@ -540,16 +586,25 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
                                           static_cast<T*>(c->Qq[1]), static_cast<T*>(c->Qq[2]));
         TPCG_CHECK_LAUNCH();
     }
+    prof_end(PK_QR, st);
     // step 2: Z formation
     const int rcap = c->rank_cap;
+    prof_begin(PK_ZBLK, st);
     TPCG_TRY((launch_gemm<T, false, true>(ga, counts, TPCG_MAX_BLOCKS, rcap, rcap, n, st)));
     TPCG_TRY((launch_gemm<T, false, false>(ga + TPCG_MAX_BLOCKS, counts, TPCG_MAX_BLOCKS, 1, n, n * rcap, st)));
+    prof_end(PK_ZBLK, st);
+    prof_begin(PK_ZGEMM, st);
     TPCG_TRY((launch_gemm<T, false, true>(ga + 2 * TPCG_MAX_BLOCKS, nullptr, 1, 1, n * n, n, st)));
+    prof_end(PK_ZGEMM, st);
     // step 3: ST-HOSVD
     T* Zc = Z0;
     T* Zn = Z1;
+    EigWork& w = c->eigw;
+    const int* Mdev = &c->plan->gM;
     for (int m = 0; m < 3; ++m) {
-        plan_gram_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Zc, static_cast<T*>(c->Part), m, MAX_SPLIT, counts);
+        prof_begin(PK_GRAM, st);
+        plan_gram_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Zc, static_cast<T*>(c->Part), m, MAX_SPLIT, counts,
+                                              prof_dev());
         TPCG_CHECK_LAUNCH();
         if (m == 0)
             TPCG_TRY((launch_gemm<T, false, true>(ga, counts, MAX_SPLIT, 1, n, n, st)));
@@ -558,18 +613,54 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
         reduce_partials_kernel<T><<<64, 256, 0, st>>>(static_cast<T*>(c->Part), counts + 1, counts + 2, counts,
                                                       static_cast<T*>(c->Gm), 0, 1.0, 0.0);
         TPCG_CHECK_LAUNCH();
-        // ldc of the reduce target: M (set inside via ldc=0 -> use M)
-        size_t sm = eig_smem_bytes(n, sizeof(T));
-        eig_select_kernel<T><<<1, 1024, sm, st>>>(c->plan, ga, static_cast<T*>(c->Gm), static_cast<T*>(c->Yw[0]),
-                                                  static_cast<T*>(c->S[m]), c->evals, Zc, Zn, m, 60, counts);
-        TPCG_CHECK_LAUNCH();
-        if (m == 0)
-            TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
-        else if (m == 1)
-            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
-        else
-            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
-        T* tmp = Zc; Zc = Zn; Zn = tmp;
+        prof_end(PK_GRAM, st);
+        prof_begin(PK_EIG, st);
+        TPCG_TRY(launch_jacobi32<T>(Mdev, static_cast<const T*>(c->Gm), w.V32, w.A32, w.lam32, n, st));
+        if constexpr (sizeof(T) == 8) {
+            TPCG_TRY(refine_eig64(Mdev, reinterpret_cast<const double*>(c->Gm), w.V32, n, w, 2, st));
+            select64_kernel<<<1, 1024, 0, st>>>(c->plan, ga, reinterpret_cast<const double*>(c->Gm), w.X, w.XtX, w.S,
+                                                w.lam, w.order, reinterpret_cast<double*>(c->S[m]), c->evals,
+                                                reinterpret_cast<const double*>(Zc), reinterpret_cast<double*>(Zn), m,
+                                                counts);
+            TPCG_CHECK_LAUNCH();
+            prof_end(PK_EIG, st);
+            prof_begin(PK_PROJ, st);
+            if (m == 0)
+                TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
+            else if (m == 1)
+                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
+            else
+                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
+            prof_end(PK_PROJ, st);
+            T* tmp = Zc; Zc = Zn; Zn = tmp;
+        } else {
+            select32a_kernel<<<1, 1024, 0, st>>>(c->plan, ga, reinterpret_cast<const float*>(c->Gm), w.V32, w.lam32,
+                                                 w.lam, w.order, w.energy, w.A32, reinterpret_cast<const float*>(Zc),
+                                                 reinterpret_cast<float*>(Zn), m, counts);
+            TPCG_CHECK_LAUNCH();
+            prof_end(PK_EIG, st);
+            prof_begin(PK_PROJ, st);
+            if (m == 0)
+                TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
+            else if (m == 1)
+                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
+            else
+                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
+            // the projected tensor has gM slices in mode m: measure them, keep the largest
+            set_gdim_kernel<<<1, 32, 0, st>>>(c->plan, m);
+            TPCG_CHECK_LAUNCH();
+            slice_energy_kernel<<<n, 256, 0, st>>>(c->plan, reinterpret_cast<const float*>(Zn), m, w.energy);
+            TPCG_CHECK_LAUNCH();
+            select32b_kernel<<<1, 1024, 0, st>>>(c->plan, w.energy, w.order, w.lam, w.A32,
+                                                 reinterpret_cast<float*>(c->S[m]), c->evals, m);
+            TPCG_CHECK_LAUNCH();
+            gather_slices_kernel<<<256, 256, 0, st>>>(c->plan, reinterpret_cast<const float*>(Zn), w.order,
+                                                      reinterpret_cast<float*>(Zc), m);
+            TPCG_CHECK_LAUNCH();
+            set_zdim_kernel<<<1, 32, 0, st>>>(c->plan, m);
+            TPCG_CHECK_LAUNCH();
+            prof_end(PK_PROJ, st);
+        }
     }
     // step 4
     plan_final_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, static_cast<const T*>(c->Qq[0]),
@@ -585,6 +676,7 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
                                              static_cast<T*>(y->core), y->core_cap,
                                              static_cast<TuckerDesc*>(y->desc), info_dev);
     TPCG_CHECK_LAUNCH();
+    prof_end(PK_ROUND, st);
     return TPCG_OK;
 }
 

@@ -20,11 +20,15 @@ STATUS = {0: "OK", 1: "E_INVALID", 2: "E_NOMEM", 3: "E_NOT_CONVERGED", 4: "E_RAN
 
 # the exported symbols declared in include/tpcg.h
 SYMBOLS = [
-    "tpcg_setup", "tpcg_problem_create", "tpcg_problem_get_info", "tpcg_problem_export", "tpcg_problem_destroy",
+    "tpcg_setup", "tpcg_problem_create", "tpcg_problem_get_info", "tpcg_problem_export", "tpcg_problem_export_w",
+    "tpcg_problem_destroy",
     "tpcg_ctx_create", "tpcg_ctx_bytes", "tpcg_ctx_destroy", "tucker_set_plain", "tucker_get_ranks",
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_round", "fd_precond_apply",
     "tpcg_params_default", "tpcg_solve", "tpcg_last_error", "tpcg_version",
+    "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count",
 ]
+PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
+              "round": 9}
 
 
 class TuckerT(C.Structure):
@@ -50,7 +54,7 @@ class ProblemArrays(C.Structure):
 class ProblemInfo(C.Structure):
     _fields_ = [("n", C.c_int), ("p", C.c_int), ("R", C.c_int), ("RP", C.c_int), ("n1", C.c_int),
                 ("n2", C.c_int), ("rf", C.c_int * 3), ("dtype", C.c_int), ("lambda_min", C.c_double),
-                ("lambda_max", C.c_double), ("MP", C.c_double), ("norm_f", C.c_double)]
+                ("lambda_max", C.c_double), ("MP", C.c_double), ("norm_f", C.c_double), ("w_nnz", C.c_int)]
 
 
 class Params(C.Structure):
@@ -88,6 +92,7 @@ def load(build_if_missing: bool = True):
         "tpcg_problem_create": (i, [C.POINTER(ProblemArrays), C.POINTER(vp)]),
         "tpcg_problem_get_info": (i, [vp, C.POINTER(ProblemInfo)]),
         "tpcg_problem_export": (i, [vp] + [vp] * 11),
+        "tpcg_problem_export_w": (i, [vp, vp, vp, vp]),
         "tpcg_problem_destroy": (None, [vp]),
         "tpcg_ctx_create": (i, [i, i, i, i, C.POINTER(vp)]),
         "tpcg_ctx_bytes": (C.c_size_t, [i, i, i, i]),
@@ -103,6 +108,10 @@ def load(build_if_missing: bool = True):
         "tpcg_params_default": (None, [C.POINTER(Params)]),
         "tpcg_solve": (i, [vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp]),
         "tpcg_last_error": (C.c_char_p, []),
+        "tpcg_profile_enable": (i, [i]),
+        "tpcg_profile_reset": (i, []),
+        "tpcg_profile_get": (i, [i, C.POINTER(d), C.POINTER(C.c_longlong), C.POINTER(d), C.POINTER(d)]),
+        "tpcg_launch_count": (C.c_longlong, []),
         "tpcg_version": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
