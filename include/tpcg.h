@@ -41,6 +41,7 @@ extern "C" {
 
 #define TPCG_F64 0
 #define TPCG_F32 1
+#define TPCG_MIXED 2          /* problems/contexts: FP64 tensors and outer loop, FP32 inner TPCG (see tpcg_solve) */
 
 #define TPCG_MAX_BLOCKS 128     /* core blocks of an unrounded Tucker tensor                          */
 #define TPCG_DESC_BYTES 8192    /* bytes of device memory a tucker_t.desc must provide                */
@@ -175,6 +176,8 @@ typedef struct {
     double beta_trunc;  /* beta of eq. rel_tol_iterates                                    (0.1)   */
     int max_it;         /* iteration cap                                                   (500)   */
     int rank_cap;       /* rank cap of every truncation; <= 0: the context's cap                   */
+    double inner_tol;   /* mixed form: relative tolerance of each FP32 inner solve          (1e-2)  */
+    int max_outer;      /* mixed form: cap on FP64 residual refinements                     (6)     */
 } tpcg_params;
 
 typedef struct {
@@ -185,12 +188,20 @@ typedef struct {
     double mem_compression; /* eq. mem_comp, percent                                                */
     int dt_trials;          /* total Alg. 2 truncations                                             */
     int max_rank_seen;      /* largest rank of any rounded iterate                                  */
+    int outer_iters;        /* mixed form: FP64 residual refinements (0 for the single-precision forms) */
+    double true_rel_res;    /* mixed form: ||f - A x|| / ||f|| of the FP64 residual before the last stop test */
 } tpcg_stats;
 
 void tpcg_params_default(tpcg_params* p);
 
 /* Alg. 5 with x_0 = 0: x receives the low-rank solution (plain, caller buffers with cap >= rank_cap and
- * core_cap >= rank_cap^3).  Synchronises the stream once per iteration for the stopping test. */
+ * core_cap >= rank_cap^3).  Synchronises the stream once per iteration for the stopping test.
+ * Mixed form (problem and context created with TPCG_MIXED; x is FP64): iterative refinement around Alg. 5.
+ * Each outer step forms the residual f - A x in FP64 (banded products and the Z formation of Alg. 1 in
+ * FP64, so the cancellation is exact to FP64 and ||Z|| is the true residual norm), truncates it in FP32
+ * to 0.1 inner_tol, solves A d = r by Alg. 5 in FP32 to inner_tol (dynamic-truncation floor 0.1 inner_tol),
+ * and accumulates x += d as an FP64 Tucker sum; x is truncated once in FP64 (tolerance tol / 10) at the end.
+ * The stopping test uses the true FP64 residual. */
 int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
 
 /* ------------------------------------------------------------------------------------ profiling */

@@ -13,7 +13,7 @@ import torch
 from . import lib as L
 from .lib import check
 
-_TORCH_DT = {L.F64: torch.float64, L.F32: torch.float32}
+_TORCH_DT = {L.F64: torch.float64, L.F32: torch.float32, L.MIXED: torch.float64}
 
 
 def _stream(stream=None):
@@ -38,7 +38,8 @@ class Tucker:
         self.U = [torch.zeros((cap, n), dtype=td, device=device) for _ in range(3)]   # column-major n x cap
         self.core = torch.zeros(max(core_cap, 1), dtype=td, device=device)
         self.desc = torch.zeros(L.DESC_BYTES, dtype=torch.uint8, device=device)
-        self.t = L.TuckerT(dtype, n, cap, core_cap, (C.c_void_p * 3)(*[u.data_ptr() for u in self.U]),
+        sdt = L.F64 if dtype == L.MIXED else dtype      # tensors of a mixed-precision problem are FP64
+        self.t = L.TuckerT(sdt, n, cap, core_cap, (C.c_void_p * 3)(*[u.data_ptr() for u in self.U]),
                            self.core.data_ptr(), self.desc.data_ptr())
 
     @property

@@ -1,5 +1,7 @@
 // C ABI entry points: contexts, problems, Tucker operations and the TPCG driver (Alg. 5).
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -158,6 +160,8 @@ extern "C" void tpcg_params_default(tpcg_params* p) {
     p->beta_trunc = 0.1;
     p->max_it = 500;
     p->rank_cap = 0;
+    p->inner_tol = 1e-2;
+    p->max_outer = 6;
 }
 
 // ======================================================================================= contexts
@@ -187,22 +191,38 @@ static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) 
 
 extern "C" size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype) {
     size_t sizes[64];
+    if (dtype == TPCG_MIXED)
+        return ctx_layout(n, max_cols, rank_cap, TPCG_F64, sizes) + ctx_layout(n, max_cols, rank_cap, TPCG_F32, sizes);
     return ctx_layout(n, max_cols, rank_cap, dtype, sizes);
 }
 
 extern "C" void tpcg_ctx_destroy(tpcg_ctx c) {
     if (!c) return;
+    if (c->lo) tpcg_ctx_destroy(c->lo);
     for (void* p : c->owned) cudaFree(p);
     delete c;
 }
 
 extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpcg_ctx* out) {
+    if (dtype == TPCG_MIXED) {
+        tpcg_ctx hi = nullptr, lo = nullptr;
+        TPCG_TRY(tpcg_ctx_create(n, max_cols, rank_cap, TPCG_F64, &hi));
+        int s = tpcg_ctx_create(n, max_cols, rank_cap, TPCG_F32, &lo);
+        if (s != TPCG_OK) {
+            tpcg_ctx_destroy(hi);
+            return s;
+        }
+        hi->lo = lo;
+        *out = hi;
+        return TPCG_OK;
+    }
     if (!out || n < 2 || n > 1024 || max_cols < 1 || rank_cap < 1 || rank_cap > n || rank_cap > 256 ||
         (dtype != TPCG_F64 && dtype != TPCG_F32)) {
         set_error("tpcg_ctx_create: invalid arguments (need 2 <= n <= 1024, 1 <= rank_cap <= min(n, 256))");
         return TPCG_E_INVALID;
     }
     tpcg_ctx c = new tpcg_ctx_s();
+    c->lo = nullptr;
     c->n = n;
     c->max_cols = max_cols;
     c->rank_cap = rank_cap;
@@ -318,6 +338,7 @@ static void host_orthonormalize_rhs(tpcg_problem pb) {
 
 extern "C" void tpcg_problem_destroy(tpcg_problem pb) {
     if (!pb) return;
+    if (pb->lo) tpcg_problem_destroy(pb->lo);
     void* ptrs[] = {pb->d_bands, pb->d_w, pb->d_lam, pb->d_mu, pb->d_wrow, pb->d_wcol, pb->d_wval, pb->d_wtrow,
                     pb->d_wtcol, pb->d_wtval, pb->d_v2u2, pb->d_dst, pb->d_omega, pb->d_alpha, pb->d_scal,
                     pb->d_f_store[0], pb->d_f_store[1], pb->d_f_store[2], pb->d_f_store[3], pb->d_f_store[4]};
@@ -328,6 +349,21 @@ extern "C" void tpcg_problem_destroy(tpcg_problem pb) {
 
 extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* out) {
     if (!a || !out) return TPCG_E_INVALID;
+    if (a->dtype == TPCG_MIXED) {
+        tpcg_problem_arrays b = *a;
+        b.dtype = TPCG_F64;
+        tpcg_problem hi = nullptr, lo = nullptr;
+        TPCG_TRY(tpcg_problem_create(&b, &hi));
+        b.dtype = TPCG_F32;
+        int s = tpcg_problem_create(&b, &lo);
+        if (s != TPCG_OK) {
+            tpcg_problem_destroy(hi);
+            return s;
+        }
+        hi->lo = lo;
+        *out = hi;
+        return TPCG_OK;
+    }
     const int n = a->n, p = a->p;
     if (n < 2 || p < 1 || p > 5 || a->R < 1 || a->R > TPCG_MAX_BLOCKS - 1 || a->n1 < 1 || a->n2 < 0 ||
         a->n1 + a->n2 != n || a->RP < 1 || a->RP > TPCG_MAX_BLOCKS || (a->dtype != TPCG_F64 && a->dtype != TPCG_F32) ||
@@ -342,6 +378,7 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
             return TPCG_E_INVALID;
         }
     tpcg_problem pb = new tpcg_problem_s();
+    pb->lo = nullptr;
     memset(pb->d_f_store, 0, sizeof(pb->d_f_store));
     pb->d_bands = pb->d_w = nullptr;
     pb->d_lam = pb->d_mu = pb->d_wval = pb->d_wtval = pb->d_v2u2 = pb->d_dst = nullptr;
@@ -624,9 +661,24 @@ static int ensure_tensors(tpcg_ctx c) {
     return TPCG_OK;
 }
 
+// ||f - A x|| / ||f|| of a solution x, in the working precision of the problem (no truncation)
+template <typename T>
+static int true_residual(tpcg_problem pb, tpcg_ctx c, const tucker_t* x, tucker_t* work, double* rel, cudaStream_t s) {
+    TPCG_TRY(apply_impl<T>(pb, x, work, true, s));
+    double* d = c->scal + 130;
+    TPCG_TRY(tensor_norm2<T>(c, work, d, s));
+    double h = 0.0;
+    TPCG_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPCG_CUDA(cudaStreamSynchronize(s));
+    *rel = pb->norm_f > 0 ? sqrt(std::max(h, 0.0)) / pb->norm_f : 0.0;
+    return TPCG_OK;
+}
+
+// Alg. 5 for the right-hand side `rhs` (the problem's f~ unless given)
 template <typename T>
 static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
-                      cudaStream_t s) {
+                      cudaStream_t s, const tucker_t* rhs = nullptr) {
+    if (!rhs) rhs = &pb->f;
     TPCG_TRY(ensure_tensors(c));
     const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
     double* sc = c->scal;
@@ -649,7 +701,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     };
     // x_0 = 0, r_0 = f
     TPCG_TRY(set_zero(x, s));
-    TPCG_TRY(copy_tensor_impl<T>(&pb->f, r, c->n, c->max_cols, s));
+    TPCG_TRY(copy_tensor_impl<T>(rhs, r, c->n, c->max_cols, s));
     TPCG_TRY(dot_impl<T>(c, r, r, sc + S_RR, s));
     launch_scalar(OP_INIT, sc, dprm, s);
     // z_0 = T(P^-1 r_0, eta_0), p_0 = z_0, q_0 = T(A p_0, eta_0), xi_0 = p_0 . q_0
@@ -664,9 +716,25 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     int k = 0;
     int status = TPCG_OK;
     int trials_total = 0;
+    const char* tr = getenv("TPCG_TRACE");
+    const bool trace = tr && tr[0] == '1';
     for (;;) {
         TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
         TPCG_CUDA(cudaStreamSynchronize(s));
+        if (trace) {
+            int rx[3], rr[3], rz[3], rp[3], rq[3], nb;
+            tucker_get_ranks(x, rx, &nb, s);
+            tucker_get_ranks(r, rr, &nb, s);
+            tucker_get_ranks(z, rz, &nb, s);
+            tucker_get_ranks(p, rp, &nb, s);
+            tucker_get_ranks(q, rq, &nb, s);
+            fprintf(stderr,
+                    "tpcg k=%d res=%.3e eta=%.2e eps=%.2e v=%.4f omega=%.3e xi=%.3e trials=%d "
+                    "rank x=(%d,%d,%d) r=(%d,%d,%d) z=(%d,%d,%d) p=(%d,%d,%d) q=(%d,%d,%d)\n",
+                    k, host[S_NR] / host[S_NF], host[S_ETA], host[S_EPS], host[S_V], host[S_OMEGA], host[S_XI],
+                    trials_total, rx[0], rx[1], rx[2], rr[0], rr[1], rr[2], rz[0], rz[1], rz[2], rp[0], rp[1], rp[2],
+                    rq[0], rq[1], rq[2]);
+        }
         if (host[S_BAD] != 0.0) { status = TPCG_E_BREAKDOWN; break; }
         if (host[S_STOP] != 0.0) break;
         if (k >= prm->max_it) { status = TPCG_E_NOT_CONVERGED; break; }
@@ -690,7 +758,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         }
         std::swap(x, big2);
         // r_{k+1} = T(f - A x_{k+1}, eta_k); eta_{k+1}
-        TPCG_TRY(apply_impl<T>(pb, x, big, true, s));
+        TPCG_TRY(apply_impl<T>(pb, x, big, true, s, rhs));
         TPCG_TRY(round_to(r, eta));
         TPCG_TRY(dot_impl<T>(c, r, r, sc + S_RR, s));
         launch_scalar(OP_RES, sc, dprm, s);
@@ -709,8 +777,10 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         launch_scalar(OP_XI, sc, dprm, s);
         ++k;
     }
-    // copy x into the caller's tensor
+    // copy x into the caller's tensor; measure its true residual (the problem's own rhs only)
     TPCG_TRY(copy_tensor_impl<T>(x, xout, c->n, xout->cap, s));
+    double true_rel = -1.0;
+    if (rhs == &pb->f) TPCG_TRY(true_residual<T>(pb, c, x, big, &true_rel, s));
     // (the internal tensors all have the same capacities, so their roles need no restoring)
     int rk[3] = {0, 0, 0};
     int nb = 0;
@@ -725,6 +795,82 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         st->mem_compression = ((double)rk[0] * rk[1] * rk[2] + n * (rk[0] + rk[1] + rk[2])) / (n * n * n) * 100.0;
         st->dt_trials = trials_total;
         st->max_rank_seen = std::max(rk[0], std::max(rk[1], rk[2]));
+        st->outer_iters = 0;
+        st->true_rel_res = true_rel;
+    }
+    return status;
+}
+
+// Mixed form: iterative refinement with FP64 residuals around FP32 Alg. 5 (see tpcg.h)
+static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
+                       cudaStream_t s) {
+    tpcg_problem pb32 = pb->lo;
+    tpcg_ctx c32 = c->lo;
+    TPCG_TRY(ensure_tensors(c));
+    TPCG_TRY(ensure_tensors(c32));
+    const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
+    tucker_t* xacc = &c->tens[0];
+    tucker_t* xtmp = &c->tens[1];
+    tucker_t* big = &c->tens[2];
+    tucker_t* r32 = &c32->tens[8];
+    tucker_t* d32 = &c32->tens[9];
+    const int max_outer = std::min(std::max(prm->max_outer, 1), 7);
+    const double nf = pb->norm_f;
+    double* info = c->scal + 120;   // 6 doubles written by the rounding
+    const char* tr = getenv("TPCG_TRACE");
+    const bool trace = tr && tr[0] == '1';
+    TPCG_TRY(set_zero(xacc, s));
+    tpcg_params in = *prm;
+    in.tol = prm->inner_tol;
+    in.eps_min = 0.1 * prm->inner_tol;
+    in.rank_cap = rc;
+    int status = TPCG_E_NOT_CONVERGED, outer = 0, inner_total = 0, trials = 0;
+    double rel = 1.0;
+    for (outer = 0; outer <= max_outer; ++outer) {
+        // r = f - A x in FP64, truncated to 0.1 inner_tol in FP32
+        TPCG_TRY(apply_impl<double>(pb, xacc, big, true, s));
+        TPCG_TRY(round_mixed(c, c32, big, r32, 0.1 * prm->inner_tol, nullptr, rc, info, s));
+        double h[6];
+        TPCG_CUDA(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
+        TPCG_CUDA(cudaStreamSynchronize(s));
+        rel = nf > 0 ? sqrt(std::max(h[0], 0.0)) / nf : 0.0;
+        if (trace) fprintf(stderr, "mixed outer=%d true_res=%.3e r-rank=(%g,%g,%g)\n", outer, rel, h[2], h[3], h[4]);
+        if (!(rel == rel)) { status = TPCG_E_BREAKDOWN; break; }
+        if (rel <= prm->tol) { status = TPCG_OK; break; }
+        if (outer == max_outer) break;
+        // keep the next residual within the block list and the factor capacity: compress x in FP64 first
+        const int rfmax = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
+        if ((outer + 2) * pb->R + 1 > TPCG_MAX_BLOCKS || pb->R * (outer + 2) * rc + rfmax > c->max_cols)
+            TPCG_TRY(round_impl<double>(c, xacc, 0.01 * prm->tol, nullptr, rc, nullptr, s));
+        tpcg_stats sin{};
+        int si = solve_impl<float>(pb32, c32, &in, d32, &sin, s, r32);
+        inner_total += sin.iters;
+        trials += sin.dt_trials;
+        if (si != TPCG_OK && si != TPCG_E_NOT_CONVERGED) { status = si; break; }
+        tucker_t* dco = &c->tens[3 + outer];
+        TPCG_TRY(promote_tensor(d32, dco, s));
+        TPCG_TRY(axpby_impl<double>(1.0, nullptr, xacc, 1.0, nullptr, dco, xtmp, nullptr, s));
+        std::swap(xacc, xtmp);
+    }
+    // one FP64 truncation of the accumulated solution, then its true residual
+    TPCG_TRY(round_impl<double>(c, xacc, 0.01 * prm->tol, nullptr, rc, nullptr, s));
+    TPCG_TRY(copy_tensor_impl<double>(xacc, xout, c->n, xout->cap, s));
+    double true_rel = rel;
+    TPCG_TRY(true_residual<double>(pb, c, xacc, big, &true_rel, s));
+    if (status == TPCG_OK && true_rel > prm->tol) status = TPCG_E_NOT_CONVERGED;
+    int rk[3] = {0, 0, 0}, nb = 0;
+    TPCG_TRY(tucker_get_ranks(xout, rk, &nb, s));
+    if (st) {
+        st->iters = inner_total;
+        st->status = status;
+        st->rel_res = rel;
+        st->true_rel_res = true_rel;
+        st->outer_iters = outer;
+        for (int t = 0; t < 3; ++t) st->rank[t] = rk[t];
+        const double n = c->n;
+        st->mem_compression = ((double)rk[0] * rk[1] * rk[2] + n * (rk[0] + rk[1] + rk[2])) / (n * n * n) * 100.0;
+        st->dt_trials = trials;
+        st->max_rank_seen = std::max(rk[0], std::max(rk[1], rk[2]));
     }
     return status;
 }
@@ -737,6 +883,16 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
         return TPCG_E_INVALID;
     }
     TPCG_TRY(check_tensor(x, pb->n, pb->dtype, "tpcg_solve x"));
+    if (pb->lo || c->lo) {
+        if (!pb->lo || !c->lo || pb->lo->n != c->lo->n) {
+            set_error("tpcg_solve: the mixed form needs a TPCG_MIXED problem and a TPCG_MIXED context");
+            return TPCG_E_INVALID;
+        }
+        if (c->max_cols < 2 * pb->R * c->rank_cap + 8) {
+            set_error("tpcg_solve: mixed form needs max_cols >= 2 R rank_cap + 8 (residual of accumulated corrections)");
+            return TPCG_E_INVALID;
+        }
+    }
     const int rfmax = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
     const int need = std::max(pb->R * c->rank_cap + rfmax, std::max(pb->RP * c->rank_cap, 2 * c->rank_cap));
     if (c->max_cols < need) {
@@ -744,5 +900,6 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
                   std::to_string(need));
         return TPCG_E_INVALID;
     }
+    if (pb->lo) return solve_mixed(pb, c, prm, x, st, S(stream));
     return by_dtype(pb->dtype, [&](auto z) { return solve_impl<decltype(z)>(pb, c, prm, x, st, S(stream)); });
 }

@@ -112,7 +112,6 @@ struct Buf {
 
 }  // namespace tpcg
 
-namespace tpcg { struct EigWork; }
 #include "eig.cuh"
 
 struct tpcg_ctx_s {
@@ -142,6 +141,7 @@ struct tpcg_ctx_s {
     tucker_t tens[10];
     bool have_tens;
     int tens_cap;
+    tpcg_ctx_s* lo;      // FP32 companion of a mixed-precision context (else null)
 };
 
 struct tpcg_problem_s {
@@ -169,4 +169,5 @@ struct tpcg_problem_s {
     double* d_omega;     // RP
     double* d_alpha;     // RP
     double* d_scal;      // problem scalars (lambda_min, ...)
+    tpcg_problem_s* lo;  // FP32 companion of a mixed-precision problem (else null)
 };

@@ -1,35 +1,27 @@
-// Eigensolver pieces used by the ST-HOSVD step of the rounding (see eig.cu).
+// Eigensolver of the mode Grams used by the ST-HOSVD step of the rounding (see eig.cu).
 #pragma once
 
-#include "common.cuh"
+#include <vector>
+
 
 namespace tpcg {
 
-// FP64 refinement work area (all M x M doubles with ld M, M <= n)
+struct RoundPlan;
+
+constexpr int SMAX_EIG = 1024;   // largest Gram (= n) the one-CTA eigensolver accepts
+
 struct EigWork {
-    double* X;
-    double* Xn;
-    double* XtX;
-    double* AX;
-    double* S;
-    double* E;
-    double* lam;       // n
-    double* Part;      // 2 * 32 * n * n partial products
-    GemmArgs* ga;      // 256 slots
-    int* counts;       // 8 ints
-    float* V32;        // n * n
-    float* A32;        // n * n scratch when the matrix does not fit shared memory
-    float* lam32;      // n
-    double* energy;    // n slice energies (FP32 form)
-    int* order;        // n kept/sorted slice indices
+    void* Aw;        // n (n + 1) elements: the Gram when it does not fit shared memory
+    void* Vw;        // n (n + 1) elements: the eigenvectors when they do not fit shared memory
 };
 
 size_t eig_work_bytes(int n);
 int eig_work_alloc(EigWork* w, int n, std::vector<void*>* owned);
 
-template <typename Tin>
-int launch_jacobi32(const int* Mdev, const Tin* G, float* V, float* Ascratch, float* lam, int n, cudaStream_t st);
-
-int refine_eig64(const int* Mdev, const double* A, const float* V32, int n, EigWork& w, int iters, cudaStream_t st);
+// Eigen-decomposition (Jacobi) of the plan's current Gram G (gM x gM, ld gM), truncation rule of mode m, kept
+// eigenvectors (orthonormal) into S (ld n); plan.s[m], plan.discarded (and for m = 0 plan.norm2/budget)
+// are updated on the device.
+template <typename T>
+int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int m, int n, cudaStream_t st);
 
 }  // namespace tpcg

@@ -8,8 +8,16 @@ namespace tpcg {
 template <typename T>
 int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
                cudaStream_t st);
+int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
+                double* info_dev, cudaStream_t st);
+// ||y||^2 of any (block) tensor by the Z formation of Alg. 1
 template <typename T>
-int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st);
+int tensor_norm2(tpcg_ctx c, tucker_t* y, double* out_dev, cudaStream_t st);
+// copy a plain FP32 tensor into an FP64 tensor (factors, core, descriptor)
+int promote_tensor(const tucker_t* src32, tucker_t* dst64, cudaStream_t st);
+template <typename T>
+int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st,
+               const tucker_t* rhs = nullptr);
 template <typename T>
 int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev, const tucker_t* y,
                tucker_t* z, int* err_dev, cudaStream_t st);

@@ -109,10 +109,10 @@ __global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const doubl
 }
 
 template <typename T>
-int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st) {
+int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st, const tucker_t* rhs) {
     const int n = pb->n;
     dim3 grid((n + 127) / 128, pb->R + (residual ? 1 : 0), 3);
-    const tucker_t* f = &pb->f;
+    const tucker_t* f = rhs ? rhs : &pb->f;
     prof_begin(PK_APPLY, st);
     apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
                                           static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
@@ -132,8 +132,8 @@ int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, c
     prof_end(PK_APPLY, st);
     return TPCG_OK;
 }
-template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t);
-template int apply_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t);
+template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*);
+template int apply_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*);
 
 // --------------------------------------------------------------------------------------------------
 // z = a x + b y: concatenated factors, block lists shifted and scaled (Sec. 2.3, sum).
@@ -543,5 +543,46 @@ int copy_tensor_impl(const tucker_t* src, tucker_t* dst, int n, int cap, cudaStr
 }
 template int copy_tensor_impl<double>(const tucker_t*, tucker_t*, int, int, cudaStream_t);
 template int copy_tensor_impl<float>(const tucker_t*, tucker_t*, int, int, cudaStream_t);
+
+// FP32 plain tensor -> FP64 tensor
+__global__ void promote_kernel(const TuckerDesc* __restrict__ sd, const float* S0, const float* S1, const float* S2,
+                               const float* Sc, double* D0, double* D1, double* D2, double* Dc, TuckerDesc* dd, int n,
+                               int cap, long long ccap) {
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+    const float* S[3] = {S0, S1, S2};
+    double* D[3] = {D0, D1, D2};
+    const int r[3] = {sd->rank[0], sd->rank[1], sd->rank[2]};
+    const bool ok = sd->nblk == 1 && r[0] <= cap && r[1] <= cap && r[2] <= cap &&
+                    (long long)r[0] * r[1] * r[2] <= ccap;
+    if (!ok) {
+        if (gt == 0) { dd->nblk = 0; dd->rank[0] = dd->rank[1] = dd->rank[2] = 0; }
+        return;
+    }
+    for (int t = 0; t < 3; ++t)
+        for (long long e = gt; e < (long long)n * r[t]; e += gs) D[t][e] = (double)S[t][e];
+    const float* core = static_cast<const float*>(sd->blk[0].core);
+    const double sc = sd->blk[0].scale;
+    for (long long e = gt; e < (long long)r[0] * r[1] * r[2]; e += gs) Dc[e] = sc * (double)core[e];
+    if (gt == 0) {
+        dd->nblk = 1;
+        for (int t = 0; t < 3; ++t) {
+            dd->rank[t] = r[t];
+            dd->blk[0].off[t] = 0;
+            dd->blk[0].r[t] = r[t];
+        }
+        dd->blk[0].core = Dc;
+        dd->blk[0].scale = 1.0;
+    }
+}
+
+int promote_tensor(const tucker_t* src32, tucker_t* dst64, cudaStream_t st) {
+    promote_kernel<<<128, 256, 0, st>>>(static_cast<const TuckerDesc*>(src32->desc), static_cast<const float*>(src32->U[0]),
+                                        static_cast<const float*>(src32->U[1]), static_cast<const float*>(src32->U[2]),
+                                        nullptr, static_cast<double*>(dst64->U[0]), static_cast<double*>(dst64->U[1]),
+                                        static_cast<double*>(dst64->U[2]), static_cast<double*>(dst64->core),
+                                        static_cast<TuckerDesc*>(dst64->desc), dst64->n, dst64->cap, dst64->core_cap);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
 
 }  // namespace tpcg

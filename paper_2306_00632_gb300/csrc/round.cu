@@ -271,8 +271,8 @@ __global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* 
 }
 
 // --------------------------------------------------------------------------------------------------
-// Truncation rule of ST-HOSVD on mode m and the plan of the projection Z x_m S_m^T.
-// FP64 form: eigenpairs refined in FP64; lambda_i = (X^T A X)_ii / (X^T X)_ii.
+// Projection Z x_m S_m^T onto the s_m kept eigenvectors of mode m (the truncation rule itself runs in the
+// eigensolver, eig.cu).
 // --------------------------------------------------------------------------------------------------
 __device__ void plan_projection(RoundPlan& p, GemmArgs* ga, const void* S, long long ldS, const void* Zc, void* Znext,
                                 int m, int s) {
@@ -295,197 +295,17 @@ __device__ void plan_projection(RoundPlan& p, GemmArgs* ga, const void* S, long 
     ga[0] = a;
 }
 
-__device__ double gram_trace(const RoundPlan& p, const void* G, bool dbl) {
-    double tr = 0.0;
-    const int M = p.gM;
-    for (int i = 0; i < M; ++i)
-        tr += dbl ? static_cast<const double*>(G)[i + (long long)i * M] : (double)static_cast<const float*>(G)[i + (long long)i * M];
-    return tr;
-}
-
-// rank-count sort (decreasing) of M values into order[], one thread per element
-__device__ void sort_desc(const double* v, int M, int* order, double* sorted) {
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const double vi = v[i];
-        int rk = 0;
-        for (int j = 0; j < M; ++j) {
-            const double vj = v[j];
-            if (vj > vi || (vj == vi && j < i)) ++rk;
-        }
-        order[rk] = i;
-        sorted[rk] = vi;
-    }
-}
-
-// smallest s whose discarded (clamped) values sum to <= budget, then the cap; returns s, adds the tail
-__device__ int choose_rank(const double* sorted, int M, RoundPlan& p) {
-    double tail = 0.0;
-    int s = M;
-    for (int i = M - 1; i >= 0; --i) {
-        const double li = sorted[i] > 0.0 ? sorted[i] : 0.0;
-        if (tail + li <= p.budget) { tail += li; s = i; } else break;
-    }
-    if (s == 0 && M > 0 && sorted[0] > 0.0 && p.norm2 > 0.0) {
-        s = 1;
-        tail -= sorted[0] > 0 ? sorted[0] : 0.0;
-        if (tail < 0) tail = 0;
-    }
-    if (p.cap > 0 && s > p.cap) {
-        for (int i = p.cap; i < s; ++i) tail += sorted[i] > 0.0 ? sorted[i] : 0.0;
-        s = p.cap;
-    }
-    p.discarded += tail;
-    return s;
-}
-
-__global__ void __launch_bounds__(1024) select64_kernel(RoundPlan* plan, GemmArgs* ga, const double* __restrict__ G,
-                                                        const double* __restrict__ X, const double* __restrict__ XtX,
-                                                        const double* __restrict__ Sm, double* lamw, int* order,
-                                                        double* S, double* evals, const double* Zc, double* Znext, int m,
-                                                        int* counts) {
+// plan of the projection onto the kept eigenvectors (after the eigensolver set plan.s[m])
+template <typename T>
+__global__ void plan_proj_kernel(RoundPlan* plan, GemmArgs* ga, const T* S, const T* Zc, T* Znext, int m, int* counts) {
+    if (threadIdx.x != 0) return;
     RoundPlan& p = *plan;
-    const int M = p.gM, n = p.n;
-    __shared__ int s_s;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        const double nn = XtX[i + (long long)i * M];
-        lamw[i] = nn > 0 ? Sm[i + (long long)i * M] / nn : 0.0;
-    }
-    __syncthreads();
-    sort_desc(lamw, M, order, evals);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (m == 0) {
-            p.norm2 = gram_trace(p, G, true);
-            p.budget = p.eps * p.eps * p.norm2 / 3.0;
-        }
-        const int s = choose_rank(evals, M, p);
-        p.s[m] = s;
-        s_s = s;
-    }
-    __syncthreads();
-    const int s = s_s;
-    for (long long e = threadIdx.x; e < (long long)M * s; e += blockDim.x) {
-        const int i = (int)(e % M), c = (int)(e / M);
-        const int src = order[c];
-        const double nn = XtX[src + (long long)src * M];
-        S[i + (long long)c * n] = X[i + (long long)src * M] / (nn > 0 ? sqrt(nn) : 1.0);
-    }
-    if (threadIdx.x == 0) {
-        plan_projection(p, ga, S, n, Zc, Znext, m, s);
-        counts[0] = 1;
-        p.zdim[m] = s;
-    }
-}
-
-// FP32 form, part 1: eigenvectors sorted by the FP32 eigenvalues, projection onto all M of them
-__global__ void __launch_bounds__(1024) select32a_kernel(RoundPlan* plan, GemmArgs* ga, const float* __restrict__ G,
-                                                         const float* __restrict__ V, const float* __restrict__ lam32,
-                                                         double* lamw, int* order, double* sorted, float* Vs,
-                                                         const float* Zc, float* Znext, int m, int* counts) {
-    RoundPlan& p = *plan;
-    const int M = p.gM;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) lamw[i] = lam32[i];
-    __syncthreads();
-    sort_desc(lamw, M, order, sorted);
-    __syncthreads();
-    for (long long e = threadIdx.x; e < (long long)M * M; e += blockDim.x) {
-        const int i = (int)(e % M), c = (int)(e / M);
-        Vs[e] = V[i + (long long)order[c] * M];
-    }
-    if (threadIdx.x == 0) {
-        if (m == 0) {
-            p.norm2 = gram_trace(p, G, false);
-            p.budget = p.eps * p.eps * p.norm2 / 3.0;
-        }
-        plan_projection(p, ga, Vs, M > 0 ? M : 1, Zc, Znext, m, M);
-        counts[0] = 1;
-    }
-}
-
-// energies of the M mode-m slices of the projected tensor (dims zdim with zdim[m] = M), one CTA per slice
-__global__ void slice_energy_kernel(const RoundPlan* __restrict__ plan, const float* __restrict__ Z, int m,
-                                    double* __restrict__ energy) {
-    const RoundPlan& p = *plan;
-    const int M = p.gM;
-    const int c = blockIdx.x;
-    if (c >= M) return;
-    const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
-    const int D[3] = {m == 0 ? M : d1, m == 1 ? M : d2, m == 2 ? M : d3};
-    const long long L = (long long)D[0] * D[1] * D[2] / (M > 0 ? M : 1);
-    double s = 0.0;
-    for (long long e = threadIdx.x; e < L; e += blockDim.x) {
-        long long idx;
-        if (m == 0) idx = c + (long long)M * e;
-        else if (m == 1) { const long long i1 = e % D[0], i3 = e / D[0]; idx = i1 + (long long)D[0] * (c + (long long)M * i3); }
-        else idx = e + (long long)D[0] * D[1] * c;
-        const double v = Z[idx];
-        s += v * v;
-    }
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        energy[c] = t;
-    }
-}
-
-// FP32 form, part 2: keep the slices of largest energy, compact S_m
-__global__ void __launch_bounds__(1024) select32b_kernel(RoundPlan* plan, const double* __restrict__ energy, int* order,
-                                                         double* sorted, const float* __restrict__ Vs, float* S,
-                                                         double* evals, int m) {
-    RoundPlan& p = *plan;
-    const int M = p.gM, n = p.n;
-    __shared__ int s_s;
-    sort_desc(energy, M, order, sorted);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int s = choose_rank(sorted, M, p);
-        p.s[m] = s;
-        s_s = s;
-        for (int i = 0; i < M; ++i) evals[i] = sorted[i];
-    }
-    __syncthreads();
-    const int s = s_s;
-    for (long long e = threadIdx.x; e < (long long)M * s; e += blockDim.x) {
-        const int i = (int)(e % M), c = (int)(e / M);
-        S[i + (long long)c * n] = Vs[i + (long long)order[c] * M];
-    }
-}
-
-// gather the kept slices (order[0..s)) of Zfull (mode m of size M) into Zout (mode m of size s)
-__global__ void gather_slices_kernel(RoundPlan* plan, const float* __restrict__ Zfull, const int* __restrict__ order,
-                                     float* __restrict__ Zout, int m) {
-    RoundPlan& p = *plan;
-    const int M = p.gM, s = p.s[m];
-    const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
-    int D[3] = {d1, d2, d3};
-    D[m] = s;
-    int F[3] = {d1, d2, d3};
-    F[m] = M;
-    const long long tot = (long long)D[0] * D[1] * D[2];
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-        long long r = e;
-        int id[3];
-        id[0] = (int)(r % D[0]); r /= D[0];
-        id[1] = (int)(r % D[1]); r /= D[1];
-        id[2] = (int)r;
-        id[m] = order[id[m]];
-        Zout[e] = Zfull[id[0] + (long long)F[0] * (id[1] + (long long)F[1] * id[2])];
-    }
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {}
+    plan_projection(p, ga, S, p.n, Zc, Znext, m, p.s[m]);
+    counts[0] = 1;
 }
 
 __global__ void set_zdim_kernel(RoundPlan* plan, int m) {
     if (threadIdx.x == 0) plan->zdim[m] = plan->s[m];
-}
-
-// after a projection onto all gM eigenvectors the working tensor has gM slices in mode m
-__global__ void set_gdim_kernel(RoundPlan* plan, int m) {
-    if (threadIdx.x == 0) plan->zdim[m] = plan->gM;
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -557,12 +377,10 @@ __global__ void final_copy_kernel(const RoundPlan* __restrict__ plan, const T* S
 // --------------------------------------------------------------------------------------------------
 // Host driver
 // --------------------------------------------------------------------------------------------------
+// Alg. 1 steps 1-2 (planner, QR of the factors, Z formation) into c->Z0 and c->plan.
 template <typename T>
-int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
-               cudaStream_t st) {
+int round_stage12(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rc, cudaStream_t st) {
     const int n = c->n;
-    const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
-    prof_begin(PK_ROUND, st);
     GemmArgs* ga = c->gargs;
     int* counts = reinterpret_cast<int*>(c->scal + 200);   // 8 ints of scratch in the scalar area
     T* Z0 = static_cast<T*>(c->Z0);
@@ -596,11 +414,21 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
     prof_begin(PK_ZGEMM, st);
     TPCG_TRY((launch_gemm<T, false, true>(ga + 2 * TPCG_MAX_BLOCKS, nullptr, 1, 1, n * n, n, st)));
     prof_end(PK_ZGEMM, st);
+    return TPCG_OK;
+}
+
+// Alg. 1 steps 3-4 (ST-HOSVD of c->Z0 under c->plan, new factors Q S and core) into y.
+template <typename T>
+int round_stage34(tpcg_ctx c, tucker_t* y, double* info_dev, cudaStream_t st) {
+    const int n = c->n;
+    GemmArgs* ga = c->gargs;
+    int* counts = reinterpret_cast<int*>(c->scal + 200);
+    T* Z0 = static_cast<T*>(c->Z0);
+    T* Z1 = static_cast<T*>(c->Z1);
+    const int rcap = c->rank_cap;
     // step 3: ST-HOSVD
     T* Zc = Z0;
     T* Zn = Z1;
-    EigWork& w = c->eigw;
-    const int* Mdev = &c->plan->gM;
     for (int m = 0; m < 3; ++m) {
         prof_begin(PK_GRAM, st);
         plan_gram_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Zc, static_cast<T*>(c->Part), m, MAX_SPLIT, counts,
@@ -615,52 +443,22 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
         TPCG_CHECK_LAUNCH();
         prof_end(PK_GRAM, st);
         prof_begin(PK_EIG, st);
-        TPCG_TRY(launch_jacobi32<T>(Mdev, static_cast<const T*>(c->Gm), w.V32, w.A32, w.lam32, n, st));
-        if constexpr (sizeof(T) == 8) {
-            TPCG_TRY(refine_eig64(Mdev, reinterpret_cast<const double*>(c->Gm), w.V32, n, w, 2, st));
-            select64_kernel<<<1, 1024, 0, st>>>(c->plan, ga, reinterpret_cast<const double*>(c->Gm), w.X, w.XtX, w.S,
-                                                w.lam, w.order, reinterpret_cast<double*>(c->S[m]), c->evals,
-                                                reinterpret_cast<const double*>(Zc), reinterpret_cast<double*>(Zn), m,
-                                                counts);
-            TPCG_CHECK_LAUNCH();
-            prof_end(PK_EIG, st);
-            prof_begin(PK_PROJ, st);
-            if (m == 0)
-                TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
-            else if (m == 1)
-                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
-            else
-                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
-            prof_end(PK_PROJ, st);
-            T* tmp = Zc; Zc = Zn; Zn = tmp;
-        } else {
-            select32a_kernel<<<1, 1024, 0, st>>>(c->plan, ga, reinterpret_cast<const float*>(c->Gm), w.V32, w.lam32,
-                                                 w.lam, w.order, w.energy, w.A32, reinterpret_cast<const float*>(Zc),
-                                                 reinterpret_cast<float*>(Zn), m, counts);
-            TPCG_CHECK_LAUNCH();
-            prof_end(PK_EIG, st);
-            prof_begin(PK_PROJ, st);
-            if (m == 0)
-                TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
-            else if (m == 1)
-                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
-            else
-                TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
-            // the projected tensor has gM slices in mode m: measure them, keep the largest
-            set_gdim_kernel<<<1, 32, 0, st>>>(c->plan, m);
-            TPCG_CHECK_LAUNCH();
-            slice_energy_kernel<<<n, 256, 0, st>>>(c->plan, reinterpret_cast<const float*>(Zn), m, w.energy);
-            TPCG_CHECK_LAUNCH();
-            select32b_kernel<<<1, 1024, 0, st>>>(c->plan, w.energy, w.order, w.lam, w.A32,
-                                                 reinterpret_cast<float*>(c->S[m]), c->evals, m);
-            TPCG_CHECK_LAUNCH();
-            gather_slices_kernel<<<256, 256, 0, st>>>(c->plan, reinterpret_cast<const float*>(Zn), w.order,
-                                                      reinterpret_cast<float*>(Zc), m);
-            TPCG_CHECK_LAUNCH();
-            set_zdim_kernel<<<1, 32, 0, st>>>(c->plan, m);
-            TPCG_CHECK_LAUNCH();
-            prof_end(PK_PROJ, st);
-        }
+        TPCG_TRY(launch_eig<T>(c->plan, static_cast<const T*>(c->Gm), c->eigw, static_cast<T*>(c->S[m]),
+                                       c->evals, m, n, st));
+        prof_end(PK_EIG, st);
+        prof_begin(PK_PROJ, st);
+        plan_proj_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, static_cast<const T*>(c->S[m]), Zc, Zn, m, counts);
+        TPCG_CHECK_LAUNCH();
+        if (m == 0)
+            TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
+        else if (m == 1)
+            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
+        else
+            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
+        set_zdim_kernel<<<1, 32, 0, st>>>(c->plan, m);
+        TPCG_CHECK_LAUNCH();
+        prof_end(PK_PROJ, st);
+        T* tmp = Zc; Zc = Zn; Zn = tmp;
     }
     // step 4
     plan_final_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, static_cast<const T*>(c->Qq[0]),
@@ -676,9 +474,82 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
                                              static_cast<T*>(y->core), y->core_cap,
                                              static_cast<TuckerDesc*>(y->desc), info_dev);
     TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+
+template <typename T>
+int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
+               cudaStream_t st) {
+    const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
+    prof_begin(PK_ROUND, st);
+    TPCG_TRY(round_stage12<T>(c, y, eps, eps_dev, rc, st));
+    TPCG_TRY(round_stage34<T>(c, y, info_dev, st));
     prof_end(PK_ROUND, st);
     return TPCG_OK;
 }
+
+// Mixed rounding: Alg. 1 steps 1-2 in FP64 (the Z formation carries the cancellation of a residual), then
+// steps 3-4 in FP32 on the rounded Z.  y64 is an FP64 (block) tensor, out32 receives an FP32 plain tensor.
+__global__ void demote_kernel(const RoundPlan* __restrict__ plan, const double* __restrict__ Z64, float* __restrict__ Z32,
+                              const double* Q0, const double* Q1, const double* Q2, float* P0, float* P1, float* P2) {
+    const RoundPlan& p = *plan;
+    const long long nz = (long long)p.kp[0] * p.kp[1] * p.kp[2];
+    const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+    for (long long e = gt; e < nz; e += gs) Z32[e] = (float)Z64[e];
+    const double* Q[3] = {Q0, Q1, Q2};
+    float* P[3] = {P0, P1, P2};
+    for (int t = 0; t < 3; ++t) {
+        if (!p.useQ[t]) continue;
+        const long long nq = (long long)p.n * p.k[t];
+        for (long long e = gt; e < nq; e += gs) P[t][e] = (float)Q[t][e];
+    }
+}
+
+int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
+                double* info_dev, cudaStream_t st) {
+    const int rc = (cap > 0 && cap < c32->rank_cap) ? cap : c32->rank_cap;
+    prof_begin(PK_ROUND, st);
+    TPCG_TRY(round_stage12<double>(c64, y64, eps, eps_dev, rc, st));
+    demote_kernel<<<256, 256, 0, st>>>(c64->plan, static_cast<const double*>(c64->Z0), static_cast<float*>(c32->Z0),
+                                       static_cast<const double*>(c64->Qq[0]), static_cast<const double*>(c64->Qq[1]),
+                                       static_cast<const double*>(c64->Qq[2]), static_cast<float*>(c32->Qq[0]),
+                                       static_cast<float*>(c32->Qq[1]), static_cast<float*>(c32->Qq[2]));
+    TPCG_CHECK_LAUNCH();
+    TPCG_CUDA(cudaMemcpyAsync(c32->plan, c64->plan, sizeof(RoundPlan), cudaMemcpyDeviceToDevice, st));
+    TPCG_TRY(round_stage34<float>(c32, out32, info_dev, st));
+    prof_end(PK_ROUND, st);
+    return TPCG_OK;
+}
+
+// ||Z||^2 of the Z formed by round_stage12 (deterministic single-CTA reduction)
+template <typename T>
+__global__ void znorm2_kernel(const RoundPlan* __restrict__ plan, const T* __restrict__ Z, double* out) {
+    const RoundPlan& p = *plan;
+    const long long nz = (long long)p.kp[0] * p.kp[1] * p.kp[2];
+    double acc = 0.0;
+    for (long long e = threadIdx.x; e < nz; e += blockDim.x) acc += (double)Z[e] * (double)Z[e];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *out = t;
+    }
+}
+
+// squared Frobenius norm of an unrounded tensor y (any block structure): Z formation of Alg. 1 in the
+// working precision, then ||Z||^2 (exact: Q has orthonormal columns)
+template <typename T>
+int tensor_norm2(tpcg_ctx c, tucker_t* y, double* out_dev, cudaStream_t st) {
+    TPCG_TRY(round_stage12<T>(c, y, 0.0, nullptr, c->rank_cap, st));
+    znorm2_kernel<T><<<1, 1024, 0, st>>>(c->plan, static_cast<const T*>(c->Z0), out_dev);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int tensor_norm2<double>(tpcg_ctx, tucker_t*, double*, cudaStream_t);
+template int tensor_norm2<float>(tpcg_ctx, tucker_t*, double*, cudaStream_t);
 
 template int round_impl<double>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t);
 template int round_impl<float>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t);

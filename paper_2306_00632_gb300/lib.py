@@ -11,7 +11,7 @@ import os
 
 from . import build as _build
 
-F64, F32 = 0, 1
+F64, F32, MIXED = 0, 1, 2
 GEOM_CUBE, GEOM_TWIST = 0, 1
 MAX_BLOCKS = 128
 DESC_BYTES = 8192
@@ -59,12 +59,14 @@ class ProblemInfo(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("tol", C.c_double), ("eps0", C.c_double), ("eps_min", C.c_double), ("alpha", C.c_double),
-                ("delta", C.c_double), ("beta_trunc", C.c_double), ("max_it", C.c_int), ("rank_cap", C.c_int)]
+                ("delta", C.c_double), ("beta_trunc", C.c_double), ("max_it", C.c_int), ("rank_cap", C.c_int),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("rel_res", C.c_double), ("rank", C.c_int * 3),
-                ("mem_compression", C.c_double), ("dt_trials", C.c_int), ("max_rank_seen", C.c_int)]
+                ("mem_compression", C.c_double), ("dt_trials", C.c_int), ("max_rank_seen", C.c_int),
+                ("outer_iters", C.c_int), ("true_rel_res", C.c_double)]
 
 
 _lib = None

@@ -232,3 +232,62 @@ def test_tpcg_twist_against_oracle_and_direct(api):
     fv = tucker.vec(tucker.full(f))
     assert np.linalg.norm(fv - A @ xg) <= 2e-6 * np.linalg.norm(fv)
     assert rel(xg, tucker.vec(tucker.full(xo))) < 1e-4
+
+
+# ------------------------------------------------------------------------------------ FP32 form
+# Bar: 1e-4 relative (single-precision storage and products; the Gram of ST-HOSVD squares the FP32 rounding).
+F32_TOL = 1e-4
+
+
+def test_f32_apply_fd_dot(api):
+    n, p = 40, 3
+    pb = gpu_problem("cube", 0.0, n, p, dtype=1)
+    terms, _, P, _ = oracle_problem("cube", 0.0, n, p)
+    X = synth.random_tucker((n, n, n), (3, 2, 4), seed=31)
+    x = _plain(api, X, dtype=1)
+    y = api.Tucker(n, cap=3 * 4 + 1, core_cap=1, dtype=1)
+    api.tucker_apply(pb, x, y)
+    core, fac = y.to_numpy(others=[x])
+    ref = tucker.matvec(terms, X, dense=True)
+    assert rel(tucker.full((core, fac)), tucker.full(ref)) < F32_TOL
+    ctx = api.Ctx(n, P.RP * 4 + 8, 8, dtype=1)
+    v = api.Tucker(n, cap=P.RP * 4 + 8, core_cap=1, dtype=1)
+    api.fd_precond_apply(pb, ctx, x, v)
+    got = tucker.full(v.to_numpy(others=[x]))
+    assert rel(got, tucker.full(P.apply(X))) < F32_TOL
+    Y = synth.random_tucker((n, n, n), (2, 5, 3), seed=32)
+    yy = _plain(api, Y, dtype=1)
+    d = api.tucker_dot(ctx, x, yy).item()
+    assert abs(d - tucker.dot(X, Y)) <= 1e-5 * tucker.norm(X) * tucker.norm(Y)
+
+
+@pytest.mark.parametrize("eps", [2e-3, 3e-2])
+def test_f32_round_rank_rule_and_tensor(api, eps):
+    n = 45
+    d = np.array([1.0, 0.5, 0.1, 3e-3, 1e-3, 2e-4, 1e-5])
+    Y = _rotated_superdiagonal(d, n, seed=5)
+    ctx = api.Ctx(n, 64, 32, dtype=1)
+    y = _plain(api, Y, cap=16, core_cap=16 ** 3, dtype=1)
+    api.tucker_round(ctx, y, eps)
+    G, U = y.to_numpy()
+    G0, U0 = rounding.t_rel(Y, eps)
+    assert G.shape == G0.shape
+    assert rel(tucker.full((G, U)), tucker.full((G0, U0))) < F32_TOL
+
+
+def test_f32_round_block_tensor(api):
+    n, p, R = 37, 3, 4
+    terms = random_banded_terms(n, p, R, seed=9)
+    f = synth.random_tucker((n, n, n), (1, 1, 1), seed=8)
+    pb = api.tpcg_problem_create(n, p, terms, f[0], f[1], identity_tables(n), dtype=1)
+    X = synth.random_tucker((n, n, n), (2, 3, 2), seed=6)
+    x = _plain(api, X, dtype=1)
+    y = api.Tucker(n, cap=16, core_cap=16 ** 3, dtype=1)
+    api.tucker_apply(pb, x, y)
+    ctx = api.Ctx(n, 16, 16, dtype=1)
+    api.tucker_round(ctx, y, 1e-4)
+    G, U = y.to_numpy()
+    ref = tucker.matvec(terms, X)
+    G0, U0 = rounding.t_rel(ref, 1e-4)
+    assert G.shape == G0.shape
+    assert rel(tucker.full((G, U)), tucker.full(ref)) < 1e-4
