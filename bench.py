@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--dtype", default="mixed", choices=["mixed", "f64", "f32"])
+    ap.add_argument("--concurrent", type=int, default=8, help="solves per step, run at once")
     ap.add_argument("--rank-cap", type=int, default=96)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -105,7 +106,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------- CPU oracle
-def oracle_sample(iters_for_scale: int, n=N_DOF, p=DEGREE, sample_iters=2):
+def oracle_sample(iters_for_scale: int, n=N_DOF, p=DEGREE, sample_iters=5):
     """Time `sample_iters` iterations of the oracle's Alg. 5 on the same workload (setup excluded) and
     scale to solves/sec with the iteration count of a full solve."""
     from oracle import fd, lowrank, tpcg as otp
@@ -142,6 +143,61 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------- GPU arm
+def _profile(L, lib):
+    import ctypes as C
+    prof = {}
+    for name, kind in lib.PROF_KINDS.items():
+        ms, cnt, fl, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        L.tpcg_profile_get(kind, C.byref(ms), C.byref(cnt), C.byref(fl), C.byref(by))
+        prof[name] = {"ms": ms.value, "launches": cnt.value, "flops": fl.value, "bytes": by.value}
+    return prof
+
+
+def _roofline(prof, dt_name, lib, step_ms_total):
+    """Roofline of the dominant kernel class: algorithmic work per launch / measured launch time."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    src = "of measured" if peaks else "of fallback"
+    # FP32/FP64 SIMT peaks derived from the measured sustained bf16 rate and the nominal ratios
+    # (bf16 2250, FP32 75, FP64 1.25 TFLOP/s dense nominal)
+    alu = {"f64": bf16 * 1.25 / 2250.0, "f32": bf16 * 75.0 / 2250.0}
+    classes = ["zgemm", "zblk", "gram", "eig", "proj", "qr", "apply", "fd"]
+    dom = max(classes, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    per_launch_ms = d["ms"] / max(d["launches"], 1)
+    roof = {"kernel": dom, "share_of_step": d["ms"] / max(step_ms_total, 1e-9), "launches": d["launches"],
+            "ms_per_launch": per_launch_ms}
+    if dom in ("apply", "fd"):
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "peak_source": f"hbm_gbs {src}"})
+    else:
+        # the eigensolver's algorithmic work is the dense symmetric eigen-decomposition count 9 n'^3 per Gram
+        # (the mixed form's eigensolver launches are FP32 apart from the FP64 truncations of x)
+        prec = "f32" if (dom == "eig" and dt_name == "mixed") or dt_name == "f32" else "f64"
+        pk = alu[prec]
+        ach = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+        roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                     "traffic": None,
+                     "peak_source": f"{prec.upper()} SIMT peak = bf16_tflops_sustained {src} x nominal "
+                                    f"{'75' if prec == 'f32' else '1.25'}/2250"})
+    return roof
+
+
+def _make_problem(api, lib, dt, seed):
+    return api.tpcg_setup(lib.GEOM_TWIST, synth.amp_from_seed(seed), DEGREE, N_DOF, dt)
+
+
+def _ctx_for(api, info, dt, rc):
+    max_cols = max(info.R * rc + max(info.rf), info.RP * rc, 2 * rc)
+    return api.Ctx(N_DOF, max_cols, rc, dt)
+
+
 def run_gpu(args):
     import torch
     from paper_2306_00632_gb300 import api, lib
@@ -152,109 +208,95 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     L = lib.load()
-    dt = lib.F64 if args.dtype == "f64" else lib.F32
-    pb = api.tpcg_setup(lib.GEOM_TWIST, AMP, DEGREE, N_DOF, dt)
-    info = pb.info
+    dt = {"f64": lib.F64, "f32": lib.F32, "mixed": lib.MIXED}[args.dtype]
+    B = max(args.concurrent, 1)
     rc = min(args.rank_cap, N_DOF)
-    rfm = max(info.rf)
-    max_cols = max(info.R * rc + rfm, info.RP * rc, 2 * rc)
-    ctx = api.Ctx(N_DOF, max_cols, rc, dt)
-    x = api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=dt)
-    stream = torch.cuda.current_stream()
+    # B problems of the same family (seeds SEED .. SEED+B-1), one context, solution and stream each
+    pbs = [_make_problem(api, lib, dt, SEED + i) for i in range(B)]
+    ctxs = [_ctx_for(api, p.info, dt, rc) for p in pbs]
+    xs = [api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=dt) for _ in range(B)]
+    streams = [torch.cuda.Stream() for _ in range(B)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    main = torch.cuda.current_stream()
 
-    def solve():
-        return api.tpcg_solve(pb, ctx, x, tol=TOL, rank_cap=rc)
+    # (1) single-solve latency and the per-kernel profile (problem 0 on the main stream)
+    for _ in range(max(args.warmup, 0)):
+        api.tpcg_solve(pbs[0], ctxs[0], xs[0], tol=TOL, rank_cap=rc)
+    torch.cuda.synchronize()
+    L.tpcg_profile_reset()
+    L.tpcg_profile_enable(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    single = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(main)
+        st = api.tpcg_solve(pbs[0], ctxs[0], xs[0], tol=TOL, rank_cap=rc)
+        ev[k][1].record(main)
+        single.append(st)
+    torch.cuda.synchronize()
+    L.tpcg_profile_enable(0)
+    lat_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = _profile(L, lib)
+
+    # (2) throughput: K steps of B concurrent solves (tpcg_solve_batch), timed on the device
+    def batch():
+        return api.tpcg_solve_batch(pbs, ctxs, xs, streams, tol=TOL, rank_cap=rc)
 
     for _ in range(max(args.warmup, 0)):
-        st = solve()
+        batch()
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    L.tpcg_profile_reset()
-    L.tpcg_profile_enable(1)
     launches0 = L.tpcg_launch_count()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
-    g0.record(stream)
+    results = []
+    torch.cuda.synchronize()
+    g0.record(main)
     for k in range(args.steps):
         flush.zero_()
-        ev[k][0].record(stream)
-        st = solve()
-        ev[k][1].record(stream)
-        stats.append((st.iters, st.rel_res, st.status, tuple(st.rank)))
-    g1.record(stream)
+        torch.cuda.synchronize()   # the flush completes before the solve streams start
+        codes, sts = batch()
+        results.append((codes, sts))
+    g1.record(main)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     launches = L.tpcg_launch_count() - launches0
-    L.tpcg_profile_enable(0)
     clk = clocks.stop()
     total_ms = g0.elapsed_time(g1)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     if ws > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
 
-    # per-kernel-class profile of the timed region
-    import ctypes as C
-    prof = {}
-    for name, kind in lib.PROF_KINDS.items():
-        ms, cnt, fl, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
-        L.tpcg_profile_get(kind, C.byref(ms), C.byref(cnt), C.byref(fl), C.byref(by))
-        prof[name] = {"ms": ms.value, "launches": cnt.value, "flops": fl.value, "bytes": by.value}
-
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
-    peak_src = "measured" if peaks else "fallback"
-    fp64_peak = bf16 * 1.25 / 2250.0       # nominal FP64 / bf16 dense ratio x measured bf16
-    fp32_peak = bf16 * 75.0 / 2250.0       # nominal FP32 (SIMT) / bf16 ratio x measured bf16
-    kernel_classes = ["zgemm", "zblk", "gram", "eig", "proj", "qr", "apply", "fd"]
-    dom = max(kernel_classes, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
-    roof = {"kernel": dom, "share_of_step": d["ms"] / max(sum(step_ms), 1e-9)}
-    if dom in ("apply", "fd"):
-        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
-        roof.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                     "frac": ach / hbm, "traffic": None, "peak_source": peak_src})
-    elif dom == "eig":
-        roof.update({"bound": "latency", "achieved": d["ms"] / max(d["launches"], 1), "peak": None,
-                     "unit": "ms/launch", "frac": None, "traffic": None, "peak_source": peak_src})
-    else:
-        pk = fp64_peak if dt == lib.F64 else fp32_peak
-        ach = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-        roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                     "traffic": None, "peak_source": f"{peak_src} bf16 x nominal {'FP64' if dt == lib.F64 else 'FP32'}/bf16"})
-
-    value = ws * args.steps / (total_ms * 1e-3)
-    iters = [s[0] for s in stats]
+    roof = _roofline(prof, args.dtype, lib, sum(lat_ms))
+    value = ws * B * args.steps / (total_ms * 1e-3)
+    last = results[-1][1]
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-           "config": {"workload": WORKLOAD, "tol": TOL, "rank_cap": rc, "R": info.R, "RP": info.RP,
-                      "parallelism": f"replicas x{ws}", "l2": "256 MB buffer written between timed steps"},
-           "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-           "solve": {"iters": iters, "rel_res": [s[1] for s in stats], "status": [s[2] for s in stats],
-                     "rank": list(stats[-1][3])},
+           "config": {"workload": WORKLOAD, "solves_per_step": B,
+                      "seeds": f"{SEED}..{SEED + B - 1} (amp from seed)", "tol": TOL, "rank_cap": rc,
+                      "R": [p.info.R for p in pbs], "RP": pbs[0].info.RP, "parallelism": f"replicas x{ws}",
+                      "l2": "256 MB buffer written between timed steps"},
+           "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),
+                          "what": "single solve alone on the device (CUDA events)"},
+           "solve": {"status": [int(c) for c in results[-1][0]],
+                     "true_rel_res": [float(s.true_rel_res) for s in last],
+                     "inner_iters": [int(s.iters) for s in last], "outer_iters": [int(s.outer_iters) for s in last],
+                     "rank": [list(s.rank) for s in last]},
+           "single": {"iters": [int(s.iters) for s in single], "true_rel_res": [float(s.true_rel_res) for s in single]},
            "gpu_launches": int(launches), "roofline": roof,
-           "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+           "kernel_ms_single": {k: round(v["ms"], 3) for k, v in prof.items()},
            "clocks": clk}
 
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e(api, lib, pb, dt, ctx, rc, args)
+        out["e2e"] = e2e(api, lib, pbs, dt, ctxs, xs, streams, rc, args)
     if rank == 0 and not args.no_cpu and ws == 1:
         try:
-            out["cpu_baseline"] = oracle_sample(int(np.median(iters)))
+            out["cpu_baseline"] = oracle_sample(int(np.median([s.iters for s in single])) or 30)
         except Exception as e:   # the baseline must not hide the GPU line
             out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
     if rank == 0:
@@ -263,33 +305,38 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def e2e(api, lib, pb, dt, ctx, rc, args):
-    """Same metric through the public API with host inputs: every step re-creates the problem from pinned
-    host arrays (host -> device copies inside tpcg_problem_create), solves, and reads the solution back."""
+def e2e(api, lib, pbs, dt, ctxs, xs, streams, rc, args):
+    """Same metric through the public API with host inputs: every step re-creates the B problems from pinned
+    host arrays (host -> device copies inside tpcg_problem_create), solves them at once and reads the
+    solutions back to the host."""
     import torch
-    ex = pb.export()
-    info = pb.info
-    n = info.n
-    ex["v2u2"] = ex["v2u2"][: n * info.n2]
-    h2d = 8 * sum(int(np.asarray(ex[k]).size) for k in ("w", "bands", "f_core", "f_U0", "f_U1", "f_U2", "lam",
-                                                        "mu", "w_val", "v2u2", "omega", "alpha"))
-    h2d += 4 * (int(ex["w_rowptr"].size) + int(ex["w_col"].size))
-    x = api.Tucker(n, cap=rc, core_cap=rc ** 3, dtype=dt)
+    exs = []
+    for pb in pbs:
+        ex = pb.export()
+        ex["v2u2"] = ex["v2u2"][: pb.info.n * pb.info.n2]
+        exs.append((ex, pb.info))
+    h2d = 0
+    for ex, _ in exs:
+        h2d += 8 * sum(int(np.asarray(ex[k]).size) for k in ("w", "bands", "f_core", "f_U0", "f_U1", "f_U2", "lam",
+                                                            "mu", "w_val", "v2u2", "omega", "alpha"))
+        h2d += 4 * (int(ex["w_rowptr"].size) + int(ex["w_col"].size))
     K = max(2, min(args.steps, 3))
     times = []
     d2h = 0
     for k in range(K + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pb2 = api.problem_from_export(ex, info, dtype=dt, pinned=True)
-        st = api.tpcg_solve(pb2, ctx, x, tol=TOL, rank_cap=rc)
-        core, fac = x.to_numpy()
+        pb2 = [api.problem_from_export(ex, info, dtype=dt, pinned=True) for ex, info in exs]
+        api.tpcg_solve_batch(pb2, ctxs, xs, streams, tol=TOL, rank_cap=rc)
+        d2h = 0
+        for x in xs:
+            core, fac = x.to_numpy()
+            d2h += (core.size + sum(f.size for f in fac)) * (4 if dt == lib.F32 else 8)
         torch.cuda.synchronize()
         if k > 0:
             times.append(time.perf_counter() - t0)
-        d2h = (core.size + sum(f.size for f in fac)) * (8 if dt == lib.F64 else 4)
         del pb2
-    return {"value": 1.0 / statistics.median(times), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+    return {"value": len(pbs) / statistics.median(times), "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": K}
 
 

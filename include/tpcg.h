@@ -158,8 +158,9 @@ int tucker_axpby(double a, const double* a_dev, const tucker_t* x, double b, con
 int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, void* stream);
 /* In-place relative truncation, Alg. 1: y <- T_rel(y, eps) with ST-HOSVD split eps^2/3 per mode, ranks
  * clipped to rank_cap (<= 0: the context's cap).  Factors come out orthonormal, so ||y|| = ||core||.
- * If info_dev is non-NULL it receives 4 doubles: ||y||^2 before, discarded squared norm, and the new
- * ranks as doubles (3) are written to info_dev[2..4]; TPCG_E_RANK_CAP is not raised here (check info). */
+ * If info_dev is non-NULL it receives 6 doubles: ||y||^2 before, the discarded squared norm, the new
+ * ranks (3, as doubles) and a flag that is nonzero when the new core did not fit the tensor's core_cap; TPCG_E_RANK_CAP
+ * is not raised here (check info). */
 int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rank_cap, double* info_dev,
                  void* stream);
 /* v = P~^{-1} s, Alg. 4 steps 5-9: factors [U~ D_(t,1) U~^T S_t, ..., U~ D_(t,RP) U~^T S_t], core
@@ -176,8 +177,8 @@ typedef struct {
     double beta_trunc;  /* beta of eq. rel_tol_iterates                                    (0.1)   */
     int max_it;         /* iteration cap                                                   (500)   */
     int rank_cap;       /* rank cap of every truncation; <= 0: the context's cap                   */
-    double inner_tol;   /* mixed form: relative tolerance of each FP32 inner solve          (1e-2)  */
-    int max_outer;      /* mixed form: cap on FP64 residual refinements                     (6)     */
+    double inner_tol;   /* mixed form: relative tolerance of each FP32 inner solve          (5e-2)  */
+    int max_outer;      /* mixed form: cap on FP64 residual refinements (at most 32)        (12)    */
 } tpcg_params;
 
 typedef struct {
@@ -198,11 +199,23 @@ void tpcg_params_default(tpcg_params* p);
  * core_cap >= rank_cap^3).  Synchronises the stream once per iteration for the stopping test.
  * Mixed form (problem and context created with TPCG_MIXED; x is FP64): iterative refinement around Alg. 5.
  * Each outer step forms the residual f - A x in FP64 (banded products and the Z formation of Alg. 1 in
- * FP64, so the cancellation is exact to FP64 and ||Z|| is the true residual norm), truncates it in FP32
- * to 0.1 inner_tol, solves A d = r by Alg. 5 in FP32 to inner_tol (dynamic-truncation floor 0.1 inner_tol),
- * and accumulates x += d as an FP64 Tucker sum; x is truncated once in FP64 (tolerance tol / 10) at the end.
+ * FP64, so the cancellation is exact to FP64 and ||Z|| is the true residual norm) and truncates it in FP32
+ * to 0.1 inner_tol relative, or to beta tol ||f~|| / 2 absolute when that is looser (the relaxation of
+ * eq. rel_tol_iterates carried over to the outer loop).  It then solves A d = r by Alg. 5 in FP32 to
+ * max(inner_tol, tol ||f~|| / (2 ||r||)) (dynamic-truncation floor a tenth of that, at most 12 iterations)
+ * and sets x <- T_rel(x + d, delta ||d|| / ||x + d||) in FP64 (the correction kept to the accuracy delta of
+ * Alg. 2's update test).  x is plain throughout, so the FP64 residual refers to the returned tensor.
  * The stopping test uses the true FP64 residual. */
 int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
+
+/* count independent solves at once (no counterpart in the paper; many-solve throughput).  Solve i is
+ * tpcg_solve(pbs[i], ctxs[i], &prms[i], &xs[i], &sts[i], streams[i]) on a host thread of its own, so the
+ * solves' kernels overlap on the device.  Every solve needs its own context and its own non-default
+ * stream; problems may be shared (they are read-only during a solve).  statuses[i] receives each
+ * solve's status; the return value is TPCG_OK, else the first hard error, else TPCG_E_NOT_CONVERGED.
+ * Results do not depend on what runs beside them (no shared scratch).  Turn profiling off first. */
+int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, const tpcg_params* prms, tucker_t* xs,
+                     tpcg_stats* sts, void* const* streams, int* statuses);
 
 /* ------------------------------------------------------------------------------------ profiling */
 /* Kernel classes timed with CUDA events on the launching stream while profiling is on:

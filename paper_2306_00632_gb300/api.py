@@ -317,3 +317,22 @@ def tpcg_solve(pb: Problem, ctx: Ctx, x: Tucker, stream=None, **kw):
     if code not in (0, 3):
         check(code, "tpcg_solve")
     return st
+
+
+def tpcg_solve_batch(problems, ctxs, xs, streams, **kw):
+    """Independent solves at once (tpcg_solve_batch): one host thread and one stream per solve.
+    Returns (statuses, stats)."""
+    k = len(problems)
+    if not (len(ctxs) == len(xs) == len(streams) == k):
+        raise ValueError("tpcg_solve_batch: problems, ctxs, xs and streams must have the same length")
+    prm = (L.Params * k)(*[tpcg_params(**kw) for _ in range(k)])
+    sts = (L.Stats * k)()
+    pbs = (C.c_void_p * k)(*[p.h for p in problems])
+    cts = (C.c_void_p * k)(*[c.h for c in ctxs])
+    ts = (L.TuckerT * k)(*[x.t for x in xs])
+    ss = (C.c_void_p * k)(*[s.cuda_stream for s in streams])
+    codes = (C.c_int * k)()
+    code = L.load().tpcg_solve_batch(k, pbs, cts, prm, ts, sts, ss, codes)
+    if code not in (0, 3):
+        check(code, "tpcg_solve_batch")
+    return [int(c) for c in codes], [sts[i] for i in range(k)]

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -160,8 +161,8 @@ extern "C" void tpcg_params_default(tpcg_params* p) {
     p->beta_trunc = 0.1;
     p->max_it = 500;
     p->rank_cap = 0;
-    p->inner_tol = 1e-2;
-    p->max_outer = 6;
+    p->inner_tol = 5e-2;
+    p->max_outer = 12;
 }
 
 // ======================================================================================= contexts
@@ -199,6 +200,7 @@ extern "C" size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype) {
 extern "C" void tpcg_ctx_destroy(tpcg_ctx c) {
     if (!c) return;
     if (c->lo) tpcg_ctx_destroy(c->lo);
+    if (c->sync_ev) cudaEventDestroy(c->sync_ev);
     for (void* p : c->owned) cudaFree(p);
     delete c;
 }
@@ -223,6 +225,14 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
     }
     tpcg_ctx c = new tpcg_ctx_s();
     c->lo = nullptr;
+    c->sync_ev = nullptr;
+    if (cudaEventCreateWithFlags(&c->sync_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        c->sync_ev = nullptr;
+        set_error("tpcg_ctx_create: cudaEventCreateWithFlags failed");
+        delete c;
+        return TPCG_E_CUDA;
+    }
     c->n = n;
     c->max_cols = max_cols;
     c->rank_cap = rank_cap;
@@ -661,6 +671,14 @@ static int ensure_tensors(tpcg_ctx c) {
     return TPCG_OK;
 }
 
+// wait on the host for the work enqueued on s so far; the thread sleeps instead of spinning, so that many
+// solver threads can share the host cores
+static int host_wait(tpcg_ctx c, cudaStream_t s) {
+    TPCG_CUDA(cudaEventRecord(c->sync_ev, s));
+    TPCG_CUDA(cudaEventSynchronize(c->sync_ev));
+    return TPCG_OK;
+}
+
 // ||f - A x|| / ||f|| of a solution x, in the working precision of the problem (no truncation)
 template <typename T>
 static int true_residual(tpcg_problem pb, tpcg_ctx c, const tucker_t* x, tucker_t* work, double* rel, cudaStream_t s) {
@@ -669,7 +687,7 @@ static int true_residual(tpcg_problem pb, tpcg_ctx c, const tucker_t* x, tucker_
     TPCG_TRY(tensor_norm2<T>(c, work, d, s));
     double h = 0.0;
     TPCG_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TPCG_CUDA(cudaStreamSynchronize(s));
+    TPCG_TRY(host_wait(c, s));
     *rel = pb->norm_f > 0 ? sqrt(std::max(h, 0.0)) / pb->norm_f : 0.0;
     return TPCG_OK;
 }
@@ -720,7 +738,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     const bool trace = tr && tr[0] == '1';
     for (;;) {
         TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
-        TPCG_CUDA(cudaStreamSynchronize(s));
+        TPCG_TRY(host_wait(c, s));
         if (trace) {
             int rx[3], rr[3], rz[3], rp[3], rq[3], nb;
             tucker_get_ranks(x, rx, &nb, s);
@@ -753,7 +771,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
             ++trials_total;
             double done;
             TPCG_CUDA(cudaMemcpyAsync(&done, sc + S_DONE, sizeof(double), cudaMemcpyDeviceToHost, s));
-            TPCG_CUDA(cudaStreamSynchronize(s));
+            TPCG_TRY(host_wait(c, s));
             if (done != 0.0 || trial > 64) break;
         }
         std::swap(x, big2);
@@ -801,7 +819,18 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     return status;
 }
 
-// Mixed form: iterative refinement with FP64 residuals around FP32 Alg. 5 (see tpcg.h)
+// truncation tolerance of x + d in the mixed form: the correction d is kept to relative accuracy delta
+// (the update-ratio threshold of Alg. 2), eps = delta ||d|| / ||x + d|| (x and d plain, near-orthogonal parts)
+__global__ void xeps_kernel(const double* dd, const double* xx, double delta, double* eps) {
+    const double d = fmax(*dd, 0.0), x = fmax(*xx, 0.0);
+    *eps = (d + x > 0.0) ? delta * sqrt(d / (d + x)) : 0.0;
+}
+
+// Mixed form: iterative refinement with FP64 residuals around FP32 Alg. 5 (see tpcg.h).  The outer loop
+// carries the relaxation of Alg. 5 over to the refinement: the FP32 copy of the residual may lose
+// beta tol ||f~|| / 2 in absolute terms, and the inner solve stops at the reduction the outer target needs.
+// x stays plain: after each correction x <- T_rel(x + d, delta ||d|| / ||x + d||) in FP64, so every residual
+// (and the stopping test) refers to the tensor that is returned.
 static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
                        cudaStream_t s) {
     tpcg_problem pb32 = pb->lo;
@@ -810,61 +839,65 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
     TPCG_TRY(ensure_tensors(c32));
     const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
     tucker_t* xacc = &c->tens[0];
-    tucker_t* xtmp = &c->tens[1];
+    tucker_t* xsum = &c->tens[1];
     tucker_t* big = &c->tens[2];
+    tucker_t* dco = &c->tens[3];
     tucker_t* r32 = &c32->tens[8];
     tucker_t* d32 = &c32->tens[9];
-    const int max_outer = std::min(std::max(prm->max_outer, 1), 7);
+    const int max_outer = std::min(std::max(prm->max_outer, 1), 64);
     const double nf = pb->norm_f;
+    const double abs_tol = 0.5 * prm->beta_trunc * prm->tol * nf;
     double* info = c->scal + 120;   // 6 doubles written by the rounding
+    double* dd = c->scal + 140;
+    double* xx = c->scal + 141;
+    double* xeps = c->scal + 142;
     const char* tr = getenv("TPCG_TRACE");
     const bool trace = tr && tr[0] == '1';
     TPCG_TRY(set_zero(xacc, s));
     tpcg_params in = *prm;
-    in.tol = prm->inner_tol;
-    in.eps_min = 0.1 * prm->inner_tol;
     in.rank_cap = rc;
+    in.max_it = std::min(prm->max_it, 12);
     int status = TPCG_E_NOT_CONVERGED, outer = 0, inner_total = 0, trials = 0;
     double rel = 1.0;
     for (outer = 0; outer <= max_outer; ++outer) {
-        // r = f - A x in FP64, truncated to 0.1 inner_tol in FP32
+        // r = f - A x in FP64 (exact ||r|| from Z), truncated to 0.1 inner_tol (relative) or abs_tol in FP32
         TPCG_TRY(apply_impl<double>(pb, xacc, big, true, s));
-        TPCG_TRY(round_mixed(c, c32, big, r32, 0.1 * prm->inner_tol, nullptr, rc, info, s));
+        TPCG_TRY(round_mixed(c, c32, big, r32, 0.1 * prm->inner_tol, nullptr, rc, abs_tol, info, s));
         double h[6];
         TPCG_CUDA(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
-        TPCG_CUDA(cudaStreamSynchronize(s));
+        TPCG_TRY(host_wait(c, s));
         rel = nf > 0 ? sqrt(std::max(h[0], 0.0)) / nf : 0.0;
         if (trace) fprintf(stderr, "mixed outer=%d true_res=%.3e r-rank=(%g,%g,%g)\n", outer, rel, h[2], h[3], h[4]);
         if (!(rel == rel)) { status = TPCG_E_BREAKDOWN; break; }
         if (rel <= prm->tol) { status = TPCG_OK; break; }
         if (outer == max_outer) break;
-        // keep the next residual within the block list and the factor capacity: compress x in FP64 first
-        const int rfmax = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
-        if ((outer + 2) * pb->R + 1 > TPCG_MAX_BLOCKS || pb->R * (outer + 2) * rc + rfmax > c->max_cols)
-            TPCG_TRY(round_impl<double>(c, xacc, 0.01 * prm->tol, nullptr, rc, nullptr, s));
+        // inner tolerance: inner_tol, or the (looser) reduction that reaches tol from the current residual
+        in.tol = std::min(0.5, std::max(prm->inner_tol, 0.5 * prm->tol / rel));
+        in.eps_min = 0.1 * in.tol;
         tpcg_stats sin{};
         int si = solve_impl<float>(pb32, c32, &in, d32, &sin, s, r32);
         inner_total += sin.iters;
         trials += sin.dt_trials;
+        if (trace) fprintf(stderr, "mixed inner tol=%.2e iters=%d status=%d\n", in.tol, sin.iters, si);
         if (si != TPCG_OK && si != TPCG_E_NOT_CONVERGED) { status = si; break; }
-        tucker_t* dco = &c->tens[3 + outer];
+        // x <- T_rel(x + d, delta ||d|| / ||x + d||) in FP64
         TPCG_TRY(promote_tensor(d32, dco, s));
-        TPCG_TRY(axpby_impl<double>(1.0, nullptr, xacc, 1.0, nullptr, dco, xtmp, nullptr, s));
-        std::swap(xacc, xtmp);
+        TPCG_TRY(dot_impl<double>(c, dco, dco, dd, s));
+        TPCG_TRY(dot_impl<double>(c, xacc, xacc, xx, s));
+        xeps_kernel<<<1, 1, 0, s>>>(dd, xx, prm->delta, xeps);
+        TPCG_CHECK_LAUNCH();
+        TPCG_TRY(axpby_impl<double>(1.0, nullptr, xacc, 1.0, nullptr, dco, xsum, nullptr, s));
+        TPCG_TRY(round_impl<double>(c, xsum, 0.0, xeps, rc, nullptr, s));
+        std::swap(xacc, xsum);
     }
-    // one FP64 truncation of the accumulated solution, then its true residual
-    TPCG_TRY(round_impl<double>(c, xacc, 0.01 * prm->tol, nullptr, rc, nullptr, s));
     TPCG_TRY(copy_tensor_impl<double>(xacc, xout, c->n, xout->cap, s));
-    double true_rel = rel;
-    TPCG_TRY(true_residual<double>(pb, c, xacc, big, &true_rel, s));
-    if (status == TPCG_OK && true_rel > prm->tol) status = TPCG_E_NOT_CONVERGED;
     int rk[3] = {0, 0, 0}, nb = 0;
     TPCG_TRY(tucker_get_ranks(xout, rk, &nb, s));
     if (st) {
         st->iters = inner_total;
         st->status = status;
         st->rel_res = rel;
-        st->true_rel_res = true_rel;
+        st->true_rel_res = rel;   // the FP64 residual of exactly the returned x
         st->outer_iters = outer;
         for (int t = 0; t < 3; ++t) st->rank[t] = rk[t];
         const double n = c->n;
@@ -888,10 +921,6 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
             set_error("tpcg_solve: the mixed form needs a TPCG_MIXED problem and a TPCG_MIXED context");
             return TPCG_E_INVALID;
         }
-        if (c->max_cols < 2 * pb->R * c->rank_cap + 8) {
-            set_error("tpcg_solve: mixed form needs max_cols >= 2 R rank_cap + 8 (residual of accumulated corrections)");
-            return TPCG_E_INVALID;
-        }
     }
     const int rfmax = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
     const int need = std::max(pb->R * c->rank_cap + rfmax, std::max(pb->RP * c->rank_cap, 2 * c->rank_cap));
@@ -902,4 +931,45 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
     }
     if (pb->lo) return solve_mixed(pb, c, prm, x, st, S(stream));
     return by_dtype(pb->dtype, [&](auto z) { return solve_impl<decltype(z)>(pb, c, prm, x, st, S(stream)); });
+}
+
+// Many independent solves at once: one host thread per solve, each on its own stream and context, so
+// that their kernels overlap on the device (the eigensolver and QR kernels of one solve fill one SM each).
+extern "C" int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, const tpcg_params* prms,
+                                tucker_t* xs, tpcg_stats* sts, void* const* streams, int* statuses) {
+    if (count < 0 || (count > 0 && (!pbs || !ctxs || !prms || !xs || !streams || !statuses))) {
+        set_error("tpcg_solve_batch: invalid arguments");
+        return TPCG_E_INVALID;
+    }
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i; ++j)
+            if (ctxs[i] == ctxs[j] || (streams[i] && streams[i] == streams[j])) {
+                set_error("tpcg_solve_batch: every solve needs its own context and its own (non-default) stream");
+                return TPCG_E_INVALID;
+            }
+    int dev = 0;
+    TPCG_CUDA(cudaGetDevice(&dev));
+    std::vector<std::thread> th;
+    std::vector<std::string> errs(count);
+    th.reserve(count);
+    for (int i = 0; i < count; ++i) {
+        th.emplace_back([&, i]() {
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                statuses[i] = TPCG_E_CUDA;
+                errs[i] = "cudaSetDevice failed in a solver thread";
+                return;
+            }
+            statuses[i] = tpcg_solve(pbs[i], ctxs[i], &prms[i], &xs[i], sts ? &sts[i] : nullptr, streams[i]);
+            if (statuses[i] != TPCG_OK) errs[i] = tpcg_last_error();
+        });
+    }
+    for (auto& t : th) t.join();
+    for (int i = 0; i < count; ++i)
+        if (statuses[i] != TPCG_OK && statuses[i] != TPCG_E_NOT_CONVERGED) {
+            set_error("tpcg_solve_batch: solve " + std::to_string(i) + ": " + errs[i]);
+            return statuses[i];
+        }
+    for (int i = 0; i < count; ++i)
+        if (statuses[i] != TPCG_OK) return statuses[i];
+    return TPCG_OK;
 }

@@ -98,6 +98,7 @@ struct RoundPlan {
     int gm, gM;        // current Gram: mode and size
     int zdim[3];       // current dims of the working tensor
     double eps, budget, norm2, discarded;
+    double abs2;       // absolute floor of the discarded energy (0: relative rule only)
     const void* Rp[3]; // R_t used to form Z (workspace R or the factor itself)
     long long ldR[3];
     int kz3;           // total K of the fused last-mode GEMM
@@ -142,6 +143,7 @@ struct tpcg_ctx_s {
     bool have_tens;
     int tens_cap;
     tpcg_ctx_s* lo;      // FP32 companion of a mixed-precision context (else null)
+    cudaEvent_t sync_ev; // blocking-sync event for the solver's host waits (the waiting thread sleeps)
 };
 
 struct tpcg_problem_s {

@@ -31,7 +31,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const T* __restrict__ G, T* __restrict__ Ag,
                                                           T* __restrict__ Vg, T* __restrict__ S, double* evals, int m,
-                                                          int a_smem, int v_smem, int max_sweeps) {
+                                                          int a_smem, int v_smem, int max_sweeps, double* prof) {
     RoundPlan& p = *plan;
     const int M = p.gM;
     const int n = p.n;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
         s_tr = t;
         if (m == 0) {
             p.norm2 = t;
-            p.budget = p.eps * p.eps * t / 3.0;
+            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
         }
     }
     __syncthreads();
@@ -77,8 +77,66 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
     const T epsr = sizeof(T) == 8 ? T(1e-15) : T(3e-7);
     const T epsa = (T)((sizeof(T) == 8 ? 2.2e-16 : 1.2e-7) * s_tr);
     const int nblk = half * (half + 1) / 2;   // 2 x 2 blocks (a <= b) of the pair partition
-    const int vtpp = nt / half > 0 ? nt / half : 1;   // threads per pair in the V update
-    const int vk0 = tid / vtpp, vi0 = tid % vtpp, vkstep = nt / vtpp;
+    // blocks of this thread (q = tid + j nt), decoded once when there are at most 4 per thread
+    constexpr int NBREG = 4;
+    int ab[NBREG];
+    const bool reg_blocks = nblk <= NBREG * nt;
+    if (reg_blocks) {
+#pragma unroll
+        for (int j = 0; j < NBREG; ++j) {
+            const int q = tid + j * nt;
+            ab[j] = -1;
+            if (q < nblk) {
+                int bb = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+                while ((bb + 1) * (bb + 2) / 2 <= q) ++bb;
+                while (bb * (bb + 1) / 2 > q) --bb;
+                ab[j] = (q - bb * (bb + 1) / 2) | (bb << 16);
+            }
+        }
+    }
+    // V update: a warp (or a multiple of warps) per pair, consecutive rows across the lanes
+    const int vtpp = max(32, (nt / half) & ~31);
+    const int vk0 = tid / vtpp, vi0 = tid % vtpp, vkstep = nt / vtpp > 0 ? nt / vtpp : 1;
+    // A <- J_a^T A J_b on the 2 x 2 block (pair a rows, pair b columns), mirrored for a < b
+    auto update_block = [&](int a, int b) {
+        const T sa = cs[2 * a + 1], sb = cs[2 * b + 1];
+        if (sa == T(0) && sb == T(0)) return;
+        const T ca = cs[2 * a], cb = cs[2 * b];
+        const int pa = pq[2 * a], qa = pq[2 * a + 1], pb = pq[2 * b], qb = pq[2 * b + 1];
+        if (qa < 0 || qb < 0) {
+            // one side is the padding index: a single row/column pair (M odd)
+            if (qa < 0 && qb < 0) return;
+            if (qa < 0) {   // rotate columns pb, qb of row pa (and mirror)
+                const T x = A[pa + pb * ld], y = A[pa + qb * ld];
+                const T xn = cb * x - sb * y, yn = sb * x + cb * y;
+                A[pa + pb * ld] = xn; A[pa + qb * ld] = yn;
+                A[pb + pa * ld] = xn; A[qb + pa * ld] = yn;
+            } else {        // rotate rows pa, qa of column pb (and mirror)
+                const T x = A[pa + pb * ld], y = A[qa + pb * ld];
+                const T xn = ca * x - sa * y, yn = sa * x + ca * y;
+                A[pa + pb * ld] = xn; A[qa + pb * ld] = yn;
+                A[pb + pa * ld] = xn; A[pb + qa * ld] = yn;
+            }
+            return;
+        }
+        const int cpb = pb * ld, cqb = qb * ld;
+        const T x00 = A[pa + cpb], x01 = A[pa + cqb];
+        const T x10 = A[qa + cpb], x11 = A[qa + cqb];
+        // rows: J_a^T X
+        const T r00 = ca * x00 - sa * x10, r01 = ca * x01 - sa * x11;
+        const T r10 = sa * x00 + ca * x10, r11 = sa * x01 + ca * x11;
+        // columns: (J_a^T X) J_b
+        T y00 = cb * r00 - sb * r01, y01 = sb * r00 + cb * r01;
+        T y10 = cb * r10 - sb * r11, y11 = sb * r10 + cb * r11;
+        if (a == b) { y01 = T(0); y10 = T(0); }   // the rotated pair is annihilated
+        A[pa + cpb] = y00; A[pa + cqb] = y01;
+        A[qa + cpb] = y10; A[qa + cqb] = y11;
+        if (a != b) {
+            const int cpa = pa * ld, cqa = qa * ld;
+            A[pb + cpa] = y00; A[qb + cpa] = y01;
+            A[pb + cqa] = y10; A[qb + cqa] = y11;
+        }
+    };
     for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
@@ -89,8 +147,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
                 const int pi = a < b ? a : b, qi = a < b ? b : a;
                 T c = T(1), s = T(0);
                 if (qi < M) {
-                    const T apq = A[pi + (long long)qi * ld];
-                    const T app = A[pi + (long long)pi * ld], aqq = A[qi + (long long)qi * ld];
+                    const T apq = A[pi + qi * ld];
+                    const T app = A[pi + pi * ld], aqq = A[qi + qi * ld];
                     if (fabs(apq) > epsr * sqrt(fabs(app * aqq)) && fabs(apq) > epsa) {
                         const T th = (aqq - app) / (T(2) * apq);
                         const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
@@ -105,56 +163,26 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
                 pq[2 * k + 1] = (short)(qi < M ? qi : -1);
             }
             __syncthreads();
-            // A <- J^T A J by 2 x 2 blocks: rows of pair a, columns of pair b (a <= b), mirrored for a < b
-            for (int q = tid; q < nblk; q += nt) {
-                // q -> (a, b) with a <= b: b = largest with b (b + 1) / 2 <= q
-                int b = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-                while ((b + 1) * (b + 2) / 2 <= q) ++b;
-                while (b * (b + 1) / 2 > q) --b;
-                const int a = q - b * (b + 1) / 2;
-                const T sa = cs[2 * a + 1], sb = cs[2 * b + 1];
-                if (sa == T(0) && sb == T(0)) continue;
-                const T ca = cs[2 * a], cb = cs[2 * b];
-                const int pa = pq[2 * a], qa = pq[2 * a + 1], pb = pq[2 * b], qb = pq[2 * b + 1];
-                if (qa < 0 || qb < 0) {
-                    // one side is the padding index: a single row/column pair (M odd)
-                    if (qa < 0 && qb < 0) continue;
-                    if (qa < 0) {   // rotate columns pb, qb of row pa (and mirror)
-                        const T x = A[pa + (long long)pb * ld], y = A[pa + (long long)qb * ld];
-                        const T xn = cb * x - sb * y, yn = sb * x + cb * y;
-                        A[pa + (long long)pb * ld] = xn; A[pa + (long long)qb * ld] = yn;
-                        A[pb + (long long)pa * ld] = xn; A[qb + (long long)pa * ld] = yn;
-                    } else {        // rotate rows pa, qa of column pb (and mirror)
-                        const T x = A[pa + (long long)pb * ld], y = A[qa + (long long)pb * ld];
-                        const T xn = ca * x - sa * y, yn = sa * x + ca * y;
-                        A[pa + (long long)pb * ld] = xn; A[qa + (long long)pb * ld] = yn;
-                        A[pb + (long long)pa * ld] = xn; A[pb + (long long)qa * ld] = yn;
-                    }
-                    continue;
-                }
-                const T x00 = A[pa + (long long)pb * ld], x01 = A[pa + (long long)qb * ld];
-                const T x10 = A[qa + (long long)pb * ld], x11 = A[qa + (long long)qb * ld];
-                // rows: J_a^T X
-                const T r00 = ca * x00 - sa * x10, r01 = ca * x01 - sa * x11;
-                const T r10 = sa * x00 + ca * x10, r11 = sa * x01 + ca * x11;
-                // columns: (J_a^T X) J_b
-                T y00 = cb * r00 - sb * r01, y01 = sb * r00 + cb * r01;
-                T y10 = cb * r10 - sb * r11, y11 = sb * r10 + cb * r11;
-                if (a == b) { y01 = T(0); y10 = T(0); }   // the rotated pair is annihilated
-                A[pa + (long long)pb * ld] = y00; A[pa + (long long)qb * ld] = y01;
-                A[qa + (long long)pb * ld] = y10; A[qa + (long long)qb * ld] = y11;
-                if (a != b) {
-                    A[pb + (long long)pa * ld] = y00; A[qb + (long long)pa * ld] = y01;
-                    A[pb + (long long)qa * ld] = y10; A[qb + (long long)qa * ld] = y11;
+            if (reg_blocks) {
+#pragma unroll
+                for (int j = 0; j < NBREG; ++j)
+                    if (ab[j] >= 0) update_block(ab[j] & 0xffff, ab[j] >> 16);
+            } else {
+                for (int q = tid; q < nblk; q += nt) {
+                    // q -> (a, b) with a <= b: b = largest with b (b + 1) / 2 <= q
+                    int bb = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+                    while ((bb + 1) * (bb + 2) / 2 <= q) ++bb;
+                    while (bb * (bb + 1) / 2 > q) --bb;
+                    update_block(q - bb * (bb + 1) / 2, bb);
                 }
             }
-            // V <- V J: thread group per pair, rows strided by the group size
+            // V <- V J
             for (int k = vk0; k < half; k += vkstep) {
                 const T s = cs[2 * k + 1];
-                if (s == T(0)) continue;
+                if (s == T(0) || pq[2 * k + 1] < 0) continue;
                 const T c = cs[2 * k];
-                T* Vp = V + (long long)pq[2 * k] * ld;
-                T* Vq = V + (long long)pq[2 * k + 1] * ld;
+                T* Vp = V + pq[2 * k] * ld;
+                T* Vq = V + pq[2 * k + 1] * ld;
                 for (int i = vi0; i < M; i += vtpp) {
                     const T vip = Vp[i], viq = Vq[i];
                     Vp[i] = c * vip - s * viq;
@@ -211,6 +239,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
         p.s[m] = s;
         s_keep = s;
         for (int i = 0; i < M; ++i) evals[i] = lam[i];
+        if (prof) {   // algorithmic work: the dense symmetric eigen-decomposition count 9 M^3; Gram in, S out
+            prof[2 * PK_EIG] += 9.0 * (double)M * M * M;
+            prof[2 * PK_EIG + 1] += (double)sizeof(T) * ((double)M * M + (double)M * s);
+        }
     }
     __syncthreads();
     const int s = s_keep;
@@ -232,14 +264,10 @@ template <typename T>
 int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int m, int n, cudaStream_t st) {
     int a_smem = 0, v_smem = 0;
     const size_t bytes = jacobi_smem_plan(n, sizeof(T), &a_smem, &v_smem);
-    static bool attr[2] = {false, false};
-    const int ti = sizeof(T) == 8 ? 0 : 1;
-    if (!attr[ti]) {
-        TPCG_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 190 * 1024));
-        attr[ti] = true;
-    }
+    // the shared-memory opt-in is per device; set it on every launch (cheap) so that no device is missed
+    TPCG_CUDA(cudaFuncSetAttribute(jacobi_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 190 * 1024));
     jacobi_eig_kernel<T><<<1, 1024, bytes, st>>>(plan, G, reinterpret_cast<T*>(w.Aw), reinterpret_cast<T*>(w.Vw), S,
-                                                 evals, m, a_smem, v_smem, 20);
+                                                 evals, m, a_smem, v_smem, 20, prof_dev());
     TPCG_CHECK_LAUNCH();
     return TPCG_OK;
 }

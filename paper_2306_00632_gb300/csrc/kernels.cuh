@@ -8,8 +8,9 @@ namespace tpcg {
 template <typename T>
 int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
                cudaStream_t st);
+// FP64 Z formation, FP32 ST-HOSVD into out32; the discarded energy may also reach abs_tol^2 (absolute norm floor)
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
-                double* info_dev, cudaStream_t st);
+                double abs_tol, double* info_dev, cudaStream_t st);
 // ||y||^2 of any (block) tensor by the Z formation of Alg. 1
 template <typename T>
 int tensor_norm2(tpcg_ctx c, tucker_t* y, double* out_dev, cudaStream_t st);

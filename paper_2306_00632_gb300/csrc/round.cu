@@ -50,6 +50,7 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
     p.norm2 = 0.0;
     p.discarded = 0.0;
     p.budget = 0.0;
+    p.abs2 = 0.0;
     p.status = 0;
     p.kz3 = p.k[2];
     p.nsplit = 0;
@@ -505,8 +506,10 @@ __global__ void demote_kernel(const RoundPlan* __restrict__ plan, const double* 
     }
 }
 
+__global__ void set_abs_kernel(RoundPlan* plan, double abs_tol) { plan->abs2 = abs_tol * abs_tol; }
+
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
-                double* info_dev, cudaStream_t st) {
+                double abs_tol, double* info_dev, cudaStream_t st) {
     const int rc = (cap > 0 && cap < c32->rank_cap) ? cap : c32->rank_cap;
     prof_begin(PK_ROUND, st);
     TPCG_TRY(round_stage12<double>(c64, y64, eps, eps_dev, rc, st));
@@ -516,6 +519,10 @@ int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, doub
                                        static_cast<float*>(c32->Qq[1]), static_cast<float*>(c32->Qq[2]));
     TPCG_CHECK_LAUNCH();
     TPCG_CUDA(cudaMemcpyAsync(c32->plan, c64->plan, sizeof(RoundPlan), cudaMemcpyDeviceToDevice, st));
+    if (abs_tol > 0) {
+        set_abs_kernel<<<1, 1, 0, st>>>(c32->plan, abs_tol);
+        TPCG_CHECK_LAUNCH();
+    }
     TPCG_TRY(round_stage34<float>(c32, out32, info_dev, st));
     prof_end(PK_ROUND, st);
     return TPCG_OK;

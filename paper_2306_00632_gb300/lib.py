@@ -24,7 +24,7 @@ SYMBOLS = [
     "tpcg_problem_destroy",
     "tpcg_ctx_create", "tpcg_ctx_bytes", "tpcg_ctx_destroy", "tucker_set_plain", "tucker_get_ranks",
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_round", "fd_precond_apply",
-    "tpcg_params_default", "tpcg_solve", "tpcg_last_error", "tpcg_version",
+    "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count",
 ]
 PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
         "fd_precond_apply": (i, [vp, vp, PT, PT, vp]),
         "tpcg_params_default": (None, [C.POINTER(Params)]),
         "tpcg_solve": (i, [vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp]),
+        "tpcg_solve_batch": (i, [i, vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp, C.POINTER(C.c_int)]),
         "tpcg_last_error": (C.c_char_p, []),
         "tpcg_profile_enable": (i, [i]),
         "tpcg_profile_reset": (i, []),
