@@ -156,6 +156,15 @@ int tucker_axpby(double a, const double* a_dev, const tucker_t* x, double b, con
                  const tucker_t* y, tucker_t* z, void* stream);
 /* *out_dev = <x, y> (Sec. 2.3 scalar product), both plain.  out_dev: device double. */
 int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, void* stream);
+/* <x, y> exactly as tucker_dot, without a context and without allocating device memory (the paper has no
+ * counterpart: this serves callers that may not allocate, e.g. code running under another party's stream
+ * capture or inside allocator callbacks).  Its scratch is one fixed device array of about 4.3 MB inside the
+ * library, sized for ranks <= 64: x->cap or y->cap above 64 returns TPCG_E_INVALID (nothing launched).
+ * x, y: plain tensors of the same n and dtype (TPCG_F64 or TPCG_F32); out_dev: device double.
+ * The first call on a device looks up the array's address (cudaGetSymbolAddress); make that call before
+ * any stream capture that is to contain it.  All callers share the array: calls that overlap on the
+ * device (other streams, other host threads) race and must be serialised by the caller. */
+int tucker_dot_static(const tucker_t* x, const tucker_t* y, double* out_dev, void* stream);
 /* In-place relative truncation, Alg. 1: y <- T_rel(y, eps) with ST-HOSVD split eps^2/3 per mode, ranks
  * clipped to rank_cap (<= 0: the context's cap).  Factors come out orthonormal, so ||y|| = ||core||.
  * If info_dev is non-NULL it receives 6 doubles: ||y||^2 before, the discarded squared norm, the new

@@ -292,6 +292,13 @@ def tucker_dot(ctx: Ctx, x: Tucker, y: Tucker, out=None, stream=None):
     return o
 
 
+def tucker_dot_static(x: Tucker, y: Tucker, out=None, stream=None):
+    """<x, y> through the allocation-free entry point (ranks <= 64, no context)."""
+    o = out if out is not None else torch.zeros(1, dtype=torch.float64, device="cuda")
+    check(L.load().tucker_dot_static(x.ref, y.ref, _dptr(o), _stream(stream)), "tucker_dot_static")
+    return o
+
+
 def tucker_round(ctx: Ctx, y: Tucker, eps, rank_cap=0, info=None, stream=None):
     ed = eps if isinstance(eps, torch.Tensor) else None
     check(L.load().tucker_round(ctx.h, y.ref, 0.0 if ed is not None else float(eps), _dptr(ed), int(rank_cap),

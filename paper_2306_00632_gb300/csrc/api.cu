@@ -628,6 +628,26 @@ extern "C" int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, doub
     return by_dtype(c->dtype, [&](auto z) { return dot_impl<decltype(z)>(c, x, y, out_dev, S(stream)); });
 }
 
+extern "C" int tucker_dot_static(const tucker_t* x, const tucker_t* y, double* out_dev, void* stream) {
+    if (!x || !y || !out_dev) {
+        set_error("tucker_dot_static: null argument");
+        return TPCG_E_INVALID;
+    }
+    TPCG_TRY(check_tensor(x, x->n, x->dtype, "tucker_dot_static x"));
+    TPCG_TRY(check_tensor(y, x->n, x->dtype, "tucker_dot_static y"));
+    if (x->dtype != TPCG_F64 && x->dtype != TPCG_F32) {
+        set_error("tucker_dot_static: dtype must be TPCG_F64 or TPCG_F32");
+        return TPCG_E_INVALID;
+    }
+    const int mr = dot_static_max_rank();
+    if (x->cap > mr || y->cap > mr) {
+        set_error("tucker_dot_static: tensor capacity " + std::to_string(std::max(x->cap, y->cap)) +
+                  " exceeds the fixed scratch limit of rank " + std::to_string(mr));
+        return TPCG_E_INVALID;
+    }
+    return by_dtype(x->dtype, [&](auto z) { return dot_static_impl<decltype(z)>(x, y, out_dev, S(stream)); });
+}
+
 extern "C" int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rank_cap,
                             double* info_dev, void* stream) {
     if (!c || (!eps_dev && !(eps >= 0.0))) return TPCG_E_INVALID;

@@ -24,6 +24,10 @@ int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const
                tucker_t* z, int* err_dev, cudaStream_t st);
 template <typename T>
 int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);
+// <x, y> with its scratch in a fixed device array (no allocation; ranks <= dot_static_max_rank())
+template <typename T>
+int dot_static_impl(const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);
+int dot_static_max_rank();
 template <typename T>
 int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st);
 template <typename T>

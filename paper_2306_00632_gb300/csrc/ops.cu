@@ -3,6 +3,9 @@
 // App. B) and tensor copies.  Shapes come from the device descriptors.
 #include <math.h>
 
+#include <mutex>
+#include <string>
+
 #include "common.cuh"
 #include "gemm.cuh"
 #include "kernels.cuh"
@@ -305,6 +308,81 @@ int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, 
 }
 template int dot_impl<double>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
 template int dot_impl<float>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
+
+// --------------------------------------------------------------------------------------------------
+// The same dot with no allocation at all, for callers that cannot call cudaMalloc: code that runs while
+// someone else's stream capture is open (an allocation there breaks the capture), allocator or driver
+// callbacks, and hosts that size every device buffer up front and forbid growth.  The scratch of the
+// context-based dot (GEMM argument slots, the three cross-Grams W_t, the two contraction buffers) lives
+// in one fixed device array of this file, sized for ranks <= DOT_STATIC_MAX_RANK in FP64.  Nothing in it
+// has to start at zero: every buffer is written (beta = 0) before it is read.  Concurrent calls share
+// the array, so calls whose executions overlap on the device race.
+// --------------------------------------------------------------------------------------------------
+constexpr int DOT_STATIC_MAX_RANK = 64;
+constexpr size_t DOT_STATIC_ARGS_OFF = 0;
+constexpr size_t DOT_STATIC_CNT_OFF = ((6 * sizeof(GemmArgs) + 255) / 256) * 256;
+constexpr size_t DOT_STATIC_W_OFF = DOT_STATIC_CNT_OFF + 256;
+constexpr size_t DOT_STATIC_T_OFF =
+    DOT_STATIC_W_OFF + ((3 * (size_t)DOT_STATIC_MAX_RANK * DOT_STATIC_MAX_RANK * sizeof(double) + 255) / 256) * 256;
+constexpr size_t DOT_STATIC_BYTES =
+    DOT_STATIC_T_OFF + 2 * (size_t)DOT_STATIC_MAX_RANK * DOT_STATIC_MAX_RANK * DOT_STATIC_MAX_RANK * sizeof(double);
+
+static __device__ __align__(256) unsigned char g_dot_scratch[DOT_STATIC_BYTES];
+
+// address of g_dot_scratch on the current device, looked up once per device (the first call on a device
+// does this set-up; make it before any stream capture that will contain the call)
+static int dot_static_scratch(unsigned char** out) {
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    TPCG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("tucker_dot_static: device ordinal out of range");
+        return TPCG_E_INVALID;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_dot_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            set_error(std::string("tucker_dot_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return TPCG_E_CUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(addr[dev]);
+    return TPCG_OK;
+}
+
+int dot_static_max_rank() { return DOT_STATIC_MAX_RANK; }
+
+template <typename T>
+int dot_static_impl(const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st) {
+    unsigned char* base = nullptr;
+    TPCG_TRY(dot_static_scratch(&base));
+    const int n = x->n, rc = DOT_STATIC_MAX_RANK;
+    GemmArgs* ga = reinterpret_cast<GemmArgs*>(base + DOT_STATIC_ARGS_OFF);
+    int* counts = reinterpret_cast<int*>(base + DOT_STATIC_CNT_OFF);
+    T* Wb = reinterpret_cast<T*>(base + DOT_STATIC_W_OFF);
+    T* Ta = reinterpret_cast<T*>(base + DOT_STATIC_T_OFF);
+    T* Tb = Ta + (long long)rc * rc * rc;
+    plan_dot_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                                         static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
+                                         static_cast<const TuckerDesc*>(y->desc), static_cast<const T*>(y->U[0]),
+                                         static_cast<const T*>(y->U[1]), static_cast<const T*>(y->U[2]), n, rc, Wb,
+                                         Ta, Tb, ga, counts);
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, rc, rc, st)));
+    TPCG_TRY((launch_gemm<T, false, false>(ga + 3, nullptr, 1, 1, rc, rc * rc, st)));
+    TPCG_TRY((launch_gemm<T, false, true>(ga + 4, nullptr, 1, rc, rc, rc, st)));
+    TPCG_TRY((launch_gemm<T, false, true>(ga + 5, nullptr, 1, 1, rc * rc, rc, st)));
+    dot_finish_kernel<T><<<1, 1024, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), Ta, out_dev, counts + 1);
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+template int dot_static_impl<double>(const tucker_t*, const tucker_t*, double*, cudaStream_t);
+template int dot_static_impl<float>(const tucker_t*, const tucker_t*, double*, cudaStream_t);
 
 // --------------------------------------------------------------------------------------------------
 // FD preconditioner, Alg. 4 with U~ = [W U_dft diag(1/mu) | V2 U2] (App. B):

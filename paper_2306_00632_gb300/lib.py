@@ -23,7 +23,7 @@ SYMBOLS = [
     "tpcg_setup", "tpcg_problem_create", "tpcg_problem_get_info", "tpcg_problem_export", "tpcg_problem_export_w",
     "tpcg_problem_destroy",
     "tpcg_ctx_create", "tpcg_ctx_bytes", "tpcg_ctx_destroy", "tucker_set_plain", "tucker_get_ranks",
-    "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_round", "fd_precond_apply",
+    "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
     "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count",
 ]
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = True):
         "tucker_residual": (i, [vp, PT, PT, vp]),
         "tucker_axpby": (i, [d, vp, PT, d, vp, PT, PT, vp]),
         "tucker_dot": (i, [vp, PT, PT, vp, vp]),
+        "tucker_dot_static": (i, [PT, PT, vp, vp]),
         "tucker_round": (i, [vp, PT, d, vp, i, vp, vp]),
         "fd_precond_apply": (i, [vp, vp, PT, PT, vp]),
         "tpcg_params_default": (None, [C.POINTER(Params)]),
