@@ -39,8 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--dtype", default="mixed", choices=["mixed", "f64", "f32"])
-    ap.add_argument("--concurrent", type=int, default=8, help="solves per step, run at once")
+    ap.add_argument("--concurrent", type=int, default=16, help="solves per step, run at once")
     ap.add_argument("--rank-cap", type=int, default=96)
+    ap.add_argument("--inner-tol", type=float, default=2e-2, help="mixed form: inner FP32 solve tolerance")
+    ap.add_argument("--refine-keep", type=float, default=3e-2, help="mixed form: accuracy kept of each correction")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -219,28 +221,32 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     main = torch.cuda.current_stream()
 
+    kw = dict(tol=TOL, rank_cap=rc, inner_tol=args.inner_tol, refine_keep=args.refine_keep)
+
     # (1) single-solve latency and the per-kernel profile (problem 0 on the main stream)
     for _ in range(max(args.warmup, 0)):
-        api.tpcg_solve(pbs[0], ctxs[0], xs[0], tol=TOL, rank_cap=rc)
+        api.tpcg_solve(pbs[0], ctxs[0], xs[0], **kw)
     torch.cuda.synchronize()
     L.tpcg_profile_reset()
     L.tpcg_profile_enable(1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     single = []
+    torch.cuda.profiler.start()   # an external profiler started with --profile-from-start off sees this region
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(main)
-        st = api.tpcg_solve(pbs[0], ctxs[0], xs[0], tol=TOL, rank_cap=rc)
+        st = api.tpcg_solve(pbs[0], ctxs[0], xs[0], **kw)
         ev[k][1].record(main)
         single.append(st)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     L.tpcg_profile_enable(0)
     lat_ms = [a.elapsed_time(b) for a, b in ev]
     prof = _profile(L, lib)
 
     # (2) throughput: K steps of B concurrent solves (tpcg_solve_batch), timed on the device
     def batch():
-        return api.tpcg_solve_batch(pbs, ctxs, xs, streams, tol=TOL, rank_cap=rc)
+        return api.tpcg_solve_batch(pbs, ctxs, xs, streams, **kw)
 
     for _ in range(max(args.warmup, 0)):
         batch()
@@ -277,7 +283,8 @@ def run_gpu(args):
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-           "config": {"workload": WORKLOAD, "solves_per_step": B,
+           "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
+                      "refine_keep": args.refine_keep,
                       "seeds": f"{SEED}..{SEED + B - 1} (amp from seed)", "tol": TOL, "rank_cap": rc,
                       "R": [p.info.R for p in pbs], "RP": pbs[0].info.RP, "parallelism": f"replicas x{ws}",
                       "l2": "256 MB buffer written between timed steps"},
@@ -293,7 +300,7 @@ def run_gpu(args):
            "clocks": clk}
 
     if rank == 0 and not args.no_e2e:
-        out["e2e"] = e2e(api, lib, pbs, dt, ctxs, xs, streams, rc, args)
+        out["e2e"] = e2e(api, lib, pbs, dt, ctxs, xs, streams, kw, args)
     if rank == 0 and not args.no_cpu and ws == 1:
         try:
             out["cpu_baseline"] = oracle_sample(int(np.median([s.iters for s in single])) or 30)
@@ -305,7 +312,7 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def e2e(api, lib, pbs, dt, ctxs, xs, streams, rc, args):
+def e2e(api, lib, pbs, dt, ctxs, xs, streams, kw, args):
     """Same metric through the public API with host inputs: every step re-creates the B problems from pinned
     host arrays (host -> device copies inside tpcg_problem_create), solves them at once and reads the
     solutions back to the host."""
@@ -327,7 +334,7 @@ def e2e(api, lib, pbs, dt, ctxs, xs, streams, rc, args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pb2 = [api.problem_from_export(ex, info, dtype=dt, pinned=True) for ex, info in exs]
-        api.tpcg_solve_batch(pb2, ctxs, xs, streams, tol=TOL, rank_cap=rc)
+        api.tpcg_solve_batch(pb2, ctxs, xs, streams, **kw)
         d2h = 0
         for x in xs:
             core, fac = x.to_numpy()

@@ -136,6 +136,7 @@ void tpcg_problem_destroy(tpcg_problem pb);
 /* Workspace for rounding, dots and TPCG on tensors with n dofs per direction, at most max_cols factor
  * columns before rounding and rank at most rank_cap after rounding. */
 int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpcg_ctx* out);
+/* Device bytes such a context holds once it has run a solve (workspace and the solver's tensors). */
 size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype);
 void tpcg_ctx_destroy(tpcg_ctx c);
 
@@ -186,8 +187,9 @@ typedef struct {
     double beta_trunc;  /* beta of eq. rel_tol_iterates                                    (0.1)   */
     int max_it;         /* iteration cap                                                   (500)   */
     int rank_cap;       /* rank cap of every truncation; <= 0: the context's cap                   */
-    double inner_tol;   /* mixed form: relative tolerance of each FP32 inner solve          (5e-2)  */
-    int max_outer;      /* mixed form: cap on FP64 residual refinements (at most 32)        (12)    */
+    double inner_tol;   /* mixed form: relative tolerance of each FP32 inner solve          (2e-2)  */
+    int max_outer;      /* mixed form: cap on FP64 residual refinements (at most 64)        (12)    */
+    double refine_keep; /* mixed form: relative accuracy to which each correction is kept in x  (3e-2) */
 } tpcg_params;
 
 typedef struct {
@@ -212,8 +214,8 @@ void tpcg_params_default(tpcg_params* p);
  * to 0.1 inner_tol relative, or to beta tol ||f~|| / 2 absolute when that is looser (the relaxation of
  * eq. rel_tol_iterates carried over to the outer loop).  It then solves A d = r by Alg. 5 in FP32 to
  * max(inner_tol, tol ||f~|| / (2 ||r||)) (dynamic-truncation floor a tenth of that, at most 12 iterations)
- * and sets x <- T_rel(x + d, delta ||d|| / ||x + d||) in FP64 (the correction kept to the accuracy delta of
- * Alg. 2's update test).  x is plain throughout, so the FP64 residual refers to the returned tensor.
+ * and sets x <- T_rel(x + d, refine_keep ||d|| / ||x + d||) in FP64.  A looser refine_keep drops the FP32
+ * rounding noise of the corrections (which later FP32 corrections cannot resolve) instead of accumulating it.  x is plain throughout, so the FP64 residual refers to the returned tensor.
  * The stopping test uses the true FP64 residual. */
 int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
 

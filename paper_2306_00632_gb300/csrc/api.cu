@@ -161,8 +161,9 @@ extern "C" void tpcg_params_default(tpcg_params* p) {
     p->beta_trunc = 0.1;
     p->max_it = 500;
     p->rank_cap = 0;
-    p->inner_tol = 5e-2;
+    p->inner_tol = 2e-2;
     p->max_outer = 12;
+    p->refine_keep = 3e-2;
 }
 
 // ======================================================================================= contexts
@@ -190,11 +191,19 @@ static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) 
     return tot;
 }
 
+// the ten solver tensors a context allocates on its first solve
+static size_t tens_bytes(int n, int max_cols, int rc, int dtype) {
+    return 10 * ((3 * (size_t)n * max_cols + (size_t)rc * rc * rc) * elt_of(dtype) + TPCG_DESC_BYTES);
+}
+
 extern "C" size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype) {
     size_t sizes[64];
     if (dtype == TPCG_MIXED)
-        return ctx_layout(n, max_cols, rank_cap, TPCG_F64, sizes) + ctx_layout(n, max_cols, rank_cap, TPCG_F32, sizes);
-    return ctx_layout(n, max_cols, rank_cap, dtype, sizes);
+        return ctx_layout(n, max_cols, rank_cap, TPCG_F64, sizes) + ctx_layout(n, max_cols, rank_cap, TPCG_F32, sizes) +
+               tens_bytes(n, max_cols, rank_cap, TPCG_F64) + tens_bytes(n, max_cols, rank_cap, TPCG_F32) +
+               2 * eig_work_bytes(n);
+    return ctx_layout(n, max_cols, rank_cap, dtype, sizes) + tens_bytes(n, max_cols, rank_cap, dtype) +
+           eig_work_bytes(n);
 }
 
 extern "C" void tpcg_ctx_destroy(tpcg_ctx c) {
@@ -839,17 +848,17 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     return status;
 }
 
-// truncation tolerance of x + d in the mixed form: the correction d is kept to relative accuracy delta
-// (the update-ratio threshold of Alg. 2), eps = delta ||d|| / ||x + d|| (x and d plain, near-orthogonal parts)
-__global__ void xeps_kernel(const double* dd, const double* xx, double delta, double* eps) {
+// truncation tolerance of x + d in the mixed form: the correction d is kept to relative accuracy `keep`,
+// eps = keep ||d|| / ||x + d|| (x and d plain)
+__global__ void xeps_kernel(const double* dd, const double* xx, double keep, double* eps) {
     const double d = fmax(*dd, 0.0), x = fmax(*xx, 0.0);
-    *eps = (d + x > 0.0) ? delta * sqrt(d / (d + x)) : 0.0;
+    *eps = (d + x > 0.0) ? keep * sqrt(d / (d + x)) : 0.0;
 }
 
 // Mixed form: iterative refinement with FP64 residuals around FP32 Alg. 5 (see tpcg.h).  The outer loop
 // carries the relaxation of Alg. 5 over to the refinement: the FP32 copy of the residual may lose
 // beta tol ||f~|| / 2 in absolute terms, and the inner solve stops at the reduction the outer target needs.
-// x stays plain: after each correction x <- T_rel(x + d, delta ||d|| / ||x + d||) in FP64, so every residual
+// x stays plain: after each correction x <- T_rel(x + d, keep ||d|| / ||x + d||) in FP64, so every residual
 // (and the stopping test) refers to the tensor that is returned.
 static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
                        cudaStream_t s) {
@@ -900,11 +909,11 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
         trials += sin.dt_trials;
         if (trace) fprintf(stderr, "mixed inner tol=%.2e iters=%d status=%d\n", in.tol, sin.iters, si);
         if (si != TPCG_OK && si != TPCG_E_NOT_CONVERGED) { status = si; break; }
-        // x <- T_rel(x + d, delta ||d|| / ||x + d||) in FP64
+        // x <- T_rel(x + d, keep ||d|| / ||x + d||) in FP64
         TPCG_TRY(promote_tensor(d32, dco, s));
         TPCG_TRY(dot_impl<double>(c, dco, dco, dd, s));
         TPCG_TRY(dot_impl<double>(c, xacc, xacc, xx, s));
-        xeps_kernel<<<1, 1, 0, s>>>(dd, xx, prm->delta, xeps);
+        xeps_kernel<<<1, 1, 0, s>>>(dd, xx, prm->refine_keep, xeps);
         TPCG_CHECK_LAUNCH();
         TPCG_TRY(axpby_impl<double>(1.0, nullptr, xacc, 1.0, nullptr, dco, xsum, nullptr, s));
         TPCG_TRY(round_impl<double>(c, xsum, 0.0, xeps, rc, nullptr, s));

@@ -17,6 +17,8 @@
 
 #include <string>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "eig.cuh"
 
@@ -26,6 +28,42 @@ template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Truncation rule of ST-HOSVD for mode m on the decreasingly sorted eigenvalues lam[0..M): the smallest s whose
+// discarded energy is <= budget, then the cap; updates p.s[m] and p.discarded.  FP64: sum of the clamped
+// discarded eigenvalues (conservative; accurate thanks to Jacobi's relative accuracy).  FP32: trace minus the
+// kept eigenvalues (unbiased; the clamped FP32 small eigenvalues are noise-dominated).  One thread.
+template <typename T>
+__device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double trace, int m) {
+    int s = M;
+    if (sizeof(T) == 8) {
+        double tail = 0.0;
+        for (int i = M - 1; i >= 0; --i) {
+            const double li = lam[i] > 0.0 ? lam[i] : 0.0;
+            if (tail + li <= p.budget) { tail += li; s = i; } else break;
+        }
+    } else {
+        double cum = 0.0;
+        for (int q = 0; q <= M; ++q) {
+            const double tail = trace - cum;
+            if (tail <= p.budget) { s = q; break; }
+            if (q < M) cum += lam[q];
+        }
+    }
+    if (s == 0 && trace > 0.0 && p.norm2 > 0.0) s = 1;
+    if (p.cap > 0 && s > p.cap) s = p.cap;
+    double disc = 0.0;
+    if (sizeof(T) == 8) {
+        for (int i = s; i < M; ++i) disc += lam[i] > 0.0 ? lam[i] : 0.0;
+    } else {
+        double cum = 0.0;
+        for (int i = 0; i < s; ++i) cum += lam[i];
+        disc = trace - cum > 0.0 ? trace - cum : 0.0;
+    }
+    p.discarded += disc;
+    p.s[m] = s;
+    return s;
 }
 
 template <typename T>
@@ -206,37 +244,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
         lam[rk] = li;
     }
     __syncthreads();
-    // truncation rule: smallest s whose discarded energy is <= budget, then the cap.  FP64: sum of the
-    // clamped discarded eigenvalues (conservative; accurate thanks to Jacobi's relative accuracy).  FP32:
-    // trace minus the kept eigenvalues (unbiased; the clamped FP32 small eigenvalues are noise-dominated).
     if (tid == 0) {
-        int s = M;
-        if (sizeof(T) == 8) {
-            double tail = 0.0;
-            for (int i = M - 1; i >= 0; --i) {
-                const double li = lam[i] > 0.0 ? lam[i] : 0.0;
-                if (tail + li <= p.budget) { tail += li; s = i; } else break;
-            }
-        } else {
-            double cum = 0.0;
-            for (int q = 0; q <= M; ++q) {
-                const double tail = s_tr - cum;
-                if (tail <= p.budget) { s = q; break; }
-                if (q < M) cum += lam[q];
-            }
-        }
-        if (s == 0 && s_tr > 0.0 && p.norm2 > 0.0) s = 1;
-        if (p.cap > 0 && s > p.cap) s = p.cap;
-        double disc = 0.0;
-        if (sizeof(T) == 8) {
-            for (int i = s; i < M; ++i) disc += lam[i] > 0.0 ? lam[i] : 0.0;
-        } else {
-            double cum = 0.0;
-            for (int i = 0; i < s; ++i) cum += lam[i];
-            disc = s_tr - cum > 0.0 ? s_tr - cum : 0.0;
-        }
-        p.discarded += disc;
-        p.s[m] = s;
+        const int s = truncation_rule<T>(p, lam, M, s_tr, m);
         s_keep = s;
         for (int i = 0; i < M; ++i) evals[i] = lam[i];
         if (prof) {   // algorithmic work: the dense symmetric eigen-decomposition count 9 M^3; Gram in, S out
@@ -248,6 +257,301 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(RoundPlan* plan, const
     const int s = s_keep;
     for (int c = 0; c < s; ++c)
         for (int i = tid; i < M; i += nt) S[i + (long long)c * n] = V[i + (long long)ord[c] * ld];
+}
+
+// ------------------------------------------------------------------------------------------------------------
+// Cluster-parallel cyclic Jacobi: one cluster of CJ_C CTAs per Gram, for n' <= CJ_MAXM.
+//
+// The M' players (matrix indices; M' = M rounded up to a multiple of 4 CJ_C, the extra ones dummies that
+// never rotate) sit in h = M'/2 pair slots, top[k] / bot[k].  CTA c owns slots [c ppc, (c+1) ppc) and keeps
+// the full COLUMNS of A and V of its 2 ppc players in shared memory (A is symmetric, so a column holds the
+// row as well).  One step of a sweep:
+//   1. each CTA computes the rotations of its own pairs (a_pp, a_qq, a_pq are in its columns) and writes them
+//      into every CTA's rotation table through distributed shared memory; cluster barrier;
+//   2. each CTA applies all h row rotations to its columns, then the column rotations of its own pairs to A
+//      and V (both columns are local), and zeroes the annihilated a_pq;
+//   3. the circle method moves every player one slot around the ring (top[0] fixed).  Inside a CTA this is a
+//      relabelling of buffers; at a CTA boundary one top column moves right and one bottom column moves left,
+//      pushed into the neighbour's landing buffers; cluster barrier; landing columns are copied into the
+//      freed buffers.
+// M'-1 steps make a sweep in which every pair meets once.  The FP64 arithmetic of a step is split over the
+// cluster's SMs, which is what matters on a part whose FP64 rate is 1/64 of FP32.
+// ------------------------------------------------------------------------------------------------------------
+constexpr int CJ_C = 8;          // CTAs per cluster (portable size)
+constexpr int CJ_THREADS = 256;
+constexpr int CJ_MAXM = 256;     // largest padded Gram
+constexpr int CJ_MAXPPC = CJ_MAXM / (2 * CJ_C);
+
+static inline int cj_padded(int M) { return ((M + 4 * CJ_C - 1) / (4 * CJ_C)) * (4 * CJ_C); }
+
+template <typename T>
+__global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
+    cjacobi_eig_kernel(RoundPlan* plan, const T* __restrict__ G, T* __restrict__ S, double* evals, int m,
+                       int max_sweeps, double* prof) {
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cluster = cgx::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    RoundPlan& p = *plan;
+    const int M = p.gM;
+    const int n = p.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (M <= 1) {   // uniform across the cluster: nothing to rotate
+        if (crank == 0 && tid == 0) {
+            double t = M == 1 ? (double)G[0] : 0.0;
+            if (m == 0) { p.norm2 = t; p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0; }
+            double lam1[1] = {t};
+            const int s = truncation_rule<T>(p, lam1, M, t, m);
+            if (M == 1) evals[0] = t;
+            if (s > 0) S[0] = T(1);
+        }
+        return;
+    }
+    const int Mp = ((M + 4 * CJ_C - 1) / (4 * CJ_C)) * (4 * CJ_C);
+    const int h = Mp / 2, ppc = h / CJ_C, lo = crank * ppc;
+    const int ncol = 2 * ppc;
+    const int ld = Mp + 1;
+    extern __shared__ unsigned char smem_raw[];
+    T* sA = reinterpret_cast<T*>(smem_raw);            // (ncol + 2) columns: slot buffers, landing top, landing bot
+    T* sV = sA + (size_t)(ncol + 2) * ld;
+    const int LT = ncol, LB = ncol + 1;
+    __shared__ T csv[2 * (CJ_MAXM / 2)];
+    __shared__ short pqv[2 * (CJ_MAXM / 2)];
+    __shared__ short tix[CJ_MAXPPC], bix[CJ_MAXPPC], topP[CJ_MAXPPC], botP[CJ_MAXPPC];
+    __shared__ short inP[2];                           // players arriving in the landing buffers (top, bot)
+    __shared__ int flags[CJ_C];
+    __shared__ int s_rot, s_keep;
+    __shared__ double lam_all[CJ_MAXM];                // CTA 0: eigenvalue of each player
+    __shared__ double lam[CJ_MAXM];
+    __shared__ short rank_of[CJ_MAXM];
+    __shared__ double s_tr;
+    // initial slots: top[k] = 2k, bot[k] = 2k + 1; buffers 0..ppc-1 top, ppc..2ppc-1 bottom
+    if (tid < ppc) {
+        tix[tid] = (short)tid;
+        bix[tid] = (short)(ppc + tid);
+        topP[tid] = (short)(2 * (lo + tid));
+        botP[tid] = (short)(2 * (lo + tid) + 1);
+    }
+    __syncthreads();
+    for (int w = tid; w < ncol * Mp; w += nt) {
+        const int j = w / Mp, i = w % Mp;
+        const int P = j < ppc ? topP[j] : botP[j - ppc];
+        const int b = j < ppc ? tix[j] : bix[j - ppc];
+        sA[b * ld + i] = (P < M && i < M) ? G[i + (long long)P * M] : T(0);
+        sV[b * ld + i] = (i == P) ? T(1) : T(0);
+    }
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
+        s_tr = t;
+        if (m == 0 && crank == 0) {
+            p.norm2 = t;
+            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+        }
+    }
+    __syncthreads();
+    const T epsr = sizeof(T) == 8 ? T(1e-15) : T(3e-7);
+    const T epsa = (T)((sizeof(T) == 8 ? 2.2e-16 : 1.2e-7) * s_tr);
+    cluster.sync();   // every CTA initialised before any remote write
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int step = 0; step < Mp - 1; ++step) {
+            // 1. rotations of the own pairs, broadcast to every CTA's table
+            if (tid < ppc) {
+                const int k = lo + tid;
+                const int Pt = topP[tid], Pb = botP[tid];
+                const int pi = Pt < Pb ? Pt : Pb, qi = Pt < Pb ? Pb : Pt;
+                const int bp = Pt < Pb ? tix[tid] : bix[tid], bq = Pt < Pb ? bix[tid] : tix[tid];
+                T c = T(1), sn = T(0);
+                if (qi < M) {
+                    const T apq = sA[bq * ld + pi];
+                    const T app = sA[bp * ld + pi], aqq = sA[bq * ld + qi];
+                    if (fabs(apq) > epsr * sqrt(fabs(app * aqq)) && fabs(apq) > epsa) {
+                        const T th = (aqq - app) / (T(2) * apq);
+                        const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+                        c = T(1) / sqrt(t * t + T(1));
+                        sn = t * c;
+                        s_rot = 1;
+                    }
+                }
+                for (int r = 0; r < CJ_C; ++r) {
+                    T* rcs = cluster.map_shared_rank(csv, r);
+                    short* rpq = cluster.map_shared_rank(pqv, r);
+                    rcs[2 * k] = c;
+                    rcs[2 * k + 1] = sn;
+                    rpq[2 * k] = (short)pi;
+                    rpq[2 * k + 1] = (short)(qi < M ? qi : -1);
+                }
+            }
+            cluster.sync();
+            // 2a. row rotations (all pairs) on the local columns; lanes run over columns (conflict-free rows)
+            for (int w = tid; w < h * ncol; w += nt) {
+                const int j = w % ncol, k = w / ncol;
+                const T sn = csv[2 * k + 1];
+                if (sn == T(0)) continue;
+                const T c = csv[2 * k];
+                const int pi = pqv[2 * k], qi = pqv[2 * k + 1];
+                T* col = sA + (j < ppc ? tix[j] : bix[j - ppc]) * ld;
+                const T x = col[pi], y = col[qi];
+                col[pi] = c * x - sn * y;
+                col[qi] = sn * x + c * y;
+            }
+            __syncthreads();
+            // 2b. column rotations of the own pairs, A and V
+            for (int w = tid; w < ppc * Mp; w += nt) {
+                const int kk = w / Mp, i = w % Mp;
+                const int k = lo + kk;
+                const T sn = csv[2 * k + 1];
+                if (sn == T(0)) continue;
+                const T c = csv[2 * k];
+                const bool topfirst = topP[kk] < botP[kk];
+                const int bp = topfirst ? tix[kk] : bix[kk], bq = topfirst ? bix[kk] : tix[kk];
+                T* Ap = sA + bp * ld;
+                T* Aq = sA + bq * ld;
+                const T x = Ap[i], y = Aq[i];
+                Ap[i] = c * x - sn * y;
+                Aq[i] = sn * x + c * y;
+                T* Vp = sV + bp * ld;
+                T* Vq = sV + bq * ld;
+                const T vx = Vp[i], vy = Vq[i];
+                Vp[i] = c * vx - sn * vy;
+                Vq[i] = sn * vx + c * vy;
+            }
+            __syncthreads();
+            if (tid < ppc) {   // the rotated pair is annihilated
+                const int k = lo + tid;
+                if (csv[2 * k + 1] != T(0)) {
+                    const int pi = pqv[2 * k], qi = pqv[2 * k + 1];
+                    const bool topfirst = topP[tid] < botP[tid];
+                    const int bp = topfirst ? tix[tid] : bix[tid], bq = topfirst ? bix[tid] : tix[tid];
+                    sA[bq * ld + pi] = T(0);
+                    sA[bp * ld + qi] = T(0);
+                }
+            }
+            __syncthreads();
+            // 3. ring move: push the boundary columns into the neighbours' landing buffers
+            const bool send_right = crank < CJ_C - 1, send_left = crank > 0;
+            if (send_right) {   // top of the last own slot -> landing top of crank + 1
+                T* rA = cluster.map_shared_rank(sA, crank + 1) + LT * ld;
+                T* rV = cluster.map_shared_rank(sV, crank + 1) + LT * ld;
+                const T* a = sA + tix[ppc - 1] * ld;
+                const T* v = sV + tix[ppc - 1] * ld;
+                for (int i = tid; i < Mp; i += nt) { rA[i] = a[i]; rV[i] = v[i]; }
+                if (tid == 0) cluster.map_shared_rank(inP, crank + 1)[0] = topP[ppc - 1];
+            }
+            if (send_left) {    // bottom of the first own slot -> landing bottom of crank - 1
+                T* rA = cluster.map_shared_rank(sA, crank - 1) + LB * ld;
+                T* rV = cluster.map_shared_rank(sV, crank - 1) + LB * ld;
+                const T* a = sA + bix[0] * ld;
+                const T* v = sV + bix[0] * ld;
+                for (int i = tid; i < Mp; i += nt) { rA[i] = a[i]; rV[i] = v[i]; }
+                if (tid == 0) cluster.map_shared_rank(inP, crank - 1)[1] = botP[0];
+            }
+            cluster.sync();
+            // relabel (one thread), then copy the landing columns into the freed buffers
+            __shared__ short fill_top, fill_bot;   // buffers that receive the landing columns (-1: none)
+            if (tid == 0) {
+                short nt_[CJ_MAXPPC], nb_[CJ_MAXPPC], ntp[CJ_MAXPPC], nbp[CJ_MAXPPC];
+                short ftop = -1, fbot = -1;
+                // tops: slot kk takes slot kk-1's top; slot 0 keeps it (CTA 0), takes the landing (others)
+                for (int kk = 1; kk < ppc; ++kk) { nt_[kk] = tix[kk - 1]; ntp[kk] = topP[kk - 1]; }
+                // bottoms: slot kk takes slot kk+1's bottom
+                for (int kk = 0; kk + 1 < ppc; ++kk) { nb_[kk] = bix[kk + 1]; nbp[kk] = botP[kk + 1]; }
+                if (crank == 0) {
+                    nt_[0] = tix[0]; ntp[0] = topP[0];
+                    nt_[1] = bix[0]; ntp[1] = botP[0];   // bot[0] -> top[1]
+                    for (int kk = 2; kk < ppc; ++kk) { nt_[kk] = tix[kk - 1]; ntp[kk] = topP[kk - 1]; }
+                } else {
+                    nt_[0] = bix[0]; ntp[0] = inP[0];     // freed bottom buffer receives the landing top
+                    ftop = bix[0];
+                }
+                if (crank == CJ_C - 1) {
+                    nb_[ppc - 1] = tix[ppc - 1]; nbp[ppc - 1] = topP[ppc - 1];   // top[h-1] -> bot[h-1]
+                } else {
+                    nb_[ppc - 1] = tix[ppc - 1]; nbp[ppc - 1] = inP[1];   // freed top buffer receives the landing bottom
+                    fbot = tix[ppc - 1];
+                }
+                for (int kk = 0; kk < ppc; ++kk) {
+                    tix[kk] = nt_[kk]; topP[kk] = ntp[kk];
+                    bix[kk] = nb_[kk]; botP[kk] = nbp[kk];
+                }
+                fill_top = ftop;
+                fill_bot = fbot;
+            }
+            __syncthreads();
+            if (fill_top >= 0)
+                for (int i = tid; i < Mp; i += nt) {
+                    sA[fill_top * ld + i] = sA[LT * ld + i];
+                    sV[fill_top * ld + i] = sV[LT * ld + i];
+                }
+            if (fill_bot >= 0)
+                for (int i = tid; i < Mp; i += nt) {
+                    sA[fill_bot * ld + i] = sA[LB * ld + i];
+                    sV[fill_bot * ld + i] = sV[LB * ld + i];
+                }
+            __syncthreads();
+        }
+        // sweep end: did any CTA rotate?  (every CTA writes its flag into every CTA, then reads locally)
+        if (tid < CJ_C) cluster.map_shared_rank(flags, tid)[crank] = s_rot;
+        cluster.sync();
+        int any = 0;
+        for (int r = 0; r < CJ_C; ++r) any |= flags[r];
+        cluster.sync();   // flags read before the next sweep may overwrite them
+        if (!any) break;
+    }
+    // eigenvalues of the real players into CTA 0
+    for (int j = tid; j < ncol; j += nt) {
+        const int P = j < ppc ? topP[j] : botP[j - ppc];
+        const int b = j < ppc ? tix[j] : bix[j - ppc];
+        if (P < M) cluster.map_shared_rank(lam_all, 0)[P] = (double)sA[b * ld + P];
+    }
+    cluster.sync();
+    if (crank == 0) {
+        // decreasing order by rank counting (ties by index), then the truncation rule
+        for (int i = tid; i < M; i += nt) {
+            const double li = lam_all[i];
+            int rk = 0;
+            for (int j = 0; j < M; ++j) {
+                const double lj = lam_all[j];
+                if (lj > li || (lj == li && j < i)) ++rk;
+            }
+            lam[rk] = li;
+            rank_of[i] = (short)rk;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int s = truncation_rule<T>(p, lam, M, s_tr, m);
+            s_keep = s;
+            for (int i = 0; i < M; ++i) evals[i] = lam[i];
+            if (prof) {
+                prof[2 * PK_EIG] += 9.0 * (double)M * M * M;
+                prof[2 * PK_EIG + 1] += (double)sizeof(T) * ((double)M * M + (double)M * s);
+            }
+        }
+        __syncthreads();
+        for (int r = 1; r < CJ_C; ++r) {
+            short* rr = cluster.map_shared_rank(rank_of, r);
+            for (int i = tid; i < M; i += nt) rr[i] = rank_of[i];
+            if (tid == 0) cluster.map_shared_rank(&s_keep, r)[0] = s_keep;
+        }
+    }
+    cluster.sync();
+    // kept eigenvectors: column rank_of[P] of S receives V's column of player P
+    const int s = s_keep;
+    for (int w = tid; w < ncol * M; w += nt) {
+        const int j = w / M, i = w % M;
+        const int P = j < ppc ? topP[j] : botP[j - ppc];
+        if (P >= M) continue;
+        const int rk = rank_of[P];
+        if (rk < s) S[i + (long long)rk * n] = sV[(j < ppc ? tix[j] : bix[j - ppc]) * ld + i];
+    }
+    cluster.sync();   // no CTA leaves while another may still address its shared memory
+}
+
+// FP64 Grams up to CJ_MAXM go to the cluster kernel (FP64 arithmetic bound); FP32 Grams stay on one CTA
+template <typename T>
+static bool use_cluster_eig(int n) {
+    return sizeof(T) == 8 && n >= 2 && cj_padded(n) <= CJ_MAXM;
 }
 
 // shared-memory layout: A (M (M+1)) and V (M (M+1)) when both fit, else A only, else neither
@@ -262,6 +566,14 @@ static size_t jacobi_smem_plan(int n, size_t elt, int* a_smem, int* v_smem) {
 
 template <typename T>
 int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int m, int n, cudaStream_t st) {
+    if (use_cluster_eig<T>(n)) {
+        const int Mp = cj_padded(n);
+        const size_t bytes = 2 * (size_t)(2 * (Mp / (2 * CJ_C)) + 2) * (Mp + 1) * sizeof(T);
+        TPCG_CUDA(cudaFuncSetAttribute(cjacobi_eig_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        cjacobi_eig_kernel<T><<<CJ_C, CJ_THREADS, bytes, st>>>(plan, G, S, evals, m, 20, prof_dev());
+        TPCG_CHECK_LAUNCH();
+        return TPCG_OK;
+    }
     int a_smem = 0, v_smem = 0;
     const size_t bytes = jacobi_smem_plan(n, sizeof(T), &a_smem, &v_smem);
     // the shared-memory opt-in is per device; set it on every launch (cheap) so that no device is missed

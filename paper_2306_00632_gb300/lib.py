@@ -60,7 +60,7 @@ class ProblemInfo(C.Structure):
 class Params(C.Structure):
     _fields_ = [("tol", C.c_double), ("eps0", C.c_double), ("eps_min", C.c_double), ("alpha", C.c_double),
                 ("delta", C.c_double), ("beta_trunc", C.c_double), ("max_it", C.c_int), ("rank_cap", C.c_int),
-                ("inner_tol", C.c_double), ("max_outer", C.c_int)]
+                ("inner_tol", C.c_double), ("max_outer", C.c_int), ("refine_keep", C.c_double)]
 
 
 class Stats(C.Structure):

@@ -1,0 +1,147 @@
+"""Continuous-batching TPCG server on one GPU.
+
+Requests (geometry, amplitude, degree, n, rank cap, tolerance) arrive over time.  Each admitted request gets
+a slot: its own solver context, solution buffers, CUDA stream and host thread, which calls ``tpcg_solve``
+(the solver's kernels are the library's; this module only schedules).  Admission is by device memory: a
+request is admitted when the bytes of its context (``tpcg_ctx_bytes``) and solution fit in the budget left by
+the requests in flight and a slot is free.  Requests that arrive while others are on the GPU are admitted as
+soon as memory and a slot free up, so their kernels overlap on the device with the running solves.
+
+Operators and preconditioner tables (``tpcg_setup``) are cached per (geometry, amplitude, degree, n, dtype):
+they are read-only during solves and shared by all requests on that geometry.
+
+Results do not depend on what else runs: every solve has its own workspace and the kernels are deterministic.
+"""
+from __future__ import annotations
+
+import dataclasses
+import threading
+import time
+
+import torch
+
+from . import api
+from . import lib as L
+
+
+@dataclasses.dataclass(frozen=True)
+class Request:
+    kind: int                 # L.GEOM_CUBE or L.GEOM_TWIST
+    amp: float
+    degree: int
+    n: int
+    rank_cap: int
+    tol: float = 1e-6
+    dtype: int = L.MIXED
+    arrival: float = 0.0      # seconds after the start of the run
+
+
+@dataclasses.dataclass
+class Result:
+    request: Request
+    status: int
+    iters: int
+    outer_iters: int
+    true_rel_res: float
+    rank: tuple
+    admitted: float           # seconds after start
+    finished: float
+    core: object = None       # host copies of the solution (when keep_solutions)
+    factors: object = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.request.arrival
+
+
+class Server:
+    def __init__(self, mem_budget_bytes: int, max_slots: int = 16, keep_solutions: bool = False):
+        self.budget = int(mem_budget_bytes)
+        self.max_slots = int(max_slots)
+        self.keep = keep_solutions
+        self._problems = {}
+        self._plock = threading.Lock()
+        self._cv = threading.Condition()
+        self._used = 0
+        self._running = 0
+
+    # ------------------------------------------------------------------ per-request resources
+    def problem(self, r: Request) -> api.Problem:
+        key = (r.kind, float(r.amp), r.degree, r.n, r.dtype)
+        with self._plock:
+            pb = self._problems.get(key)
+            if pb is None:
+                pb = api.tpcg_setup(r.kind, r.amp, r.degree, r.n, r.dtype)
+                self._problems[key] = pb
+            return pb
+
+    @staticmethod
+    def _shape(r: Request, info):
+        rc = min(r.rank_cap, r.n)
+        max_cols = max(info.R * rc + max(info.rf), info.RP * rc, 2 * rc)
+        return rc, max_cols
+
+    def footprint(self, r: Request, info) -> int:
+        """Device bytes a request holds while in flight: its context and its solution buffers."""
+        rc, max_cols = self._shape(r, info)
+        elt = 4 if r.dtype == L.F32 else 8
+        sol = elt * (3 * r.n * rc + rc ** 3) + 8192
+        return int(L.load().tpcg_ctx_bytes(r.n, max_cols, rc, r.dtype)) + sol
+
+    # ------------------------------------------------------------------ serving loop
+    def _solve(self, r: Request, pb, t0: float, admitted: float, need: int, out: list, idx: int):
+        try:
+            rc, max_cols = self._shape(r, pb.info)
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                ctx = api.Ctx(r.n, max_cols, rc, r.dtype)
+                x = api.Tucker(r.n, cap=rc, core_cap=rc ** 3, dtype=r.dtype)
+                st = api.tpcg_solve(pb, ctx, x, stream=stream, tol=r.tol, rank_cap=rc)
+                core = fac = None
+                if self.keep:
+                    core, fac = x.to_numpy()
+                stream.synchronize()
+            out[idx] = Result(r, int(st.status), int(st.iters), int(st.outer_iters), float(st.true_rel_res),
+                              tuple(st.rank), admitted, time.perf_counter() - t0, core, fac)
+            del ctx, x
+        finally:
+            with self._cv:
+                self._used -= need
+                self._running -= 1
+                self._cv.notify_all()
+
+    def run(self, requests):
+        """Serve `requests` (sorted by arrival time) and return their results in the same order."""
+        requests = sorted(requests, key=lambda q: q.arrival)
+        # operators are built before the clock starts (a cache warm-up, not part of a request)
+        infos = [self.problem(r).info for r in requests]
+        needs = [self.footprint(r, info) for r, info in zip(requests, infos)]
+        for i, need in enumerate(needs):
+            if need > self.budget:
+                raise ValueError(f"request {i} needs {need} bytes, more than the whole budget {self.budget}")
+        out = [None] * len(requests)
+        threads = []
+        t0 = time.perf_counter()
+        for i, r in enumerate(requests):
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            need = needs[i]
+            with self._cv:
+                while self._running >= self.max_slots or self._used + need > self.budget:
+                    self._cv.wait()
+                self._used += need
+                self._running += 1
+            admitted = time.perf_counter() - t0
+            th = threading.Thread(target=self._solve, args=(r, self.problem(r), t0, admitted, need, out, i))
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+        return out
+
+
+def percentiles(results, qs=(50, 99)):
+    import numpy as np
+    lat = np.array([r.latency for r in results])
+    return {f"p{q}": float(np.percentile(lat, q)) for q in qs}
