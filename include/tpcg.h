@@ -228,6 +228,40 @@ int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x,
 int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, const tpcg_params* prms, tucker_t* xs,
                      tpcg_stats* sts, void* const* streams, int* statuses);
 
+/* ------------------------------------------------------------------------------------ elasticity */
+/* Compressible linear elasticity (Sec. 5.3), b(u, v) = 2 mu (eps(u), eps(v)) + lambda (div u, div v) on the
+ * mapped cube, homogeneous Dirichlet conditions on every face and a constant body force.  The system is the
+ * 3 x 3 block matrix [A_ij] (eq. block-system-elasticity): block A_ij (test component i, trial component j) is
+ * a Kronecker sum built from the coefficients C^{ij}_{kl} = det J [mu delta_ij (G G^T)_kl + mu G_ki G_lj +
+ * lambda G_kj G_li], G = J^-1, exactly as the Poisson operator is built from Q (App. A).  A block vector is
+ * an array of three tucker_t (components 1, 2, 3); products, sums, scalar products and truncations act per
+ * block.  The preconditioner is block diagonal: block i is Alg. 4 for mu (K M M + M K M + M M K) +
+ * (lambda + mu) (K in direction i), i.e. the FD with direction weights c_t = mu + (lambda + mu) delta_ti.
+ * Forms: TPCG_F64 and TPCG_F32. */
+typedef struct tpcg_elast_s* tpcg_elast;
+
+/* Host FP64 setup of all nine blocks (force: 3 host doubles, the constant body force), then upload. */
+int tpcg_elast_setup(const tpcg_geometry* geo, int degree, int n, double lame_lambda, double lame_mu,
+                     const double* force, int dtype, tpcg_elast* out);
+/* The same from caller tables: blocks[3 i + j] describes A_ij (its rhs fields give f_i; the preconditioner
+ * tables of the diagonal blocks are used).  All nine share n, p and dtype. */
+int tpcg_elast_create(const tpcg_problem_arrays* blocks, double lame_lambda, double lame_mu, tpcg_elast* out);
+/* R[9]: Kronecker terms of every block; RP: exponential-sum length; norm_f: ||[f_1; f_2; f_3]|| (host). */
+int tpcg_elast_get_info(tpcg_elast e, int* R, int* RP, double* norm_f);
+/* y_i = sum_j A_ij x_j (unrounded; the blocks of A_ij x_j are appended to y_i's block list).  x, y: 3 tensors;
+ * y_i needs cap >= sum_j R_ij rank(x_j) and at most 128 blocks. */
+int tpcg_elast_apply(tpcg_elast e, const tucker_t* x, tucker_t* y, void* stream);
+/* y_i = f_i - sum_j A_ij x_j (unrounded). */
+int tpcg_elast_residual(tpcg_elast e, const tucker_t* x, tucker_t* y, void* stream);
+/* v_i = P~_i^-1 s_i (Alg. 4 with the direction weights of block i); s plain, v_i needs cap >= R_P rank(s_i). */
+int tpcg_elast_precond(tpcg_elast e, tpcg_ctx c, const tucker_t* s, tucker_t* v, void* stream);
+/* Alg. 5 on block vectors with x_0 = 0; x: 3 caller tensors (cap >= rank_cap, core_cap >= rank_cap^3).
+ * Uses 21 of the context's solver tensors (context: same n and dtype, max_cols >= max_i (rf_i + sum_j R_ij
+ * rank_cap) and >= R_P rank_cap).  stats: iterations, the largest rank per mode over the components,
+ * memory compression as defined in Sec. 5.3, and the true relative residual of the returned x. */
+int tpcg_elast_solve(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
+void tpcg_elast_destroy(tpcg_elast e);
+
 /* ------------------------------------------------------------------------------------ profiling */
 /* Kernel classes timed with CUDA events on the launching stream while profiling is on:
  *   0 fused last-mode GEMM of Alg. 1 step 2 (Z formation)   1 per-block mode products of step 2

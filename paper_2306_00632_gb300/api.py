@@ -199,9 +199,8 @@ def problem_from_export(ex, info, dtype=L.F64, pinned=True) -> Problem:
     return Problem(h.value, dtype)
 
 
-def tpcg_problem_create(n, p, terms, f_core, f_U, fd, dtype=L.F64) -> Problem:
-    """Problem from host arrays.  terms: list of (w, [K1, K2, K3]) dense banded n x n matrices;
-    fd: dict with lam, mu, W (dense n x n1), v2u2 (n x n2), omega, alpha, lambda_min."""
+def _problem_arrays(n, p, terms, f_core, f_U, fd, dtype, keep):
+    """tpcg_problem_arrays from host arrays (the numpy buffers are appended to `keep`)."""
     R = len(terms)
     bw = 2 * p + 1
     bands = np.zeros((R, 3, bw, n))
@@ -213,7 +212,6 @@ def tpcg_problem_create(n, p, terms, f_core, f_U, fd, dtype=L.F64) -> Problem:
                     jj = i + d - p
                     if 0 <= jj < n:
                         bands[j, t, d, i] = K[i, jj]
-    keep = []
 
     def dp(a, ct=C.c_double):
         a = np.ascontiguousarray(a, dtype=np.float64 if ct is C.c_double else np.int32)
@@ -248,6 +246,14 @@ def tpcg_problem_create(n, p, terms, f_core, f_U, fd, dtype=L.F64) -> Problem:
     a.omega = dp(fd["omega"])
     a.alpha = dp(fd["alpha"])
     a.lambda_min = float(fd["lambda_min"])
+    return a
+
+
+def tpcg_problem_create(n, p, terms, f_core, f_U, fd, dtype=L.F64) -> Problem:
+    """Problem from host arrays.  terms: list of (w, [K1, K2, K3]) dense banded n x n matrices;
+    fd: dict with lam, mu, W (dense n x n1), v2u2 (n x n2), omega, alpha, lambda_min."""
+    keep = []
+    a = _problem_arrays(n, p, terms, f_core, f_U, fd, dtype, keep)
     h = C.c_void_p()
     check(L.load().tpcg_problem_create(C.byref(a), C.byref(h)), "tpcg_problem_create")
     return Problem(h.value, dtype)
@@ -309,6 +315,14 @@ def fd_precond_apply(pb: Problem, ctx: Ctx, s: Tucker, v: Tucker, stream=None):
     check(L.load().fd_precond_apply(pb.h, ctx.h, s.ref, v.ref, _stream(stream)), "fd_precond_apply")
 
 
+def max_cols_for(info, rank_cap: int, dtype: int) -> int:
+    """Factor columns a context needs for solves of this problem at this rank cap: residuals hold the rhs
+    columns plus R rank_cap (in the mixed form the inner rhs is itself a residual of rank <= rank_cap),
+    preconditioner outputs R_P rank_cap, sums 2 rank_cap."""
+    rhs = max(max(info.rf), rank_cap) if dtype == L.MIXED else max(info.rf)
+    return max(info.R * rank_cap + rhs, info.RP * rank_cap, 2 * rank_cap)
+
+
 def tpcg_params(**kw):
     p = L.Params()
     L.load().tpcg_params_default(C.byref(p))
@@ -343,3 +357,73 @@ def tpcg_solve_batch(problems, ctxs, xs, streams, **kw):
     if code not in (0, 3):
         check(code, "tpcg_solve_batch")
     return [int(c) for c in codes], [sts[i] for i in range(k)]
+
+
+# ------------------------------------------------------------------------------------------- elasticity
+class Elast:
+    """Elasticity block system (Sec. 5.3) owned by the library."""
+
+    def __init__(self, handle, dtype):
+        self.h = C.c_void_p(handle)
+        self.dtype = dtype
+        R = (C.c_int * 9)()
+        RP = C.c_int()
+        nf = C.c_double()
+        check(L.load().tpcg_elast_get_info(self.h, R, C.byref(RP), C.byref(nf)), "tpcg_elast_get_info")
+        self.R = [R[q] for q in range(9)]
+        self.RP = RP.value
+        self.norm_f = nf.value
+
+    def __del__(self):
+        try:
+            if self.h:
+                L.load().tpcg_elast_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def tpcg_elast_setup(kind, amp, degree, n, lame_lambda, lame_mu, force, dtype=L.F64, eps_geo=0.0, eps_prec=0.0):
+    g = L.Geometry(kind, amp, eps_geo, eps_prec)
+    f = (C.c_double * 3)(*[float(v) for v in force])
+    h = C.c_void_p()
+    check(L.load().tpcg_elast_setup(C.byref(g), degree, n, float(lame_lambda), float(lame_mu), f, dtype, C.byref(h)),
+          "tpcg_elast_setup")
+    return Elast(h.value, dtype)
+
+
+def tpcg_elast_create(n, p, blocks, f, fd, lame_lambda, lame_mu, dtype=L.F64) -> Elast:
+    """blocks[i][j]: Kronecker terms of A_ij; f[i]: Tucker rhs component (core, factors); fd: FD tables."""
+    keep = []
+    arr = (L.ProblemArrays * 9)()
+    for i in range(3):
+        for j in range(3):
+            arr[3 * i + j] = _problem_arrays(n, p, blocks[i][j], f[i][0], f[i][1], fd, dtype, keep)
+    h = C.c_void_p()
+    check(L.load().tpcg_elast_create(arr, float(lame_lambda), float(lame_mu), C.byref(h)), "tpcg_elast_create")
+    return Elast(h.value, dtype)
+
+
+def _block(ts):
+    return (L.TuckerT * 3)(*[t.t for t in ts])
+
+
+def elast_apply(e: Elast, x, y, stream=None):
+    check(L.load().tpcg_elast_apply(e.h, _block(x), _block(y), _stream(stream)), "tpcg_elast_apply")
+
+
+def elast_residual(e: Elast, x, y, stream=None):
+    check(L.load().tpcg_elast_residual(e.h, _block(x), _block(y), _stream(stream)), "tpcg_elast_residual")
+
+
+def elast_precond(e: Elast, ctx: Ctx, s, v, stream=None):
+    check(L.load().tpcg_elast_precond(e.h, ctx.h, _block(s), _block(v), _stream(stream)), "tpcg_elast_precond")
+
+
+def elast_solve(e: Elast, ctx: Ctx, x, stream=None, **kw):
+    prm = tpcg_params(**kw)
+    st = L.Stats()
+    code = L.load().tpcg_elast_solve(e.h, ctx.h, C.byref(prm), _block(x), C.byref(st), _stream(stream))
+    if code not in (0, 3):
+        check(code, "tpcg_elast_solve")
+    return st

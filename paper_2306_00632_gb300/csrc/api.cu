@@ -56,12 +56,7 @@ static int upload_int(int** dst, const int* src, size_t count, std::vector<void*
 }
 
 // ------------------------------------------------------------------------------------ scalars of Alg. 5
-enum {
-    S_NF = 0, S_NR, S_ETA, S_RP, S_XI, S_OMEGA, S_EPS, S_EPSMIN, S_PXK, S_PXN, S_PP, S_V, S_DONE, S_ZQ, S_BETA,
-    S_STOP, S_RR, S_BAD, S_TRIALS, S_COUNT
-};
-enum { P_TOL = 0, P_EPS0, P_EPSMIN, P_ALPHA, P_DELTA, P_BT, P_COUNT };
-enum { OP_INIT = 0, OP_OMEGA, OP_DT, OP_RES, OP_BETA, OP_XI };
+// (slot layout in kernels.cuh)
 
 __global__ void scalar_kernel(int op, double* s, const double* prm) {
     if (threadIdx.x != 0) return;
@@ -132,7 +127,7 @@ static int by_dtype(int dtype, F&& f) {
     return TPCG_E_INVALID;
 }
 
-static int check_tensor(const tucker_t* t, int n, int dtype, const char* what) {
+int check_tensor(const tucker_t* t, int n, int dtype, const char* what) {
     if (!t || !t->desc || !t->U[0] || !t->U[1] || !t->U[2] || !t->core) {
         set_error(std::string(what) + ": null pointer in tucker_t");
         return TPCG_E_INVALID;
@@ -191,16 +186,17 @@ static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) 
     return tot;
 }
 
-// the ten solver tensors a context allocates on its first solve
-static size_t tens_bytes(int n, int max_cols, int rc, int dtype) {
-    return 10 * ((3 * (size_t)n * max_cols + (size_t)rc * rc * rc) * elt_of(dtype) + TPCG_DESC_BYTES);
+// the solver tensors a context allocates on first use: 10 for a scalar solve, 17 for the FP64 level of a mixed
+// solve (its FP64 fallback inner solve uses tensors 10..16), 21 for an elasticity solve
+static size_t tens_bytes(int n, int max_cols, int rc, int dtype, int count = 10) {
+    return count * ((3 * (size_t)n * max_cols + (size_t)rc * rc * rc) * elt_of(dtype) + TPCG_DESC_BYTES);
 }
 
 extern "C" size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype) {
     size_t sizes[64];
     if (dtype == TPCG_MIXED)
         return ctx_layout(n, max_cols, rank_cap, TPCG_F64, sizes) + ctx_layout(n, max_cols, rank_cap, TPCG_F32, sizes) +
-               tens_bytes(n, max_cols, rank_cap, TPCG_F64) + tens_bytes(n, max_cols, rank_cap, TPCG_F32) +
+               tens_bytes(n, max_cols, rank_cap, TPCG_F64, 17) + tens_bytes(n, max_cols, rank_cap, TPCG_F32) +
                2 * eig_work_bytes(n);
     return ctx_layout(n, max_cols, rank_cap, dtype, sizes) + tens_bytes(n, max_cols, rank_cap, dtype) +
            eig_work_bytes(n);
@@ -247,7 +243,7 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
     c->rank_cap = rank_cap;
     c->dtype = dtype;
     c->elt = elt_of(dtype);
-    c->have_tens = false;
+    c->have_tens = 0;
     c->tens_cap = 0;
     size_t sizes[64];
     ctx_layout(n, max_cols, rank_cap, dtype, sizes);
@@ -682,10 +678,14 @@ extern "C" int fd_precond_apply(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, 
 }
 
 // ======================================================================================= TPCG (Alg. 5)
-static int ensure_tensors(tpcg_ctx c) {
-    if (c->have_tens) return TPCG_OK;
+int tpcg::ensure_tensors(tpcg_ctx c, int count) {
+    if (count > TPCG_CTX_TENSORS) {
+        set_error("ensure_tensors: too many solver tensors requested");
+        return TPCG_E_INVALID;
+    }
+    if (c->have_tens >= count) return TPCG_OK;
     const int n = c->n, cap = c->max_cols, rc = c->rank_cap;
-    for (int i = 0; i < 10; ++i) {
+    for (int i = c->have_tens; i < count; ++i) {
         tucker_t& t = c->tens[i];
         t.dtype = c->dtype;
         t.n = n;
@@ -695,14 +695,14 @@ static int ensure_tensors(tpcg_ctx c) {
         TPCG_TRY(dmalloc(&t.core, (size_t)t.core_cap * c->elt, &c->owned));
         TPCG_TRY(dmalloc(&t.desc, TPCG_DESC_BYTES, &c->owned));
         TPCG_CUDA(cudaMemset(t.desc, 0, TPCG_DESC_BYTES));
+        c->have_tens = i + 1;
     }
-    c->have_tens = true;
     return TPCG_OK;
 }
 
 // wait on the host for the work enqueued on s so far; the thread sleeps instead of spinning, so that many
 // solver threads can share the host cores
-static int host_wait(tpcg_ctx c, cudaStream_t s) {
+int tpcg::host_wait(tpcg_ctx c, cudaStream_t s) {
     TPCG_CUDA(cudaEventRecord(c->sync_ev, s));
     TPCG_CUDA(cudaEventSynchronize(c->sync_ev));
     return TPCG_OK;
@@ -724,21 +724,26 @@ static int true_residual(tpcg_problem pb, tpcg_ctx c, const tucker_t* x, tucker_
 // Alg. 5 for the right-hand side `rhs` (the problem's f~ unless given)
 template <typename T>
 static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
-                      cudaStream_t s, const tucker_t* rhs = nullptr) {
+                      cudaStream_t s, const tucker_t* rhs = nullptr, int tbase = 0) {
     if (!rhs) rhs = &pb->f;
-    TPCG_TRY(ensure_tensors(c));
+    TPCG_TRY(ensure_tensors(c, std::max(10, tbase + 7)));
     const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
     double* sc = c->scal;
     double* dprm = c->scal + 100;
     double hp[P_COUNT] = {prm->tol, prm->eps0, prm->eps_min, prm->alpha, prm->delta, prm->beta_trunc};
     TPCG_CUDA(cudaMemcpyAsync(dprm, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
-    tucker_t* x = &c->tens[0];
-    tucker_t* r = &c->tens[1];
-    tucker_t* z = &c->tens[2];
-    tucker_t* p = &c->tens[3];
-    tucker_t* q = &c->tens[4];
-    tucker_t* big = &c->tens[5];
-    tucker_t* big2 = &c->tens[6];
+    // capacity flags of the operator apply (problem) and of the preconditioner (context), read every iteration
+    int* apply_err = reinterpret_cast<int*>(pb->d_scal + 60);
+    int* fd_err = reinterpret_cast<int*>(sc + 230);
+    TPCG_CUDA(cudaMemsetAsync(apply_err, 0, sizeof(int), s));
+    TPCG_CUDA(cudaMemsetAsync(fd_err, 0, sizeof(int), s));
+    tucker_t* x = &c->tens[tbase + 0];
+    tucker_t* r = &c->tens[tbase + 1];
+    tucker_t* z = &c->tens[tbase + 2];
+    tucker_t* p = &c->tens[tbase + 3];
+    tucker_t* q = &c->tens[tbase + 4];
+    tucker_t* big = &c->tens[tbase + 5];
+    tucker_t* big2 = &c->tens[tbase + 6];
     double* eta = sc + S_ETA;
     auto round_to = [&](tucker_t*& dst, const double* eps_dev) -> int {
         // round `big` in place, then make it the new `dst` (swap buffers)
@@ -766,8 +771,17 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     const char* tr = getenv("TPCG_TRACE");
     const bool trace = tr && tr[0] == '1';
     for (;;) {
+        int flags[2] = {0, 0};
         TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
+        TPCG_CUDA(cudaMemcpyAsync(&flags[0], apply_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TPCG_CUDA(cudaMemcpyAsync(&flags[1], fd_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         TPCG_TRY(host_wait(c, s));
+        if (flags[0] || flags[1]) {
+            set_error(std::string("tpcg_solve: an unrounded ") + (flags[0] ? "operator product" : "preconditioner output") +
+                      " exceeded the context's max_cols or the block limit");
+            status = TPCG_E_INVALID;
+            break;
+        }
         if (trace) {
             int rx[3], rr[3], rz[3], rp[3], rq[3], nb;
             tucker_get_ranks(x, rx, &nb, s);
@@ -864,8 +878,8 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
                        cudaStream_t s) {
     tpcg_problem pb32 = pb->lo;
     tpcg_ctx c32 = c->lo;
-    TPCG_TRY(ensure_tensors(c));
-    TPCG_TRY(ensure_tensors(c32));
+    TPCG_TRY(ensure_tensors(c, 10));
+    TPCG_TRY(ensure_tensors(c32, 10));
     const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
     tucker_t* xacc = &c->tens[0];
     tucker_t* xsum = &c->tens[1];
@@ -908,9 +922,23 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
         inner_total += sin.iters;
         trials += sin.dt_trials;
         if (trace) fprintf(stderr, "mixed inner tol=%.2e iters=%d status=%d\n", in.tol, sin.iters, si);
-        if (si != TPCG_OK && si != TPCG_E_NOT_CONVERGED) { status = si; break; }
+        if (si == TPCG_E_BREAKDOWN) {
+            // the FP32 curvature p.q lost its sign (truncation noise at FP32 resolution): take this correction
+            // from Alg. 5 in FP64 instead, on the FP64 residual truncated in FP64 (tensors 10..16 of the context)
+            TPCG_TRY(round_impl<double>(c, big, 0.1 * prm->inner_tol, nullptr, rc, nullptr, s));
+            tpcg_stats s64{};
+            si = solve_impl<double>(pb, c, &in, dco, &s64, s, big, 10);
+            inner_total += s64.iters;
+            trials += s64.dt_trials;
+            if (trace) fprintf(stderr, "mixed FP64 inner iters=%d status=%d\n", s64.iters, si);
+            if (si != TPCG_OK && si != TPCG_E_NOT_CONVERGED) { status = si; break; }
+        } else if (si != TPCG_OK && si != TPCG_E_NOT_CONVERGED) {
+            status = si;
+            break;
+        } else {
+            TPCG_TRY(promote_tensor(d32, dco, s));
+        }
         // x <- T_rel(x + d, keep ||d|| / ||x + d||) in FP64
-        TPCG_TRY(promote_tensor(d32, dco, s));
         TPCG_TRY(dot_impl<double>(c, dco, dco, dd, s));
         TPCG_TRY(dot_impl<double>(c, xacc, xacc, xx, s));
         xeps_kernel<<<1, 1, 0, s>>>(dd, xx, prm->refine_keep, xeps);
@@ -952,7 +980,9 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
         }
     }
     const int rfmax = std::max(pb->rf[0], std::max(pb->rf[1], pb->rf[2]));
-    const int need = std::max(pb->R * c->rank_cap + rfmax, std::max(pb->RP * c->rank_cap, 2 * c->rank_cap));
+    // residuals hold rhs columns + R rank_cap; in the mixed form the inner rhs is a residual of rank <= rank_cap
+    const int rhs_cols = pb->lo ? std::max(rfmax, c->rank_cap) : rfmax;
+    const int need = std::max(pb->R * c->rank_cap + rhs_cols, std::max(pb->RP * c->rank_cap, 2 * c->rank_cap));
     if (c->max_cols < need) {
         set_error("tpcg_solve: context max_cols " + std::to_string(c->max_cols) + " < required " +
                   std::to_string(need));

@@ -115,6 +115,8 @@ struct Buf {
 
 #include "eig.cuh"
 
+constexpr int TPCG_CTX_TENSORS = 24;   // solver tensors of a context (allocated on first use)
+
 struct tpcg_ctx_s {
     int n, max_cols, rank_cap, dtype;
     size_t elt;
@@ -139,8 +141,8 @@ struct tpcg_ctx_s {
     tpcg::EigWork eigw;  // eigensolver work area
     // TPCG iterate tensors (allocated on first solve)
     std::vector<void*> owned;
-    tucker_t tens[10];
-    bool have_tens;
+    tucker_t tens[TPCG_CTX_TENSORS];
+    int have_tens;       // solver tensors allocated so far
     int tens_cap;
     tpcg_ctx_s* lo;      // FP32 companion of a mixed-precision context (else null)
     cudaEvent_t sync_ev; // blocking-sync event for the solver's host waits (the waiting thread sleeps)

@@ -19,6 +19,9 @@ int promote_tensor(const tucker_t* src32, tucker_t* dst64, cudaStream_t st);
 template <typename T>
 int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st,
                const tucker_t* rhs = nullptr);
+// y <- y + sign A x with the new blocks appended to y's block list
+template <typename T>
+int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st);
 template <typename T>
 int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev, const tucker_t* y,
                tucker_t* z, int* err_dev, cudaStream_t st);
@@ -28,15 +31,30 @@ int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, 
 template <typename T>
 int dot_static_impl(const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);
 int dot_static_max_rank();
+// v = P~^-1 s (Alg. 4); wdir: direction weights c_t of a weighted Kronecker sum (null: all 1)
 template <typename T>
-int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st);
+int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st, const double* wdir = nullptr);
 template <typename T>
 int copy_tensor_impl(const tucker_t* src, tucker_t* dst, int n, int cap, cudaStream_t st);
 
 int set_plain(tucker_t* t, int r1, int r2, int r3, cudaStream_t st);
 int set_zero(tucker_t* t, cudaStream_t st);
 
-// TPCG scalar updates (one thread each); layout of the scalar array in solver.cu.
+// ---- Alg. 5 scalars: slots of ctx->scal (device doubles), parameters at scal + 100, update ops
+enum {
+    S_NF = 0, S_NR, S_ETA, S_RP, S_XI, S_OMEGA, S_EPS, S_EPSMIN, S_PXK, S_PXN, S_PP, S_V, S_DONE, S_ZQ, S_BETA,
+    S_STOP, S_RR, S_BAD, S_TRIALS, S_COUNT
+};
+enum { P_TOL = 0, P_EPS0, P_EPSMIN, P_ALPHA, P_DELTA, P_BT, P_COUNT };
+enum { OP_INIT = 0, OP_OMEGA, OP_DT, OP_RES, OP_BETA, OP_XI };
+// TPCG scalar updates (one thread each)
 void launch_scalar(int op, double* s, const double* prm, cudaStream_t st);
+
+// ---- solver helpers (api.cu)
+int check_tensor(const tucker_t* t, int n, int dtype, const char* what);
+// allocate the first `count` solver tensors of the context (n x max_cols factors, rank_cap^3 core)
+int ensure_tensors(tpcg_ctx c, int count);
+// wait on the host for the work enqueued on s (blocking-sync event: the thread sleeps)
+int host_wait(tpcg_ctx c, cudaStream_t s);
 
 }  // namespace tpcg

@@ -77,7 +77,7 @@ __global__ void apply_kernel(const T* __restrict__ bands, int n, int p, int R, c
 
 // output descriptor of the apply: blocks (f) + (j, b) for every term j and input block b
 __global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const double* __restrict__ w, int R,
-                                  double sign, const TuckerDesc* __restrict__ fdsc, TuckerDesc* yd, int cap,
+                                  double sign, const TuckerDesc* fdsc, TuckerDesc* yd, int cap,
                                   int* err, double* prof, int n, int p, int elt) {
     if (threadIdx.x != 0) return;
     if (prof) {   // algorithmic work of the banded products: bands read once, X read, Y written
@@ -87,9 +87,12 @@ __global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const doubl
     }
     int nb = 0;
     int base[3] = {0, 0, 0};
-    if (fdsc) {
-        for (int b = 0; b < fdsc->nblk; ++b) yd->blk[nb++] = fdsc->blk[b];
+    if (fdsc) {   // leading blocks: the rhs (residual) or y itself (append; fdsc == yd, nothing to copy)
         for (int t = 0; t < 3; ++t) base[t] = fdsc->rank[t];
+        if (fdsc == yd)
+            nb = fdsc->nblk;
+        else
+            for (int b = 0; b < fdsc->nblk; ++b) yd->blk[nb++] = fdsc->blk[b];
     }
     const int kx[3] = {xd->rank[0], xd->rank[1], xd->rank[2]};
     bool ok = (nb + R * xd->nblk <= TPCG_MAX_BLOCKS);
@@ -135,6 +138,31 @@ int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, c
     prof_end(PK_APPLY, st);
     return TPCG_OK;
 }
+// y <- y + sign A x: the R new blocks and their factor columns are appended after y's own (block sums of
+// operators, e.g. y_i = sum_j A_ij x_j of the elasticity system)
+template <typename T>
+int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st) {
+    const int n = pb->n;
+    dim3 grid((n + 127) / 128, pb->R, 3);
+    prof_begin(PK_APPLY, st);
+    apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
+                                          static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                                          static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
+                                          static_cast<T*>(y->U[0]), static_cast<T*>(y->U[1]),
+                                          static_cast<T*>(y->U[2]), y->cap, static_cast<const TuckerDesc*>(y->desc),
+                                          nullptr, nullptr, nullptr);
+    TPCG_CHECK_LAUNCH();
+    apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R, sign,
+                                        static_cast<const TuckerDesc*>(y->desc), static_cast<TuckerDesc*>(y->desc),
+                                        y->cap, reinterpret_cast<int*>(pb->d_scal + 60), prof_dev(), n, pb->p,
+                                        (int)sizeof(T));
+    TPCG_CHECK_LAUNCH();
+    prof_end(PK_APPLY, st);
+    return TPCG_OK;
+}
+template int apply_append_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, double, cudaStream_t);
+template int apply_append_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, double, cudaStream_t);
+
 template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*);
 template int apply_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*);
 
@@ -455,7 +483,8 @@ __global__ void plan_fd_kernel(const TuckerDesc* __restrict__ sd, const T* S0, c
 template <typename T>
 __global__ void fd_scale_kernel(const TuckerDesc* __restrict__ sd, const T* U0, const T* U1, const T* U2,
                                 const T* __restrict__ lam, const T* __restrict__ mu, const double* __restrict__ alpha,
-                                double lmin, int n1, int n2, int RP, T* E0, T* E1, T* E2, int vcap) {
+                                double lmin, double c0, double c1, double c2, int n1, int n2, int RP, T* E0, T* E1,
+                                T* E2, int vcap) {
     const int t = blockIdx.z;
     const int r = sd->rank[t];
     const int n = n1 + n2;
@@ -465,7 +494,8 @@ __global__ void fd_scale_kernel(const TuckerDesc* __restrict__ sd, const T* U0, 
     const T* U = t == 0 ? U0 : (t == 1 ? U1 : U2);
     T* E = t == 0 ? E0 : (t == 1 ? E1 : E2);
     const long long cols = (long long)RP * r;
-    const double aj = alpha[j] / lmin;
+    // direction weight c_t (1 for the Poisson operator; mu + (lambda + mu) delta_ti for elasticity block i)
+    const double aj = alpha[j] * (t == 0 ? c0 : (t == 1 ? c1 : c2)) / lmin;
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const T dl = (T)exp(-aj * (double)lam[l]);
         if (l < n1) {
@@ -518,7 +548,10 @@ __global__ void fd_desc_kernel(const TuckerDesc* __restrict__ sd, const double* 
 }
 
 template <typename T>
-int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st) {
+int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st, const double* wdir) {
+    const double cw[3] = {wdir ? wdir[0] : 1.0, wdir ? wdir[1] : 1.0, wdir ? wdir[2] : 1.0};
+    // weighted spectrum sum_t c_t lambda_t: its minimum is (sum_t c_t) / 3 times the unweighted lambda_min
+    const double lmin = pb->lambda_min * (cw[0] + cw[1] + cw[2]) / 3.0;
     const int n = pb->n, n1 = pb->n1, n2 = pb->n2, RP = pb->RP;
     const int rc = c->rank_cap;
     GemmArgs* ga = c->gargs + 2 * TPCG_MAX_BLOCKS + 16;
@@ -547,7 +580,7 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
     if (n2 > 0) TPCG_TRY((launch_gemm<T, true, false>(ga + 3, counts, 3, 1, n2, rc, st)));
     dim3 g2(2, RP * rc, 3);
     fd_scale_kernel<T><<<g2, 256, 0, st>>>(sd, buf[0][1], buf[1][1], buf[2][1], static_cast<const T*>(pb->d_lam),
-                                           static_cast<const T*>(pb->d_mu), pb->d_alpha, pb->lambda_min, n1, n2, RP,
+                                           static_cast<const T*>(pb->d_mu), pb->d_alpha, lmin, cw[0], cw[1], cw[2], n1, n2, RP,
                                            buf[0][2], buf[1][2], buf[2][2], v->cap);
     TPCG_CHECK_LAUNCH();
     TPCG_TRY((launch_gemm<T, false, false>(ga + 6, counts, 3, 1, n1, RP * rc, st)));
@@ -557,14 +590,14 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
                                              static_cast<T*>(v->U[1]), static_cast<T*>(v->U[2]), v->cap);
     TPCG_CHECK_LAUNCH();
     if (n2 > 0) TPCG_TRY((launch_gemm<T, false, false>(ga + 9, counts, 3, 1, n, RP * rc, st)));
-    fd_desc_kernel<<<1, 32, 0, st>>>(sd, pb->d_omega, pb->lambda_min, RP, static_cast<TuckerDesc*>(v->desc), v->cap,
+    fd_desc_kernel<<<1, 32, 0, st>>>(sd, pb->d_omega, lmin, RP, static_cast<TuckerDesc*>(v->desc), v->cap,
                                      err);
     TPCG_CHECK_LAUNCH();
     prof_end(PK_FD, st);
     return TPCG_OK;
 }
-template int fd_impl<double>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t);
-template int fd_impl<float>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t);
+template int fd_impl<double>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t, const double*);
+template int fd_impl<float>(tpcg_problem, tpcg_ctx, const tucker_t*, tucker_t*, cudaStream_t, const double*);
 
 // --------------------------------------------------------------------------------------------------
 // copies

@@ -403,11 +403,12 @@ Mat band_to_dense(const double* band, int n, int p) {
 // ---------------------------------------------------------------------------------------------- geometry
 const double CENTROID = 28.0 / (9.0 * M_PI);
 
-void coefficients(int kind, double amp, double e1, double e2, double e3, double Q[3][3], double* om) {
+// G = J^-1 and det J of the map at a parametric point (J[a][b] = dF_a / d eta_b)
+void inverse_jacobian(int kind, double amp, double e1, double e2, double e3, double Ji[3][3], double* detJ) {
     if (kind == TPCG_GEOM_CUBE) {
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) Q[a][b] = (a == b) ? 1.0 : 0.0;
-        *om = 3 * M_PI * M_PI * sin(M_PI * e1) * sin(M_PI * e2) * sin(M_PI * e3);
+            for (int b = 0; b < 3; ++b) Ji[a][b] = (a == b) ? 1.0 : 0.0;
+        *detJ = 1.0;
         return;
     }
     const double rho = 1 + e1, th = 0.5 * M_PI * e2;
@@ -427,16 +428,47 @@ void coefficients(int kind, double amp, double e1, double e2, double e3, double 
             C[a][b] = J[a1][b1] * J[a2][b2] - J[a1][b2] * J[a2][b1];
         }
     const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
-    double Ji[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) Ji[a][b] = C[b][a] / det;
+    *detJ = det;
+}
+
+// Poisson: Q = det J J^-1 J^-T and omega = det J f (App. A)
+void coefficients(int kind, double amp, double e1, double e2, double e3, double Q[3][3], double* om) {
+    double Ji[3][3], det;
+    inverse_jacobian(kind, amp, e1, e2, e3, Ji, &det);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             double v = 0;
             for (int k = 0; k < 3; ++k) v += Ji[a][k] * Ji[b][k];
             Q[a][b] = det * v;
         }
-    *om = det * 1.0;
+    if (kind == TPCG_GEOM_CUBE)
+        *om = 3 * M_PI * M_PI * sin(M_PI * e1) * sin(M_PI * e2) * sin(M_PI * e3);
+    else
+        *om = det * 1.0;
+}
+
+// Elasticity (Sec. 5.3), trial phi e_j with derivative k, test psi e_i with derivative l:
+// C[i][j][k][l] = det [mu delta_ij (G G^T)_kl + mu G_ki G_lj + lambda G_kj G_li], G = J^-1
+void elast_coefficients(int kind, double amp, double lam, double mu, double e1, double e2, double e3,
+                        double Cc[3][3][3][3], double* detJ) {
+    double G[3][3], det;
+    inverse_jacobian(kind, amp, e1, e2, e3, G, &det);
+    double GGt[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double v = 0;
+            for (int q = 0; q < 3; ++q) v += G[a][q] * G[b][q];
+            GGt[a][b] = v;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l)
+                    Cc[i][j][k][l] = det * (mu * (i == j ? 1.0 : 0.0) * GGt[k][l] + mu * G[k][i] * G[l][j] +
+                                            lam * G[k][j] * G[l][i]);
+    *detJ = det;
 }
 
 // ---------------------------------------------------------------------------------------------- Chebyshev
@@ -523,37 +555,10 @@ int expsum_sinc(double M, double eps_prec, std::vector<double>* omega, std::vect
 }
 
 // ---------------------------------------------------------------------------------------------- setup
-int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
-    const int n_el = n - p + 2;
-    if (p < 1 || p > 5 || n_el <= p || n > 1024 || (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST)) {
-        set_error("tpcg_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024 and a known geometry");
-        return TPCG_E_INVALID;
-    }
-    const double eps_geo = geo.eps_geo > 0 ? geo.eps_geo : 1e-8;
-    const double eps_prec = geo.eps_prec > 0 ? geo.eps_prec : 0.1;
-    HostProblem& H = *out;
-    Spline sp(p, n_el);
-    Quad Q = make_quad(sp);
+// Kronecker terms of sum_{k,l} int C_kl d_k phi d_l psi: per entry (k, l), ST-HOSVD of the Chebyshev samples,
+// fold the largest-rank mode (App. A, eq. matrix_CP); appended to H.w / H.bands
+static int terms_from_coeffs(Ten (&Tq)[3][3], double eps_geo, const Quad& Q, int n, int p, HostProblem& H) {
     const int bw = 2 * p + 1;
-
-    // ---- coefficient samples on the Chebyshev grid
-    Ten Tq[3][3], Tw;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) {
-            Tq[a][b].d[0] = Tq[a][b].d[1] = Tq[a][b].d[2] = NCHEB;
-            Tq[a][b].a.assign((size_t)NCHEB * NCHEB * NCHEB, 0.0);
-        }
-    Tw.d[0] = Tw.d[1] = Tw.d[2] = NCHEB;
-    Tw.a.assign((size_t)NCHEB * NCHEB * NCHEB, 0.0);
-    for (int k = 0; k < NCHEB; ++k)
-        for (int j = 0; j < NCHEB; ++j)
-            for (int i = 0; i < NCHEB; ++i) {
-                double Qv[3][3], om;
-                coefficients(geo.kind, geo.amp, cheb_pt(i), cheb_pt(j), cheb_pt(k), Qv, &om);
-                for (int a = 0; a < 3; ++a)
-                    for (int b = 0; b < 3; ++b) Tq[a][b].at(i, j, k) = Qv[a][b];
-                Tw.at(i, j, k) = om;
-            }
     double nmax = 0, nrm[3][3];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
@@ -562,8 +567,6 @@ int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
             nrm[a][b] = sqrt(s);
             nmax = std::max(nmax, nrm[a][b]);
         }
-
-    // ---- operator terms: per entry (k, l), ST-HOSVD, fold the largest-rank mode (App. A, eq. matrix_CP)
     H.w.clear();
     H.bands.clear();
     for (int k = 0; k < 3; ++k)
@@ -612,7 +615,11 @@ int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
         return TPCG_E_INVALID;
     }
 
-    // ---- rhs (App. A): core W, factors F_t[i, r] = int b_i u_{t,r}
+    return TPCG_OK;
+}
+
+// Tucker rhs (App. A): core of the samples' ST-HOSVD times `scale`, factors F_t[i, r] = int b_i u_{t,r}
+static void rhs_from_samples(const Ten& Tw, double eps_geo, const Quad& Q, int n, int p, double scale, HostProblem& H) {
     {
         Ten core;
         Mat S[3];
@@ -630,9 +637,15 @@ int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
                 }
         }
         H.f_core = core.a;
+        for (double& v : H.f_core) v *= scale;
     }
 
-    // ---- approximate eigenpairs (App. B)
+}
+
+// App. B eigenpairs (sparse sine factorization, V2 U2, Lambda~) and the exponential sum of Prop. 1
+static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_prec, HostProblem& H) {
+    const int n_el = n - p + 2;
+    const int bw = 2 * p + 1;
     const int n1 = (p % 2 == 1) ? n_el - 1 : n_el;
     const int n2 = n - n1;
     const int nc = n2 / 2;   // conditions per end: even derivatives 2k <= p - 1
@@ -799,6 +812,95 @@ int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
         set_error("tpcg_setup: no exponential sum found");
         return TPCG_E_INVALID;
     }
+    return TPCG_OK;
+}
+
+int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
+    const int n_el = n - p + 2;
+    if (p < 1 || p > 5 || n_el <= p || n > 1024 || (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST)) {
+        set_error("tpcg_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024 and a known geometry");
+        return TPCG_E_INVALID;
+    }
+    const double eps_geo = geo.eps_geo > 0 ? geo.eps_geo : 1e-8;
+    const double eps_prec = geo.eps_prec > 0 ? geo.eps_prec : 0.1;
+    HostProblem& H = *out;
+    Spline sp(p, n_el);
+    Quad Q = make_quad(sp);
+
+    // ---- coefficient samples on the Chebyshev grid
+    Ten Tq[3][3], Tw;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            Tq[a][b].d[0] = Tq[a][b].d[1] = Tq[a][b].d[2] = NCHEB;
+            Tq[a][b].a.assign((size_t)NCHEB * NCHEB * NCHEB, 0.0);
+        }
+    Tw.d[0] = Tw.d[1] = Tw.d[2] = NCHEB;
+    Tw.a.assign((size_t)NCHEB * NCHEB * NCHEB, 0.0);
+    for (int k = 0; k < NCHEB; ++k)
+        for (int j = 0; j < NCHEB; ++j)
+            for (int i = 0; i < NCHEB; ++i) {
+                double Qv[3][3], om;
+                coefficients(geo.kind, geo.amp, cheb_pt(i), cheb_pt(j), cheb_pt(k), Qv, &om);
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) Tq[a][b].at(i, j, k) = Qv[a][b];
+                Tw.at(i, j, k) = om;
+            }
+    {
+        const int st = terms_from_coeffs(Tq, eps_geo, Q, n, p, H);
+        if (st != TPCG_OK) return st;
+    }
+    rhs_from_samples(Tw, eps_geo, Q, n, p, 1.0, H);
+    return fd_tables(sp, Q, n, p, eps_prec, H);
+}
+
+
+// Elasticity (Sec. 5.3): out[3 i + j] holds block A_ij (Kronecker terms of C^{ij}_{kl}), the rhs component f_i
+// (force_i times the load of a unit body force, det J) and the shared App. B / Prop. 1 tables.
+int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double mu, const double force[3],
+                     HostProblem out[9]) {
+    const int n_el = n - p + 2;
+    if (p < 1 || p > 5 || n_el <= p || n > 1024 || (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST) ||
+        !(mu > 0) || !(lam >= 0)) {
+        set_error("tpcg_elast_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024, a known geometry, mu > 0, lambda >= 0");
+        return TPCG_E_INVALID;
+    }
+    const double eps_geo = geo.eps_geo > 0 ? geo.eps_geo : 1e-8;
+    const double eps_prec = geo.eps_prec > 0 ? geo.eps_prec : 0.1;
+    Spline sp(p, n_el);
+    Quad Q = make_quad(sp);
+    const size_t N3 = (size_t)NCHEB * NCHEB * NCHEB;
+    std::vector<Ten> Tc(81);   // [((i*3 + j)*3 + k)*3 + l]
+    for (Ten& T : Tc) {
+        T.d[0] = T.d[1] = T.d[2] = NCHEB;
+        T.a.assign(N3, 0.0);
+    }
+    Ten Tw;
+    Tw.d[0] = Tw.d[1] = Tw.d[2] = NCHEB;
+    Tw.a.assign(N3, 0.0);
+    for (int k3 = 0; k3 < NCHEB; ++k3)
+        for (int j3 = 0; j3 < NCHEB; ++j3)
+            for (int i3 = 0; i3 < NCHEB; ++i3) {
+                double C[3][3][3][3], det;
+                elast_coefficients(geo.kind, geo.amp, lam, mu, cheb_pt(i3), cheb_pt(j3), cheb_pt(k3), C, &det);
+                for (int q = 0; q < 81; ++q) Tc[q].at(i3, j3, k3) = C[q / 27][(q / 9) % 3][(q / 3) % 3][q % 3];
+                Tw.at(i3, j3, k3) = det;
+            }
+    HostProblem fdh;
+    {
+        const int st = fd_tables(sp, Q, n, p, eps_prec, fdh);
+        if (st != TPCG_OK) return st;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            HostProblem& H = out[3 * i + j];
+            H = fdh;   // App. B tables and exponential sum
+            Ten Tq[3][3];
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) Tq[k][l] = Tc[((i * 3 + j) * 3 + k) * 3 + l];
+            const int st = terms_from_coeffs(Tq, eps_geo, Q, n, p, H);
+            if (st != TPCG_OK) return st;
+            rhs_from_samples(Tw, eps_geo, Q, n, p, force[i], H);
+        }
     return TPCG_OK;
 }
 

@@ -25,6 +25,9 @@ struct HostProblem {
 };
 
 int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out);
+// elasticity (Sec. 5.3): out[3 i + j] = block A_ij with rhs component f_i and the shared FD tables
+int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double mu, const double force[3],
+                     HostProblem out[9]);
 
 // pieces exposed for the exponential-sum search (also used by tests through the C ABI of the setup)
 double expsum_error(const double* omega, const double* alpha, int R, double M, int npts);

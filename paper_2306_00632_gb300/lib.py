@@ -26,6 +26,8 @@ SYMBOLS = [
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
     "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count",
+    "tpcg_elast_setup", "tpcg_elast_create", "tpcg_elast_get_info", "tpcg_elast_apply", "tpcg_elast_residual",
+    "tpcg_elast_precond", "tpcg_elast_solve", "tpcg_elast_destroy",
 ]
 PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
               "round": 9}
@@ -117,6 +119,14 @@ def load(build_if_missing: bool = True):
         "tpcg_profile_get": (i, [i, C.POINTER(d), C.POINTER(C.c_longlong), C.POINTER(d), C.POINTER(d)]),
         "tpcg_launch_count": (C.c_longlong, []),
         "tpcg_version": (C.c_char_p, []),
+        "tpcg_elast_setup": (i, [C.POINTER(Geometry), i, i, d, d, C.POINTER(d), i, C.POINTER(vp)]),
+        "tpcg_elast_create": (i, [C.POINTER(ProblemArrays), d, d, C.POINTER(vp)]),
+        "tpcg_elast_get_info": (i, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(d)]),
+        "tpcg_elast_apply": (i, [vp, PT, PT, vp]),
+        "tpcg_elast_residual": (i, [vp, PT, PT, vp]),
+        "tpcg_elast_precond": (i, [vp, vp, PT, PT, vp]),
+        "tpcg_elast_solve": (i, [vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp]),
+        "tpcg_elast_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

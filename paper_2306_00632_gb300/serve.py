@@ -7,8 +7,9 @@ request is admitted when the bytes of its context (``tpcg_ctx_bytes``) and solut
 the requests in flight and a slot is free.  Requests that arrive while others are on the GPU are admitted as
 soon as memory and a slot free up, so their kernels overlap on the device with the running solves.
 
-Operators and preconditioner tables (``tpcg_setup``) are cached per (geometry, amplitude, degree, n, dtype):
-they are read-only during solves and shared by all requests on that geometry.
+Requests are scalar Poisson problems (``tpcg_solve``) or linear elasticity block systems (Sec. 5.3,
+``tpcg_elast_solve``).  Operators and preconditioner tables are cached per problem description: they are
+read-only during solves and shared by all requests on that geometry.
 
 Results do not depend on what else runs: every solve has its own workspace and the kernels are deterministic.
 """
@@ -32,8 +33,12 @@ class Request:
     n: int
     rank_cap: int
     tol: float = 1e-6
-    dtype: int = L.MIXED
+    dtype: int = L.MIXED      # elasticity requests run L.F64 or L.F32
     arrival: float = 0.0      # seconds after the start of the run
+    problem: str = "poisson"  # "poisson" or "elasticity" (Sec. 5.3)
+    lame_lambda: float = 0.3 / 0.52
+    lame_mu: float = 1.0 / 2.6
+    force: tuple = (0.0, 0.0, -1.0)
 
 
 @dataclasses.dataclass
@@ -66,40 +71,57 @@ class Server:
         self._running = 0
 
     # ------------------------------------------------------------------ per-request resources
-    def problem(self, r: Request) -> api.Problem:
-        key = (r.kind, float(r.amp), r.degree, r.n, r.dtype)
+    def problem(self, r: Request):
+        key = (r.problem, r.kind, float(r.amp), r.degree, r.n, r.dtype, r.lame_lambda, r.lame_mu, tuple(r.force))
         with self._plock:
             pb = self._problems.get(key)
             if pb is None:
-                pb = api.tpcg_setup(r.kind, r.amp, r.degree, r.n, r.dtype)
+                if r.problem == "elasticity":
+                    pb = api.tpcg_elast_setup(r.kind, r.amp, r.degree, r.n, r.lame_lambda, r.lame_mu, r.force, r.dtype)
+                else:
+                    pb = api.tpcg_setup(r.kind, r.amp, r.degree, r.n, r.dtype)
                 self._problems[key] = pb
             return pb
 
     @staticmethod
-    def _shape(r: Request, info):
+    def _shape(r: Request, pb):
         rc = min(r.rank_cap, r.n)
-        max_cols = max(info.R * rc + max(info.rf), info.RP * rc, 2 * rc)
-        return rc, max_cols
+        if r.problem == "elasticity":
+            rows = [sum(pb.R[3 * i:3 * i + 3]) * rc + 8 for i in range(3)]
+            return rc, max(max(rows), pb.RP * rc, 2 * rc)
+        return rc, api.max_cols_for(pb.info, rc, r.dtype)
 
-    def footprint(self, r: Request, info) -> int:
-        """Device bytes a request holds while in flight: its context and its solution buffers."""
-        rc, max_cols = self._shape(r, info)
+    def footprint(self, r: Request, pb) -> int:
+        """Device bytes a request holds while in flight: its context (with the solver tensors it allocates)
+        and its solution buffers."""
+        rc, max_cols = self._shape(r, pb)
         elt = 4 if r.dtype == L.F32 else 8
-        sol = elt * (3 * r.n * rc + rc ** 3) + 8192
-        return int(L.load().tpcg_ctx_bytes(r.n, max_cols, rc, r.dtype)) + sol
+        ncomp = 3 if r.problem == "elasticity" else 1
+        sol = ncomp * (elt * (3 * r.n * rc + rc ** 3) + 8192)
+        ctx = int(L.load().tpcg_ctx_bytes(r.n, max_cols, rc, r.dtype))
+        if r.problem == "elasticity":   # 21 solver tensors instead of the 10 counted by tpcg_ctx_bytes
+            ctx += 11 * (elt * (3 * r.n * max_cols + rc ** 3) + 8192)
+        return ctx + sol
 
     # ------------------------------------------------------------------ serving loop
     def _solve(self, r: Request, pb, t0: float, admitted: float, need: int, out: list, idx: int):
         try:
-            rc, max_cols = self._shape(r, pb.info)
+            rc, max_cols = self._shape(r, pb)
             stream = torch.cuda.Stream()
             with torch.cuda.stream(stream):
                 ctx = api.Ctx(r.n, max_cols, rc, r.dtype)
-                x = api.Tucker(r.n, cap=rc, core_cap=rc ** 3, dtype=r.dtype)
-                st = api.tpcg_solve(pb, ctx, x, stream=stream, tol=r.tol, rank_cap=rc)
                 core = fac = None
-                if self.keep:
-                    core, fac = x.to_numpy()
+                if r.problem == "elasticity":
+                    x = [api.Tucker(r.n, cap=rc, core_cap=rc ** 3, dtype=r.dtype) for _ in range(3)]
+                    st = api.elast_solve(pb, ctx, x, stream=stream, tol=r.tol, rank_cap=rc)
+                    if self.keep:
+                        parts = [xi.to_numpy() for xi in x]
+                        core, fac = [c for c, _ in parts], [f for _, f in parts]
+                else:
+                    x = api.Tucker(r.n, cap=rc, core_cap=rc ** 3, dtype=r.dtype)
+                    st = api.tpcg_solve(pb, ctx, x, stream=stream, tol=r.tol, rank_cap=rc)
+                    if self.keep:
+                        core, fac = x.to_numpy()
                 stream.synchronize()
             out[idx] = Result(r, int(st.status), int(st.iters), int(st.outer_iters), float(st.true_rel_res),
                               tuple(st.rank), admitted, time.perf_counter() - t0, core, fac)
@@ -114,8 +136,7 @@ class Server:
         """Serve `requests` (sorted by arrival time) and return their results in the same order."""
         requests = sorted(requests, key=lambda q: q.arrival)
         # operators are built before the clock starts (a cache warm-up, not part of a request)
-        infos = [self.problem(r).info for r in requests]
-        needs = [self.footprint(r, info) for r, info in zip(requests, infos)]
+        needs = [self.footprint(r, self.problem(r)) for r in requests]
         for i, need in enumerate(needs):
             if need > self.budget:
                 raise ValueError(f"request {i} needs {need} bytes, more than the whole budget {self.budget}")

@@ -55,7 +55,7 @@ def test_admission_respects_memory_budget(mods):
     lib, serve = mods
     reqs = _requests(lib, serve, lib.F64)[:4]
     srv = serve.Server(1 << 40, max_slots=8)
-    fp = [srv.footprint(r, srv.problem(r).info) for r in reqs]
+    fp = [srv.footprint(r, srv.problem(r)) for r in reqs]
     budget = max(fp)
     res = serve.Server(budget, max_slots=8).run(reqs)
     # two requests whose footprints do not fit together never overlap in time
@@ -67,3 +67,29 @@ def test_admission_respects_memory_budget(mods):
     need = budget
     with pytest.raises(ValueError, match="more than the whole budget"):
         serve.Server(need // 2, max_slots=8).run(reqs)
+
+
+def test_poisson_and_elasticity_requests_share_the_device(mods):
+    # the serving mix of Poisson and elasticity requests: each result equals the request alone
+    lib, serve = mods
+    import synth
+    arr = synth.poisson_arrivals(300.0, 6, seed=9)
+    reqs = []
+    for i in range(6):
+        if i % 2:
+            reqs.append(serve.Request(lib.GEOM_TWIST, 0.1 + 0.02 * i, 2, 12, 12, tol=1e-6, dtype=lib.F64,
+                                      arrival=float(arr[i]), problem="elasticity", lame_mu=0.3 + 0.1 * i,
+                                      lame_lambda=1.0, force=(0.0, 0.1, -1.0)))
+        else:
+            reqs.append(serve.Request(lib.GEOM_TWIST, 0.1 + 0.02 * i, 3, 16, 16, tol=1e-6, dtype=lib.MIXED,
+                                      arrival=float(arr[i])))
+    free, _ = torch.cuda.mem_get_info()
+    alone = serve.Server(free // 4, max_slots=1, keep_solutions=True).run(reqs)
+    mix = serve.Server(free // 4, max_slots=6, keep_solutions=True).run(reqs)
+    for a, b in zip(alone, mix):
+        assert a.status == b.status == 0 and b.true_rel_res <= 1e-6
+        if a.request.problem == "elasticity":
+            for i in range(3):
+                assert rel(tucker.full((b.core[i], b.factors[i])), tucker.full((a.core[i], a.factors[i]))) < 1e-13
+        else:
+            assert rel(tucker.full((b.core, b.factors)), tucker.full((a.core, a.factors))) < 1e-13
