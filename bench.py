@@ -42,10 +42,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--dtype", default="mixed", choices=["mixed", "f64", "f32"])
-    ap.add_argument("--concurrent", type=int, default=16, help="solves per step, run at once")
+    ap.add_argument("--concurrent", type=int, default=32, help="solves per step, run at once")
     ap.add_argument("--rank-cap", type=int, default=96)
     ap.add_argument("--inner-tol", type=float, default=2e-2, help="mixed form: inner FP32 solve tolerance")
     ap.add_argument("--refine-keep", type=float, default=3e-2, help="mixed form: accuracy kept of each correction")
+    ap.add_argument("--gemm-ctas-per-sm", type=int, default=2, help="grouped-GEMM CTA budget per SM (0: uncapped)")
+    ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -147,6 +149,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------------------------- replicas
+def max_over_ranks(x: float, device: str) -> float:
+    """The slowest rank's time: replicas finish when the last one does."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, solves_per_step: int, steps: int, total_ms: float) -> float:
+    """Whole-job solves/s: every rank solved `solves_per_step` problems per step (weak scaling)."""
+    return world * solves_per_step * steps / (total_ms * 1e-3)
+
+
+def rank_seeds(rank: int, solves_per_step: int):
+    """Seeds of the problems one rank solves: replicas take disjoint seed ranges."""
+    return [SEED + rank * solves_per_step + i for i in range(solves_per_step)]
+
+
 # ------------------------------------------------------------------------------------------- GPU arm
 def _profile(L, lib):
     import ctypes as C
@@ -216,10 +238,13 @@ def run_gpu(args):
     B = max(args.concurrent, 1)
     rc = min(args.rank_cap, N_DOF)
     # B problems of the same family (seeds SEED .. SEED+B-1), one context, solution and stream each
-    pbs = [_make_problem(api, lib, dt, SEED + i) for i in range(B)]
+    seeds = rank_seeds(rank, B)
+    pbs = [_make_problem(api, lib, dt, sd) for sd in seeds]
     ctxs = [_ctx_for(api, p.info, dt, rc) for p in pbs]
     xs = [api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=dt) for _ in range(B)]
-    streams = [torch.cuda.Stream() for _ in range(B)]
+    # by default the library gives each solve a stream of its own (torch's pool holds 32 streams per priority)
+    streams = [torch.cuda.Stream() for _ in range(B)] if args.torch_streams else [None] * B
+    lib.check(L.tpcg_set_option(1, args.gemm_ctas_per_sm), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     main = torch.cuda.current_stream()
 
@@ -275,19 +300,19 @@ def run_gpu(args):
     clk = clocks.stop()
     total_ms = g0.elapsed_time(g1)
     if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
 
     roof = _roofline(prof, args.dtype, lib, sum(lat_ms))
-    value = ws * B * args.steps / (total_ms * 1e-3)
+    value = job_throughput(ws, B, args.steps, total_ms)
     last = results[-1][1]
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
+                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm,
                       "refine_keep": args.refine_keep,
-                      "seeds": f"{SEED}..{SEED + B - 1} (amp from seed)", "tol": TOL, "rank_cap": rc,
+                      "seeds": f"{seeds[0]}..{seeds[-1]} on rank 0, disjoint ranges per rank (amp from seed)",
+                      "tol": TOL, "rank_cap": rc,
                       "R": [p.info.R for p in pbs], "RP": pbs[0].info.RP, "parallelism": f"replicas x{ws}",
                       "l2": "256 MB buffer written between timed steps"},
            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99)),

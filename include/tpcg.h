@@ -221,8 +221,9 @@ int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x,
 
 /* count independent solves at once (no counterpart in the paper; many-solve throughput).  Solve i is
  * tpcg_solve(pbs[i], ctxs[i], &prms[i], &xs[i], &sts[i], streams[i]) on a host thread of its own, so the
- * solves' kernels overlap on the device.  Every solve needs its own context and its own non-default
- * stream; problems may be shared (they are read-only during a solve).  statuses[i] receives each
+ * solves' kernels overlap on the device.  Every solve needs its own context and its own stream; a NULL
+ * entry runs that solve on a non-blocking stream owned by its context (created on first use).  Problems may be
+ * shared (read-only during a solve, apart from a capacity-error flag).  statuses[i] receives each
  * solve's status; the return value is TPCG_OK, else the first hard error, else TPCG_E_NOT_CONVERGED.
  * Results do not depend on what runs beside them (no shared scratch).  Turn profiling off first. */
 int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, const tpcg_params* prms, tucker_t* xs,
@@ -261,6 +262,14 @@ int tpcg_elast_precond(tpcg_elast e, tpcg_ctx c, const tucker_t* s, tucker_t* v,
  * memory compression as defined in Sec. 5.3, and the true relative residual of the returned x. */
 int tpcg_elast_solve(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tucker_t* x, tpcg_stats* st, void* stream);
 void tpcg_elast_destroy(tpcg_elast e);
+
+/* ------------------------------------------------------------------------------------ tuning */
+/* Launch-shape options (no counterpart in the paper), process-wide:
+ *   TPCG_OPT_GEMM_CTAS_PER_SM: CTA budget per SM of the grouped GEMM launches (0 = one CTA per output tile
+ *   and argument group; 1..64 caps the grid and the kernel strides over the groups; default 2, measured best
+ *   with 32 solves at once: 4.0 against 3.6 solves/s uncapped). */
+#define TPCG_OPT_GEMM_CTAS_PER_SM 1
+int tpcg_set_option(int key, long long value);
 
 /* ------------------------------------------------------------------------------------ profiling */
 /* Kernel classes timed with CUDA events on the launching stream while profiling is on:

@@ -351,7 +351,7 @@ def tpcg_solve_batch(problems, ctxs, xs, streams, **kw):
     pbs = (C.c_void_p * k)(*[p.h for p in problems])
     cts = (C.c_void_p * k)(*[c.h for c in ctxs])
     ts = (L.TuckerT * k)(*[x.t for x in xs])
-    ss = (C.c_void_p * k)(*[s.cuda_stream for s in streams])
+    ss = (C.c_void_p * k)(*[(s.cuda_stream if s is not None else None) for s in streams])
     codes = (C.c_int * k)()
     code = L.load().tpcg_solve_batch(k, pbs, cts, prm, ts, sts, ss, codes)
     if code not in (0, 3):

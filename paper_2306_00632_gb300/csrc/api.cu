@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gemm.cuh"
 #include "kernels.cuh"
 #include "setup.h"
 
@@ -206,6 +207,8 @@ extern "C" void tpcg_ctx_destroy(tpcg_ctx c) {
     if (!c) return;
     if (c->lo) tpcg_ctx_destroy(c->lo);
     if (c->sync_ev) cudaEventDestroy(c->sync_ev);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    for (auto& g : c->rgraphs) cudaGraphExecDestroy(g.exec);
     for (void* p : c->owned) cudaFree(p);
     delete c;
 }
@@ -228,9 +231,13 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
         set_error("tpcg_ctx_create: invalid arguments (need 2 <= n <= 1024, 1 <= rank_cap <= min(n, 256))");
         return TPCG_E_INVALID;
     }
+    // per-device launch attributes are settled here, outside any stream capture
+    TPCG_TRY(eig_prepare());
+    (void)sm_count();
     tpcg_ctx c = new tpcg_ctx_s();
     c->lo = nullptr;
     c->sync_ev = nullptr;
+    c->own_stream = nullptr;
     if (cudaEventCreateWithFlags(&c->sync_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         c->sync_ev = nullptr;
@@ -747,14 +754,14 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     double* eta = sc + S_ETA;
     auto round_to = [&](tucker_t*& dst, const double* eps_dev) -> int {
         // round `big` in place, then make it the new `dst` (swap buffers)
-        TPCG_TRY(round_impl<T>(c, big, 0.0, eps_dev, rc, nullptr, s));
+        TPCG_TRY(round_cached<T>(c, big, eps_dev, rc, s));
         std::swap(dst, big);
         return TPCG_OK;
     };
     // x_0 = 0, r_0 = f
     TPCG_TRY(set_zero(x, s));
     TPCG_TRY(copy_tensor_impl<T>(rhs, r, c->n, c->max_cols, s));
-    TPCG_TRY(dot_impl<T>(c, r, r, sc + S_RR, s));
+    TPCG_TRY(dot_cached<T>(c, r, r, sc + S_RR, s));
     launch_scalar(OP_INIT, sc, dprm, s);
     // z_0 = T(P^-1 r_0, eta_0), p_0 = z_0, q_0 = T(A p_0, eta_0), xi_0 = p_0 . q_0
     TPCG_TRY(fd_impl<T>(pb, c, r, big, s));
@@ -762,7 +769,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     TPCG_TRY(copy_tensor_impl<T>(z, p, c->n, c->max_cols, s));
     TPCG_TRY(apply_impl<T>(pb, p, big, false, s));
     TPCG_TRY(round_to(q, eta));
-    TPCG_TRY(dot_impl<T>(c, p, q, sc + S_XI, s));
+    TPCG_TRY(dot_cached<T>(c, p, q, sc + S_XI, s));
     launch_scalar(OP_XI, sc, dprm, s);
     double host[S_COUNT];
     int k = 0;
@@ -800,16 +807,16 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         if (host[S_STOP] != 0.0) break;
         if (k >= prm->max_it) { status = TPCG_E_NOT_CONVERGED; break; }
         // omega_k = r_k . p_k / xi_k
-        TPCG_TRY(dot_impl<T>(c, r, p, sc + S_RP, s));
+        TPCG_TRY(dot_cached<T>(c, r, p, sc + S_RP, s));
         launch_scalar(OP_OMEGA, sc, dprm, s);
         // dynamic truncation of x_k + omega_k p_k (Alg. 2)
-        TPCG_TRY(dot_impl<T>(c, p, x, sc + S_PXK, s));
-        TPCG_TRY(dot_impl<T>(c, p, p, sc + S_PP, s));
+        TPCG_TRY(dot_cached<T>(c, p, x, sc + S_PXK, s));
+        TPCG_TRY(dot_cached<T>(c, p, p, sc + S_PP, s));
         TPCG_TRY(axpby_impl<T>(1.0, nullptr, x, 0.0, sc + S_OMEGA, p, big, nullptr, s));
         for (int trial = 0;; ++trial) {
             TPCG_TRY(copy_tensor_impl<T>(big, big2, c->n, c->max_cols, s));
-            TPCG_TRY(round_impl<T>(c, big2, 0.0, sc + S_EPS, rc, nullptr, s));
-            TPCG_TRY(dot_impl<T>(c, p, big2, sc + S_PXN, s));
+            TPCG_TRY(round_cached<T>(c, big2, sc + S_EPS, rc, s));
+            TPCG_TRY(dot_cached<T>(c, p, big2, sc + S_PXN, s));
             launch_scalar(OP_DT, sc, dprm, s);
             ++trials_total;
             double done;
@@ -821,12 +828,12 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         // r_{k+1} = T(f - A x_{k+1}, eta_k); eta_{k+1}
         TPCG_TRY(apply_impl<T>(pb, x, big, true, s, rhs));
         TPCG_TRY(round_to(r, eta));
-        TPCG_TRY(dot_impl<T>(c, r, r, sc + S_RR, s));
+        TPCG_TRY(dot_cached<T>(c, r, r, sc + S_RR, s));
         launch_scalar(OP_RES, sc, dprm, s);
         // z_{k+1} = T(P^-1 r_{k+1}, eta_{k+1});  beta_k = -z_{k+1} . q_k / xi_k
         TPCG_TRY(fd_impl<T>(pb, c, r, big, s));
         TPCG_TRY(round_to(z, eta));
-        TPCG_TRY(dot_impl<T>(c, z, q, sc + S_ZQ, s));
+        TPCG_TRY(dot_cached<T>(c, z, q, sc + S_ZQ, s));
         launch_scalar(OP_BETA, sc, dprm, s);
         // p_{k+1} = T(z_{k+1} + beta_k p_k, eta_{k+1})
         TPCG_TRY(axpby_impl<T>(1.0, nullptr, z, 0.0, sc + S_BETA, p, big, nullptr, s));
@@ -834,7 +841,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         // q_{k+1} = T(A p_{k+1}, eta_{k+1});  xi_{k+1} = p_{k+1} . q_{k+1}
         TPCG_TRY(apply_impl<T>(pb, p, big, false, s));
         TPCG_TRY(round_to(q, eta));
-        TPCG_TRY(dot_impl<T>(c, p, q, sc + S_XI, s));
+        TPCG_TRY(dot_cached<T>(c, p, q, sc + S_XI, s));
         launch_scalar(OP_XI, sc, dprm, s);
         ++k;
     }
@@ -1003,7 +1010,7 @@ extern "C" int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_c
     for (int i = 0; i < count; ++i)
         for (int j = 0; j < i; ++j)
             if (ctxs[i] == ctxs[j] || (streams[i] && streams[i] == streams[j])) {
-                set_error("tpcg_solve_batch: every solve needs its own context and its own (non-default) stream");
+                set_error("tpcg_solve_batch: every solve needs its own context and its own stream (or NULL)");
                 return TPCG_E_INVALID;
             }
     int dev = 0;
@@ -1018,8 +1025,19 @@ extern "C" int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_c
                 errs[i] = "cudaSetDevice failed in a solver thread";
                 return;
             }
-            statuses[i] = tpcg_solve(pbs[i], ctxs[i], &prms[i], &xs[i], sts ? &sts[i] : nullptr, streams[i]);
+            // a NULL stream entry: the solve runs on its context's own stream (created once, kept with the
+            // context so that its captured graphs keep launching on the same stream)
+            if (!streams[i] && !ctxs[i]->own_stream &&
+                cudaStreamCreateWithFlags(&ctxs[i]->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                ctxs[i]->own_stream = nullptr;
+                statuses[i] = TPCG_E_CUDA;
+                errs[i] = "cudaStreamCreateWithFlags failed in a solver thread";
+                return;
+            }
+            cudaStream_t st = streams[i] ? static_cast<cudaStream_t>(streams[i]) : ctxs[i]->own_stream;
+            statuses[i] = tpcg_solve(pbs[i], ctxs[i], &prms[i], &xs[i], sts ? &sts[i] : nullptr, st);
             if (statuses[i] != TPCG_OK) errs[i] = tpcg_last_error();
+            cudaStreamSynchronize(st);
         });
     }
     for (auto& t : th) t.join();

@@ -18,6 +18,7 @@ void set_error(const std::string& msg);
 
 // ------------------------------------------------------------------------------------ profiling
 extern std::atomic<long long> g_launches;
+extern thread_local long long t_launches;   // launches (or captured kernel nodes) issued by this thread
 enum { PK_ZGEMM = 0, PK_ZBLK, PK_GRAM, PK_EIG, PK_PROJ, PK_QR, PK_APPLY, PK_FD, PK_DOT, PK_ROUND, PK_FINAL,
        PK_COUNT = 16 };
 bool prof_on();
@@ -37,6 +38,7 @@ void prof_end(int kind, cudaStream_t st);
 #define TPCG_CHECK_LAUNCH()                                                               \
     do {                                                                                  \
         ::tpcg::g_launches.fetch_add(1, std::memory_order_relaxed);                       \
+        ++::tpcg::t_launches;                                                             \
         cudaError_t e_ = cudaGetLastError();                                              \
         if (e_ != cudaSuccess) {                                                          \
             ::tpcg::set_error(std::string("kernel launch: ") + cudaGetErrorString(e_));   \
@@ -146,6 +148,17 @@ struct tpcg_ctx_s {
     int tens_cap;
     tpcg_ctx_s* lo;      // FP32 companion of a mixed-precision context (else null)
     cudaEvent_t sync_ev; // blocking-sync event for the solver's host waits (the waiting thread sleeps)
+    cudaStream_t own_stream;   // created on first use by tpcg_solve_batch for NULL stream entries
+    // captured roundings (CUDA graphs) of the solver tensors, keyed by tensor and tolerance source
+    struct RoundGraph {
+        const void* desc;
+        const void* U0;
+        const double* eps_dev;
+        int rc;
+        cudaGraphExec_t exec;
+        long long nkern;
+    };
+    std::vector<RoundGraph> rgraphs;
 };
 
 struct tpcg_problem_s {

@@ -16,6 +16,8 @@ struct EigWork {
 };
 
 size_t eig_work_bytes(int n);
+// shared-memory opt-ins of the eigensolver kernels on the current device (before any stream capture)
+int eig_prepare();
 int eig_work_alloc(EigWork* w, int n, std::vector<void*>* owned);
 
 // Eigen-decomposition (Jacobi) of the plan's current Gram G (gM x gM, ld gM), truncation rule of mode m, kept

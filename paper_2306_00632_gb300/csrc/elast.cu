@@ -69,7 +69,7 @@ static int elast_precond_impl(tpcg_elast e, tpcg_ctx c, tucker_t* const* s, tuck
 template <typename T>
 static int elast_dot_impl(tpcg_ctx c, tucker_t* const* x, tucker_t* const* y, double* out, cudaStream_t st) {
     double* part = c->scal + 160;
-    for (int i = 0; i < 3; ++i) TPCG_TRY(dot_impl<T>(c, x[i], y[i], part + i, st));
+    for (int i = 0; i < 3; ++i) TPCG_TRY(dot_cached<T>(c, x[i], y[i], part + i, st));
     sum3_kernel<<<1, 1, 0, st>>>(part, out);
     TPCG_CHECK_LAUNCH();
     return TPCG_OK;
@@ -107,7 +107,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
         for (int i = 0; i < 3; ++i) std::swap(a[i], b[i]);
     };
     auto bround = [&](tucker_t** y, const double* eps_dev) -> int {
-        for (int i = 0; i < 3; ++i) TPCG_TRY(round_impl<T>(c, y[i], 0.0, eps_dev, rc, nullptr, s));
+        for (int i = 0; i < 3; ++i) TPCG_TRY(round_cached<T>(c, y[i], eps_dev, rc, s));
         return TPCG_OK;
     };
     auto bcopy = [&](tucker_t** a, tucker_t** b) -> int {

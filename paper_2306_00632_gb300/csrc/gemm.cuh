@@ -6,6 +6,8 @@
 // registers; operands staged through shared memory with loads coalesced along the contiguous index.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tpcg {
@@ -134,12 +136,36 @@ __global__ void reduce_partials_kernel(const T* __restrict__ P, const int* Mdev,
     }
 }
 
+// CTA budget per SM of a grouped GEMM launch (0: one CTA per output tile and group, uncapped); set through
+// tpcg_set_option
+int gemm_ctas_per_sm();
+
+// multiprocessors of the current device (queried once per device)
+inline int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+
 template <typename T, bool TA, bool TB>
 inline int launch_gemm(const GemmArgs* args, const int* count_dev, int ngroups_max, int bmax, int Mmax, int Nmax,
                        cudaStream_t st) {
     if (ngroups_max <= 0 || bmax <= 0 || Mmax <= 0 || Nmax <= 0) return TPCG_OK;
     const long long zmax = (long long)ngroups_max * bmax;
-    dim3 grid((Mmax + GBM - 1) / GBM, (Nmax + GBN - 1) / GBN, (unsigned)(zmax < 65535 ? zmax : 65535));
+    // the kernel strides over z, so the grid can be capped at a CTA budget per SM: argument lists sized for
+    // the worst case (most groups empty at run time) then do not flood the CTA scheduler
+    const long long gx = (Mmax + GBM - 1) / GBM, gy = (Nmax + GBN - 1) / GBN;
+    const int per_sm = gemm_ctas_per_sm();
+    const long long zcap = per_sm > 0 ? std::max(1LL, ((long long)per_sm * sm_count()) / std::max(1LL, gx * gy))
+                                      : zmax;
+    const long long gz = std::min(std::min(zmax, zcap), 65535LL);
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz);
     if (grid.y > 65535u || zmax > (1LL << 30)) {
         set_error("gemm grid too large");
         return TPCG_E_INVALID;

@@ -9,6 +9,9 @@ template <typename T>
 int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
                cudaStream_t st);
 // FP64 Z formation, FP32 ST-HOSVD into out32; the discarded energy may also reach abs_tol^2 (absolute norm floor)
+// round_impl(c, y, 0, eps_dev, cap) replayed from a per-context CUDA graph (captured on first use)
+template <typename T>
+int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st);
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
                 double abs_tol, double* info_dev, cudaStream_t st);
 // ||y||^2 of any (block) tensor by the Z formation of Alg. 1
@@ -27,6 +30,9 @@ int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const
                tucker_t* z, int* err_dev, cudaStream_t st);
 template <typename T>
 int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);
+// dot_impl replayed from a per-context CUDA graph keyed by (x, y, out)
+template <typename T>
+int dot_cached(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);
 // <x, y> with its scratch in a fixed device array (no allocation; ranks <= dot_static_max_rank())
 template <typename T>
 int dot_static_impl(const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st);

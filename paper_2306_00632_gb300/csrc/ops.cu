@@ -337,6 +337,45 @@ int dot_impl(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, 
 template int dot_impl<double>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
 template int dot_impl<float>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
 
+// dot_impl replayed from a per-context CUDA graph keyed by (x, y, out), as round_cached
+template <typename T>
+int dot_cached(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, cudaStream_t st) {
+    if (prof_on() || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+        return dot_impl<T>(c, x, y, out_dev, st);
+    for (const auto& g : c->rgraphs)
+        if (g.rc == -1 && g.desc == x->desc && g.U0 == y->desc && g.eps_dev == out_dev) {
+            TPCG_CUDA(cudaGraphLaunch(g.exec, st));
+            g_launches.fetch_add(g.nkern, std::memory_order_relaxed);
+            return TPCG_OK;
+        }
+    const long long k0 = t_launches;
+    TPCG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int s = dot_impl<T>(c, x, y, out_dev, st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != TPCG_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (s != TPCG_OK) return s;
+        set_error(std::string("dot_cached: stream capture failed: ") + cudaGetErrorString(e));
+        return TPCG_E_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("dot_cached: graph instantiation failed: ") + cudaGetErrorString(ei));
+        return TPCG_E_CUDA;
+    }
+    c->rgraphs.push_back({x->desc, y->desc, out_dev, -1, exec, t_launches - k0});
+    TPCG_CUDA(cudaGraphLaunch(exec, st));
+    return TPCG_OK;
+}
+template int dot_cached<double>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
+template int dot_cached<float>(tpcg_ctx, const tucker_t*, const tucker_t*, double*, cudaStream_t);
+
+
 // --------------------------------------------------------------------------------------------------
 // The same dot with no allocation at all, for callers that cannot call cudaMalloc: code that runs while
 // someone else's stream capture is open (an allocation there breaks the capture), allocator or driver

@@ -9,6 +9,7 @@
 namespace tpcg {
 
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
 
 namespace {
 struct EvPair {
@@ -110,4 +111,18 @@ extern "C" int tpcg_profile_get(int kind, double* ms_total, long long* count, do
     if (flops) *flops = h[0];
     if (bytes) *bytes = h[1];
     return TPCG_OK;
+}
+
+namespace tpcg {
+static std::atomic<int> g_gemm_ctas_per_sm{2};
+int gemm_ctas_per_sm() { return g_gemm_ctas_per_sm.load(std::memory_order_relaxed); }
+}  // namespace tpcg
+
+extern "C" int tpcg_set_option(int key, long long value) {
+    if (key == TPCG_OPT_GEMM_CTAS_PER_SM && value >= 0 && value <= 64) {
+        tpcg::g_gemm_ctas_per_sm.store((int)value);
+        return TPCG_OK;
+    }
+    tpcg::set_error("tpcg_set_option: unknown key or value out of range");
+    return TPCG_E_INVALID;
 }

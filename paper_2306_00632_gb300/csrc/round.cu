@@ -14,6 +14,8 @@
 // sequence of launches without synchronising.
 #include <math.h>
 
+#include <string>
+
 #include "common.cuh"
 #include "gemm.cuh"
 #include "eig.cuh"
@@ -488,6 +490,48 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
     prof_end(PK_ROUND, st);
     return TPCG_OK;
 }
+
+// round_impl captured once per (tensor, device tolerance, cap) into a CUDA graph and replayed: the ~30
+// launches of a truncation become one graph launch, which matters when many solves share the host.  The
+// launch sequence of a truncation does not depend on ranks (all sizes are read on the device), so the
+// replay is exact.  Falls back to direct launches while profiling or on the legacy default stream.
+template <typename T>
+int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st) {
+    const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
+    if (prof_on() || !eps_dev || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+        return round_impl<T>(c, y, 0.0, eps_dev, cap, nullptr, st);
+    for (const auto& g : c->rgraphs)
+        if (g.desc == y->desc && g.U0 == y->U[0] && g.eps_dev == eps_dev && g.rc == rc) {
+            TPCG_CUDA(cudaGraphLaunch(g.exec, st));
+            g_launches.fetch_add(g.nkern, std::memory_order_relaxed);
+            return TPCG_OK;
+        }
+    const long long k0 = t_launches;
+    TPCG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int s = round_impl<T>(c, y, 0.0, eps_dev, rc, nullptr, st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != TPCG_OK || e != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (s != TPCG_OK) return s;
+        set_error(std::string("round_cached: stream capture failed: ") + cudaGetErrorString(e));
+        return TPCG_E_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("round_cached: graph instantiation failed: ") + cudaGetErrorString(ei));
+        return TPCG_E_CUDA;
+    }
+    c->rgraphs.push_back({y->desc, y->U[0], eps_dev, rc, exec, t_launches - k0});
+    TPCG_CUDA(cudaGraphLaunch(exec, st));   // the kernels counted during capture run now
+    return TPCG_OK;
+}
+template int round_cached<double>(tpcg_ctx, tucker_t*, const double*, int, cudaStream_t);
+template int round_cached<float>(tpcg_ctx, tucker_t*, const double*, int, cudaStream_t);
 
 // Mixed rounding: Alg. 1 steps 1-2 in FP64 (the Z formation carries the cancellation of a residual), then
 // steps 3-4 in FP32 on the rounded Z.  y64 is an FP64 (block) tensor, out32 receives an FP32 plain tensor.

@@ -25,7 +25,7 @@ SYMBOLS = [
     "tpcg_ctx_create", "tpcg_ctx_bytes", "tpcg_ctx_destroy", "tucker_set_plain", "tucker_get_ranks",
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
     "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_last_error", "tpcg_version",
-    "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count",
+    "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count", "tpcg_set_option",
     "tpcg_elast_setup", "tpcg_elast_create", "tpcg_elast_get_info", "tpcg_elast_apply", "tpcg_elast_residual",
     "tpcg_elast_precond", "tpcg_elast_solve", "tpcg_elast_destroy",
 ]
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
         "tpcg_profile_reset": (i, []),
         "tpcg_profile_get": (i, [i, C.POINTER(d), C.POINTER(C.c_longlong), C.POINTER(d), C.POINTER(d)]),
         "tpcg_launch_count": (C.c_longlong, []),
+        "tpcg_set_option": (i, [i, C.c_longlong]),
         "tpcg_version": (C.c_char_p, []),
         "tpcg_elast_setup": (i, [C.POINTER(Geometry), i, i, d, d, C.POINTER(d), i, C.POINTER(vp)]),
         "tpcg_elast_create": (i, [C.POINTER(ProblemArrays), d, d, C.POINTER(vp)]),
