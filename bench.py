@@ -19,6 +19,10 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# concurrent solves run on separate streams: give the device as many hardware work queues as it has
+# (the default of 8 makes streams beyond the eighth share queues and wait on each other's kernels); this must
+# be set before the CUDA context exists
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
@@ -194,6 +198,9 @@ def _roofline(prof, dt_name, lib, step_ms_total):
     # (bf16 2250, FP32 75, FP64 1.25 TFLOP/s dense nominal)
     alu = {"f64": bf16 * 1.25 / 2250.0, "f32": bf16 * 75.0 / 2250.0}
     classes = ["zgemm", "zblk", "gram", "eig", "proj", "qr", "apply", "fd"]
+    # DRAM bytes per launch of the FP32 eigensolver from one ncu capture of this workload (dram__bytes_read.sum +
+    # dram__bytes_write.sum, mean of 3 launches); other kernels: no capture, traffic null
+    ncu_traffic = {"eig": 58539.0} if dt_name == "mixed" else {}
     dom = max(classes, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     per_launch_ms = d["ms"] / max(d["launches"], 1)
@@ -210,7 +217,7 @@ def _roofline(prof, dt_name, lib, step_ms_total):
         pk = alu[prec]
         ach = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
         roof.update({"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                     "traffic": None,
+                     "traffic": ncu_traffic.get(dom),
                      "peak_source": f"{prec.upper()} SIMT peak = bf16_tflops_sustained {src} x nominal "
                                     f"{'75' if prec == 'f32' else '1.25'}/2250"})
     return roof

@@ -276,7 +276,8 @@ int tpcg_set_option(int key, long long value);
  *   0 fused last-mode GEMM of Alg. 1 step 2 (Z formation)   1 per-block mode products of step 2
  *   2 mode Grams of ST-HOSVD (split-K GEMM + reduction)       3 eigensolver + truncation rule
  *   4 ST-HOSVD projections   5 Householder QR   6 banded matvec (apply/residual)   7 FD application
- *   8 Tucker dot   9 whole tucker_round   10 reserved.
+ *   8 Tucker dot   9 whole tucker_round   10 reserved   11 one-CTA Jacobi sweeps (flops field: sweeps,
+ *   bytes field: Grams; no time).
  * flops/bytes are the algorithmic work of the launches (accumulated on the device from the actual ranks). */
 #define TPCG_PROF_KINDS 16
 int tpcg_profile_enable(int on);

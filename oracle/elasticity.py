@@ -16,7 +16,7 @@ folded into Kronecker terms exactly as the Poisson coefficient Q_{kl} (App. A, `
 A_ij is a Kronecker sum.  Block vectors are lists of three Tucker tensors; products, sums, scalar products and
 truncations act block-wise (Sec. 5.3).
 
-Readings (listed in DESIGN.md):
+Readings:
   * boundary conditions: homogeneous Dirichlet on every face for every component (the paper's column test
     mixes Dirichlet and Neumann faces on a geometry it does not give);
   * body force: a constant vector f, so component i of the rhs is f_i times the Poisson load of f = 1;

@@ -3,7 +3,7 @@ exponential sums (Prop. 1, eq. estimate_prec_rel) and the low-rank application (
 
 Oracle module (test infrastructure only).  Dense matrices, direct sums for the sine transforms.
 
-Readings (listed in DESIGN.md):
+Readings:
   * App. B, U1: the columns of V1 U1 are the B-spline coefficients of the interpolant in V_h,1 of
     the L2-normalised sines sqrt(2) sin(j pi x) at the points x_i (one factor sqrt(2)).
   * App. B, V2: V2 = M^{-1} N with N a basis of null(V1^T), which makes span(V2) the

@@ -5,7 +5,7 @@ Oracle module (test infrastructure only).
 For a map F: [0,1]^3 -> Omega the stiffness matrix and load vector become integrals over the
 parametric cube with Q(eta) = det(J) J^-1 J^-T and omega(eta) = det(J) f(F(eta)).
 
-Geometries (synthetic stand-ins for the paper's domains; the recipe is stated in the design doc):
+Geometries (synthetic stand-ins for the paper's domains):
   cube   -- identity map, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
   twist  -- quarter annulus (rho = 1 + eta1 in [1,2], theta = pi/2 eta2) extruded along z = eta3,
             with the cross-section rotated about its centroid c by tau(eta3) = amp sin(pi eta3); f = 1.

@@ -2,7 +2,7 @@
 
 Oracle module (test infrastructure only).
 
-Readings (listed in DESIGN.md):
+Readings:
   * ST-HOSVD (Sec. 2.3, Vannieuwenhoven et al.) processes modes 1, 2, 3 in order; mode m keeps the
     smallest s_m whose discarded squared singular values sum to <= eps^2 ||Z||^2 / 3, so that the
     total error is <= eps ||Z|| (the errors of the three sequential projections add in squares).

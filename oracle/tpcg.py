@@ -2,7 +2,7 @@
 
 Oracle module (test infrastructure only).
 
-Readings (listed in DESIGN.md):
+Readings:
   * the stopping test is relative, ||r_k|| <= tol ||f~||, and ||f|| in eq. rel_tol_iterates is ||f~||;
   * the truncation parameter beta of eq. rel_tol_iterates is called ``beta_trunc``; the CG
     coefficient beta_k keeps its name;

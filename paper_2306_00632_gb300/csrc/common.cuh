@@ -19,7 +19,7 @@ void set_error(const std::string& msg);
 // ------------------------------------------------------------------------------------ profiling
 extern std::atomic<long long> g_launches;
 extern thread_local long long t_launches;   // launches (or captured kernel nodes) issued by this thread
-enum { PK_ZGEMM = 0, PK_ZBLK, PK_GRAM, PK_EIG, PK_PROJ, PK_QR, PK_APPLY, PK_FD, PK_DOT, PK_ROUND, PK_FINAL,
+enum { PK_ZGEMM = 0, PK_ZBLK, PK_GRAM, PK_EIG, PK_PROJ, PK_QR, PK_APPLY, PK_FD, PK_DOT, PK_ROUND, PK_FINAL, PK_SWEEPS,
        PK_COUNT = 16 };
 bool prof_on();
 double* prof_dev();                       // device accumulators [kind*2] flops, [kind*2+1] bytes, or null

@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
             A[pb + cqa] = y10; A[qb + cqa] = y11;
         }
     };
+    int nsweeps = 0;
     for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
+        ++nsweeps;
         if (tid == 0) s_rot = 0;
         __syncthreads();
         for (int step = 0; step < P; ++step) {
@@ -264,6 +266,8 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
         if (prof) {   // algorithmic work: the dense symmetric eigen-decomposition count 9 M^3; Gram in, S out
             prof[2 * PK_EIG] += 9.0 * (double)M * M * M;
             prof[2 * PK_EIG + 1] += (double)sizeof(T) * ((double)M * M + (double)M * s);
+            prof[2 * PK_SWEEPS] += nsweeps;       // Jacobi sweeps, and the number of Grams
+            prof[2 * PK_SWEEPS + 1] += 1.0;
         }
     }
     __syncthreads();

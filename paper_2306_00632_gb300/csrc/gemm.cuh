@@ -3,7 +3,8 @@
 // sequence is fixed (CUDA-graph capturable).  Column-major, op(A) is M x K, op(B) is K x N.
 //
 // Tiling: 64 x 64 output tile per CTA, K-step 16, 256 threads, 4 x 4 outputs per thread held in
-// registers; operands staged through shared memory with loads coalesced along the contiguous index.
+// registers; operands staged through two shared-memory stages (the next K-step is fetched into registers
+// while the current one is consumed), with loads coalesced along the contiguous index.
 #pragma once
 
 #include <algorithm>
@@ -14,35 +15,54 @@ namespace tpcg {
 
 constexpr int GBM = 64, GBN = 64, GBK = 16, GTHREADS = 256;
 
+constexpr int GLOAD = (GBM * GBK) / GTHREADS;   // elements of each operand tile a thread moves per K-step
+
+// global -> registers (bounds-checked; zero outside), coalesced along the contiguous index
 template <typename T, bool TA>
-__device__ __forceinline__ void gemm_load_a(T (*As)[GBM + 1], const T* A, long long lda, int M, int K, int m0,
-                                            int k0, int tid) {
+__device__ __forceinline__ void gemm_fetch_a(T (&r)[GLOAD], const T* A, long long lda, int M, int K, int m0, int k0,
+                                             int tid) {
 #pragma unroll
-    for (int q = 0; q < (GBM * GBK) / GTHREADS; ++q) {
-        int e = tid + q * GTHREADS;
+    for (int q = 0; q < GLOAD; ++q) {
+        const int e = tid + q * GTHREADS;
         int mm, kk;
         if (!TA) { mm = e % GBM; kk = e / GBM; }   // A[m + k lda]: contiguous in m
         else     { kk = e % GBK; mm = e / GBK; }   // A[k + m lda]: contiguous in k
-        int m = m0 + mm, k = k0 + kk;
-        T v = T(0);
-        if (m < M && k < K) v = TA ? A[k + (long long)m * lda] : A[m + (long long)k * lda];
-        As[kk][mm] = v;
+        const int m = m0 + mm, k = k0 + kk;
+        r[q] = (m < M && k < K) ? (TA ? A[k + (long long)m * lda] : A[m + (long long)k * lda]) : T(0);
+    }
+}
+
+template <typename T, bool TA>
+__device__ __forceinline__ void gemm_store_a(T (*As)[GBM + 1], const T (&r)[GLOAD], int tid) {
+#pragma unroll
+    for (int q = 0; q < GLOAD; ++q) {
+        const int e = tid + q * GTHREADS;
+        if (!TA) As[e / GBM][e % GBM] = r[q];
+        else     As[e % GBK][e / GBK] = r[q];
     }
 }
 
 template <typename T, bool TB>
-__device__ __forceinline__ void gemm_load_b(T (*Bs)[GBN + 1], const T* B, long long ldb, int N, int K, int n0,
-                                            int k0, int tid) {
+__device__ __forceinline__ void gemm_fetch_b(T (&r)[GLOAD], const T* B, long long ldb, int N, int K, int n0, int k0,
+                                             int tid) {
 #pragma unroll
-    for (int q = 0; q < (GBN * GBK) / GTHREADS; ++q) {
-        int e = tid + q * GTHREADS;
+    for (int q = 0; q < GLOAD; ++q) {
+        const int e = tid + q * GTHREADS;
         int nn, kk;
         if (!TB) { kk = e % GBK; nn = e / GBK; }   // B[k + n ldb]: contiguous in k
         else     { nn = e % GBN; kk = e / GBN; }   // B[n + k ldb]: contiguous in n
-        int nI = n0 + nn, k = k0 + kk;
-        T v = T(0);
-        if (nI < N && k < K) v = TB ? B[nI + (long long)k * ldb] : B[k + (long long)nI * ldb];
-        Bs[kk][nn] = v;
+        const int nI = n0 + nn, k = k0 + kk;
+        r[q] = (nI < N && k < K) ? (TB ? B[nI + (long long)k * ldb] : B[k + (long long)nI * ldb]) : T(0);
+    }
+}
+
+template <typename T, bool TB>
+__device__ __forceinline__ void gemm_store_b(T (*Bs)[GBN + 1], const T (&r)[GLOAD], int tid) {
+#pragma unroll
+    for (int q = 0; q < GLOAD; ++q) {
+        const int e = tid + q * GTHREADS;
+        if (!TB) Bs[e % GBK][e / GBK] = r[q];
+        else     Bs[e / GBN][e % GBN] = r[q];
     }
 }
 
@@ -51,8 +71,9 @@ template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(GTHREADS) gemm_grouped_kernel(const GemmArgs* __restrict__ args,
                                                                 const int* __restrict__ count_dev, int bmax,
                                                                 int zmax) {
-    __shared__ T As[GBK][GBM + 1];
-    __shared__ T Bs[GBK][GBN + 1];
+    // two shared-memory stages: the next K-step is fetched into registers while the current one is used
+    __shared__ T As[2][GBK][GBM + 1];
+    __shared__ T Bs[2][GBK][GBN + 1];
     const int gcount = count_dev != nullptr ? *count_dev : (zmax / bmax);
     for (int z = blockIdx.z; z < zmax; z += gridDim.z) {
     const int g = z / bmax;
@@ -77,23 +98,37 @@ __global__ void __launch_bounds__(GTHREADS) gemm_grouped_kernel(const GemmArgs* 
         const int bi = a.acc ? b : ib;
         const T* A = static_cast<const T*>(a.A) + (long long)bi * a.sA;
         const T* B = static_cast<const T*>(a.B) + (long long)bi * a.sB;
+        T ra[GLOAD], rb[GLOAD];
+        gemm_fetch_a<T, TA>(ra, A, a.lda, M, K, m0, 0, tid);
+        gemm_fetch_b<T, TB>(rb, B, a.ldb, N, K, n0, 0, tid);
+        gemm_store_a<T, TA>(As[0], ra, tid);
+        gemm_store_b<T, TB>(Bs[0], rb, tid);
+        __syncthreads();
+        int cur = 0;
         for (int k0 = 0; k0 < K; k0 += GBK) {
-            gemm_load_a<T, TA>(As, A, a.lda, M, K, m0, k0, tid);
-            gemm_load_b<T, TB>(Bs, B, a.ldb, N, K, n0, k0, tid);
-            __syncthreads();
+            const bool more = k0 + GBK < K;
+            if (more) {
+                gemm_fetch_a<T, TA>(ra, A, a.lda, M, K, m0, k0 + GBK, tid);
+                gemm_fetch_b<T, TB>(rb, B, a.ldb, N, K, n0, k0 + GBK, tid);
+            }
 #pragma unroll
             for (int kk = 0; kk < GBK; ++kk) {
                 T av[4], bv[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) av[i] = As[kk][tx + 16 * i];
+                for (int i = 0; i < 4; ++i) av[i] = As[cur][kk][tx + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][ty + 16 * j];
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[cur][kk][ty + 16 * j];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
             }
+            if (more) {
+                gemm_store_a<T, TA>(As[cur ^ 1], ra, tid);
+                gemm_store_b<T, TB>(Bs[cur ^ 1], rb, tid);
+            }
             __syncthreads();
+            cur ^= 1;
         }
     }
     T* C = static_cast<T*>(a.C) + (a.acc ? 0LL : (long long)ib * a.sC);

@@ -31,6 +31,7 @@ SYMBOLS = [
 ]
 PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
               "round": 9}
+PROF_SWEEPS = 11   # one-CTA Jacobi: (sweeps, Grams) in the (flops, bytes) fields of this kind
 
 
 class TuckerT(C.Structure):

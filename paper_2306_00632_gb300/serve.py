@@ -12,6 +12,8 @@ Requests are scalar Poisson problems (``tpcg_solve``) or linear elasticity block
 read-only during solves and shared by all requests on that geometry.
 
 Results do not depend on what else runs: every solve has its own workspace and the kernels are deterministic.
+Set CUDA_DEVICE_MAX_CONNECTIONS=32 before the CUDA context is created: with the default of 8 hardware queues,
+solves beyond the eighth share queues and wait on each other's kernels.
 """
 from __future__ import annotations
 
