@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--refine-keep", type=float, default=3e-2, help="mixed form: accuracy kept of each correction")
     ap.add_argument("--gemm-ctas-per-sm", type=int, default=2, help="grouped-GEMM CTA budget per SM (0: uncapped)")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
+    ap.add_argument("--serve", type=float, default=0.0,
+                    help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
+    ap.add_argument("--requests", type=int, default=48, help="requests in the --serve stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -250,6 +253,8 @@ def run_gpu(args):
     ctxs = [_ctx_for(api, p.info, dt, rc) for p in pbs]
     xs = [api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=dt) for _ in range(B)]
     # by default the library gives each solve a stream of its own (torch's pool holds 32 streams per priority)
+    if args.torch_streams and B > 32:
+        raise SystemExit("--torch-streams: torch's pool has 32 streams per priority; concurrent solves need their own")
     streams = [torch.cuda.Stream() for _ in range(B)] if args.torch_streams else [None] * B
     lib.check(L.tpcg_set_option(1, args.gemm_ctas_per_sm), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -381,10 +386,61 @@ def e2e(api, lib, pbs, dt, ctxs, xs, streams, kw, args):
             "d2h_bytes_per_step": int(d2h), "steps": K}
 
 
+def run_serve(args):
+    """Continuous-batching server under a Poisson-arrival stream: half scalar Poisson requests (mixed form,
+    n in {32, 64, 96, 128}, p in {2, 3}), half elasticity requests (FP64, n in {16, 24, 32}, lambda = 1,
+    mu in [0.3, 1], body force (0, 0.1, -1)), seeded.  Prints p50/p99 latency and throughput."""
+    import torch
+    from paper_2306_00632_gb300 import lib, serve
+    lib.load()
+    arr = synth.poisson_arrivals(args.serve, args.requests, seed=SEED)
+    reqs = []
+    for i, t in enumerate(arr):
+        sd = SEED + 1000 + i
+        if i % 2 == 0:
+            n = (32, 64, 96, 128)[int(synth.unit_from_seed(sd, 2) * 4)]
+            p = 2 + int(synth.unit_from_seed(sd, 3) * 2)
+            reqs.append(serve.Request(lib.GEOM_TWIST, synth.amp_from_seed(sd), p, n, min(n, 64), tol=TOL,
+                                      dtype=lib.MIXED, arrival=float(t)))
+        else:
+            n = (16, 24, 32)[int(synth.unit_from_seed(sd, 2) * 3)]
+            mu = 0.3 + 0.7 * synth.unit_from_seed(sd, 5)
+            reqs.append(serve.Request(lib.GEOM_TWIST, synth.amp_from_seed(sd), 2, n, n, tol=TOL, dtype=lib.F64,
+                                      arrival=float(t), problem="elasticity", lame_lambda=1.0, lame_mu=mu,
+                                      force=(0.0, 0.1, -1.0)))
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(int(free * 0.6), max_slots=32)
+    srv.run(reqs[:4])   # warm-up: operators cached, contexts and graphs exercised
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    lat = serve.percentiles(res)
+    ok = sum(1 for r in res if r.status == 0 and r.true_rel_res <= TOL)
+    line = {"metric": "served TPCG requests: p50/p99 latency and solves/s", "unit": "s",
+            "rate_hz": args.serve, "requests": len(res), "converged": ok,
+            "latency_s": {"p50": lat["p50"], "p99": lat["p99"]},
+            "solves_per_s": len(res) / max(max(r.finished for r in res), 1e-9), "wall_s": wall,
+            "mix": "50/50 Poisson (mixed form, n 32-128) / elasticity (FP64, n 16-32), seeded twisted annuli",
+            "max_slots": 32}
+    by = {}
+    for r in res:
+        k = r.request.problem
+        d = by.setdefault(k, {"requests": 0, "status": {}, "iters": [], "latency_s": [], "n": []})
+        d["requests"] += 1
+        d["status"][str(r.status)] = d["status"].get(str(r.status), 0) + 1
+        d["iters"].append(r.iters)
+        d["latency_s"].append(round(r.latency, 2))
+        d["n"].append(r.request.n)
+    line["by_problem"] = by
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve > 0:
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -226,6 +226,11 @@ int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x,
  * shared (read-only during a solve, apart from a capacity-error flag).  statuses[i] receives each
  * solve's status; the return value is TPCG_OK, else the first hard error, else TPCG_E_NOT_CONVERGED.
  * Results do not depend on what runs beside them (no shared scratch).  Turn profiling off first. */
+/* The non-blocking stream owned by a context (created on first use, destroyed with the context; no counterpart
+ * in the paper).  Concurrent solves must not share a stream: the solver replays CUDA graphs captured on its
+ * stream, and a capture in progress on a shared stream would take in another solve's work.  Callers that
+ * draw streams from a recycling pool (torch keeps 32 per priority) should use this one instead. */
+int tpcg_ctx_stream(tpcg_ctx c, void** out);
 int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, const tpcg_params* prms, tucker_t* xs,
                      tpcg_stats* sts, void* const* streams, int* statuses);
 

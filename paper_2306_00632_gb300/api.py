@@ -340,6 +340,13 @@ def tpcg_solve(pb: Problem, ctx: Ctx, x: Tucker, stream=None, **kw):
     return st
 
 
+def ctx_stream(ctx: "Ctx"):
+    """The context's own CUDA stream as a torch stream (tpcg_ctx_stream): a stream no other solve shares."""
+    h = C.c_void_p()
+    check(L.load().tpcg_ctx_stream(ctx.h, C.byref(h)), "tpcg_ctx_stream")
+    return torch.cuda.ExternalStream(h.value)
+
+
 def tpcg_solve_batch(problems, ctxs, xs, streams, **kw):
     """Independent solves at once (tpcg_solve_batch): one host thread and one stream per solve.
     Returns (statuses, stats)."""

@@ -1001,6 +1001,18 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
 
 // Many independent solves at once: one host thread per solve, each on its own stream and context, so
 // that their kernels overlap on the device (the eigensolver and QR kernels of one solve fill one SM each).
+extern "C" int tpcg_ctx_stream(tpcg_ctx c, void** out) {
+    if (!c || !out) return TPCG_E_INVALID;
+    if (!c->own_stream && cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->own_stream = nullptr;
+        cudaGetLastError();
+        set_error("tpcg_ctx_stream: cudaStreamCreateWithFlags failed");
+        return TPCG_E_CUDA;
+    }
+    *out = c->own_stream;
+    return TPCG_OK;
+}
+
 extern "C" int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, const tpcg_params* prms,
                                 tucker_t* xs, tpcg_stats* sts, void* const* streams, int* statuses) {
     if (count < 0 || (count > 0 && (!pbs || !ctxs || !prms || !xs || !streams || !statuses))) {

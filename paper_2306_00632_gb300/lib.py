@@ -24,7 +24,7 @@ SYMBOLS = [
     "tpcg_problem_destroy",
     "tpcg_ctx_create", "tpcg_ctx_bytes", "tpcg_ctx_destroy", "tucker_set_plain", "tucker_get_ranks",
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
-    "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_last_error", "tpcg_version",
+    "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_ctx_stream", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count", "tpcg_set_option",
     "tpcg_elast_setup", "tpcg_elast_create", "tpcg_elast_get_info", "tpcg_elast_apply", "tpcg_elast_residual",
     "tpcg_elast_precond", "tpcg_elast_solve", "tpcg_elast_destroy",
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
         "fd_precond_apply": (i, [vp, vp, PT, PT, vp]),
         "tpcg_params_default": (None, [C.POINTER(Params)]),
         "tpcg_solve": (i, [vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp]),
+        "tpcg_ctx_stream": (i, [vp, C.POINTER(vp)]),
         "tpcg_solve_batch": (i, [i, vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp, C.POINTER(C.c_int)]),
         "tpcg_last_error": (C.c_char_p, []),
         "tpcg_profile_enable": (i, [i]),

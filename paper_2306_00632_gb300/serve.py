@@ -109,9 +109,11 @@ class Server:
     def _solve(self, r: Request, pb, t0: float, admitted: float, need: int, out: list, idx: int):
         try:
             rc, max_cols = self._shape(r, pb)
-            stream = torch.cuda.Stream()
+            ctx = api.Ctx(r.n, max_cols, rc, r.dtype)
+            # the context's own stream: torch's pool recycles 32 streams, and two solves on one stream would
+            # interleave with each other's graph captures
+            stream = api.ctx_stream(ctx)
             with torch.cuda.stream(stream):
-                ctx = api.Ctx(r.n, max_cols, rc, r.dtype)
                 core = fac = None
                 if r.problem == "elasticity":
                     x = [api.Tucker(r.n, cap=rc, core_cap=rc ** 3, dtype=r.dtype) for _ in range(3)]
