@@ -400,7 +400,7 @@ def run_serve(args):
         if i % 2 == 0:
             n = (32, 64, 96, 128)[int(synth.unit_from_seed(sd, 2) * 4)]
             p = 2 + int(synth.unit_from_seed(sd, 3) * 2)
-            reqs.append(serve.Request(lib.GEOM_TWIST, synth.amp_from_seed(sd), p, n, min(n, 64), tol=TOL,
+            reqs.append(serve.Request(lib.GEOM_TWIST, synth.amp_from_seed(sd), p, n, min(n, 96), tol=TOL,
                                       dtype=lib.MIXED, arrival=float(t)))
         else:
             n = (16, 24, 32)[int(synth.unit_from_seed(sd, 2) * 3)]
