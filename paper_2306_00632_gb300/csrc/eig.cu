@@ -76,7 +76,9 @@ __device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double tr
     return s;
 }
 
-template <typename T>
+// SM: A and V both in shared memory (known at compile time, so the step loop uses shared-memory accesses
+// rather than generic ones); otherwise a_smem / v_smem choose per matrix at run time.
+template <typename T, bool SM>
 __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan, const T* __restrict__ G, T* __restrict__ Ag,
                                                           T* __restrict__ Vg, T* __restrict__ S, double* evals, int m,
                                                           int a_smem, int v_smem, int max_sweeps, double* prof) {
@@ -87,8 +89,8 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
     extern __shared__ unsigned char smem_raw[];
     T* sbase = reinterpret_cast<T*>(smem_raw);
     const int ld = M + 1;
-    T* A = a_smem ? sbase : Ag;
-    T* V = v_smem ? sbase + (long long)M * ld : Vg;
+    T* A = SM ? sbase : (a_smem ? sbase : Ag);
+    T* V = SM ? sbase + M * ld : (v_smem ? sbase + (long long)M * ld : Vg);
     __shared__ T cs[2 * 512];
     __shared__ short pq[2 * 512];
     __shared__ double lam[SMAX_EIG];
@@ -196,7 +198,12 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
         for (int step = 0; step < P; ++step) {
             for (int k = tid; k < half; k += nt) {
                 int a, b;
-                if (k == 0) { a = P; b = step; } else { a = (step + k) % P; b = (step - k + P) % P; }
+                if (k == 0) {
+                    a = P; b = step;
+                } else {   // (step + k) mod P and (step - k) mod P, with 0 < k < P and 0 <= step < P
+                    a = step + k; if (a >= P) a -= P;
+                    b = step - k; if (b < 0) b += P;
+                }
                 const int pi = a < b ? a : b, qi = a < b ? b : a;
                 T c = T(1), s = T(0);
                 if (qi < M) {
@@ -569,7 +576,7 @@ __global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
 // that takes driver locks, so it stays off the per-launch path that many solver threads share.
 static int smem_optin(const void* func, int slot, int bytes) {
     static std::mutex mu;
-    static bool done[4][64] = {};
+    static bool done[8][64] = {};
     int dev = 0;
     TPCG_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) dev = 63;
@@ -609,17 +616,26 @@ int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int
     }
     int a_smem = 0, v_smem = 0;
     const size_t bytes = jacobi_smem_plan(n, sizeof(T), &a_smem, &v_smem);
-    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T>), sizeof(T) == 8 ? 2 : 3, 190 * 1024));
-    jacobi_eig_kernel<T><<<1, EIG_THREADS, bytes, st>>>(plan, G, reinterpret_cast<T*>(w.Aw), reinterpret_cast<T*>(w.Vw), S,
-                                                 evals, m, a_smem, v_smem, 20, prof_dev());
+    T* Aw = reinterpret_cast<T*>(w.Aw);
+    T* Vw = reinterpret_cast<T*>(w.Vw);
+    if (a_smem && v_smem) {
+        TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T, true>), sizeof(T) == 8 ? 4 : 5, 190 * 1024));
+        jacobi_eig_kernel<T, true><<<1, EIG_THREADS, bytes, st>>>(plan, G, Aw, Vw, S, evals, m, 1, 1, 20, prof_dev());
+    } else {
+        TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T, false>), sizeof(T) == 8 ? 2 : 3, 190 * 1024));
+        jacobi_eig_kernel<T, false><<<1, EIG_THREADS, bytes, st>>>(plan, G, Aw, Vw, S, evals, m, a_smem, v_smem, 20,
+                                                                  prof_dev());
+    }
     TPCG_CHECK_LAUNCH();
     return TPCG_OK;
 }
 int eig_prepare() {
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(cjacobi_eig_kernel<double>), 0, 200 * 1024));
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(cjacobi_eig_kernel<float>), 1, 200 * 1024));
-    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<double>), 2, 190 * 1024));
-    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<float>), 3, 190 * 1024));
+    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<double, false>), 2, 190 * 1024));
+    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<float, false>), 3, 190 * 1024));
+    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<double, true>), 4, 190 * 1024));
+    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<float, true>), 5, 190 * 1024));
     return TPCG_OK;
 }
 
