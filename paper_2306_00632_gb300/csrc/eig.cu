@@ -594,6 +594,211 @@ static bool use_cluster_eig(int n) {
     return sizeof(T) == 8 && n >= 2 && cj_padded(n) <= CJ_MAXM;
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// FP32 Grams up to JV_MAXM with A and V resident in shared memory: the cyclic Jacobi of jacobi_eig_kernel (same
+// pair order, thresholds, rotation formula and truncation rule) with fewer instructions per step.  Each pair's
+// rotation is packed as float2 (c, s) and its indices as int4 (p, q, p ld, q ld); the 2 x 2 block products and
+// the V update use paired FP32 FMAs (__ffma2_rn / __fmul2_rn); V's columns are 16-byte aligned, so a warp
+// rotates a pair of V columns with one float4 load and store per lane and column.
+// ------------------------------------------------------------------------------------------------------------
+constexpr int JV_MAXM = 128;   // a V column is at most 32 float4 (one per lane)
+
+static inline size_t jv_smem_bytes(int n) {
+    const size_t a = ((size_t)n * (n + 1) + 3) & ~(size_t)3;
+    return (a + (size_t)n * ((n + 3) & ~3)) * sizeof(float);
+}
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+__global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* plan, const float* __restrict__ G,
+                                                                   float* __restrict__ S, double* evals, int m,
+                                                                   int max_sweeps, double* prof) {
+    RoundPlan& p = *plan;
+    const int M = p.gM;
+    const int n = p.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    extern __shared__ __align__(16) unsigned char jv_smem[];
+    const int ld = M + 1;
+    const int ldv = (M + 3) & ~3;
+    float* A = reinterpret_cast<float*>(jv_smem);
+    float* V = A + ((M * ld + 3) & ~3);
+    __shared__ float2 cs[JV_MAXM / 2];
+    __shared__ int4 pinfo[JV_MAXM / 2];
+    __shared__ double lam[JV_MAXM];
+    __shared__ short ord[JV_MAXM];
+    __shared__ int s_rot, s_keep;
+    __shared__ double s_tr;
+    if (M <= 0) {
+        if (tid == 0) {
+            p.s[m] = 0;
+            if (m == 0) { p.norm2 = 0; p.budget = 0; }
+        }
+        return;
+    }
+    for (int e = tid; e < M * M; e += nt) {
+        const int i = e % M, j = e / M;
+        A[i + j * ld] = G[e];
+    }
+    for (int e = tid; e < M * ldv; e += nt) {   // V = I, padding rows zero (they stay zero under rotations)
+        const int i = e % ldv, j = e / ldv;
+        V[e] = (i == j) ? 1.f : 0.f;
+    }
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
+        s_tr = t;
+        if (m == 0) {
+            p.norm2 = t;
+            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+        }
+    }
+    __syncthreads();
+    const int Mp = (M + 1) & ~1;
+    const int half = Mp / 2;
+    const int P = Mp - 1;
+    const float epsr = (float)jacobi_tau<float>();
+    const float epsa = (float)(1.2e-7 * s_tr);
+    const int nblk = half * (half + 1) / 2;
+    constexpr int NBREG = 4;   // 2 x 2 blocks per thread: nblk <= 2080 <= 4 x 1024 for M <= 128
+    int ab[NBREG];
+#pragma unroll
+    for (int j = 0; j < NBREG; ++j) {
+        const int q = tid + j * nt;
+        ab[j] = -1;
+        if (q < nblk) {
+            int bb = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+            while ((bb + 1) * (bb + 2) / 2 <= q) ++bb;
+            while (bb * (bb + 1) / 2 > q) --bb;
+            ab[j] = (q - bb * (bb + 1) / 2) | (bb << 16);
+        }
+    }
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+    const bool vlane = 4 * lane < M;
+    // A <- J_a^T A J_b on the 2 x 2 block (pair a rows, pair b columns), mirrored for a < b
+    auto update_block = [&](int a, int b) {
+        const float2 ra = cs[a], rb = cs[b];
+        if (ra.y == 0.f && rb.y == 0.f) return;
+        const int4 ia = pinfo[a], ib = pinfo[b];
+        const float ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
+        const int pa = ia.x, qa = ia.y, pb = ib.x, qb = ib.y;
+        if (qa < 0 || qb < 0) {   // one side is the padding index (M odd): a single row / column pair
+            if (qa < 0 && qb < 0) return;
+            if (qa < 0) {   // rotate columns pb, qb of row pa (and mirror)
+                const float x = A[pa + ib.z], y = A[pa + ib.w];
+                const float xn = cb * x - sb * y, yn = sb * x + cb * y;
+                A[pa + ib.z] = xn; A[pa + ib.w] = yn;
+                A[pb + ia.z] = xn; A[qb + ia.z] = yn;
+            } else {        // rotate rows pa, qa of column pb (and mirror)
+                const float x = A[pa + ib.z], y = A[qa + ib.z];
+                const float xn = ca * x - sa * y, yn = sa * x + ca * y;
+                A[pa + ib.z] = xn; A[qa + ib.z] = yn;
+                A[pb + ia.z] = xn; A[pb + ia.w] = yn;
+            }
+            return;
+        }
+        const int cpb = ib.z, cqb = ib.w;
+        const float2 X0 = f2(A[pa + cpb], A[pa + cqb]);   // row pa: columns pb, qb
+        const float2 X1 = f2(A[qa + cpb], A[qa + cqb]);   // row qa
+        // rows: J_a^T X
+        const float2 R0 = __ffma2_rn(f2(ca, ca), X0, __fmul2_rn(f2(-sa, -sa), X1));
+        const float2 R1 = __ffma2_rn(f2(sa, sa), X0, __fmul2_rn(f2(ca, ca), X1));
+        // columns: (J_a^T X) J_b, on (r00, r10) and (r01, r11)
+        const float2 C0 = f2(R0.x, R1.x), C1 = f2(R0.y, R1.y);
+        float2 Y0 = __ffma2_rn(f2(cb, cb), C0, __fmul2_rn(f2(-sb, -sb), C1));   // (y00, y10)
+        float2 Y1 = __ffma2_rn(f2(sb, sb), C0, __fmul2_rn(f2(cb, cb), C1));     // (y01, y11)
+        if (a == b) { Y1.x = 0.f; Y0.y = 0.f; }   // the rotated pair is annihilated
+        A[pa + cpb] = Y0.x; A[pa + cqb] = Y1.x;
+        A[qa + cpb] = Y0.y; A[qa + cqb] = Y1.y;
+        if (a != b) {
+            const int cpa = ia.z, cqa = ia.w;
+            A[pb + cpa] = Y0.x; A[qb + cpa] = Y1.x;
+            A[pb + cqa] = Y0.y; A[qb + cqa] = Y1.y;
+        }
+    };
+    int nsweeps = 0;
+    for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
+        ++nsweeps;
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int step = 0; step < P; ++step) {
+            for (int k = tid; k < half; k += nt) {
+                int a, b;
+                if (k == 0) {
+                    a = P; b = step;
+                } else {   // (step + k) mod P and (step - k) mod P, with 0 < k < P and 0 <= step < P
+                    a = step + k; if (a >= P) a -= P;
+                    b = step - k; if (b < 0) b += P;
+                }
+                const int pi = a < b ? a : b, qi = a < b ? b : a;
+                float c = 1.f, s = 0.f;
+                if (qi < M) {
+                    const float apq = A[pi + qi * ld];
+                    const float app = A[pi + pi * ld], aqq = A[qi + qi * ld];
+                    if (fabsf(apq) > epsr * sqrtf(fabsf(app * aqq)) && fabsf(apq) > epsa) {
+                        const float th = (aqq - app) / (2.f * apq);
+                        const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+                        c = 1.f / sqrtf(t * t + 1.f);
+                        s = t * c;
+                        s_rot = 1;
+                    }
+                }
+                cs[k] = f2(c, s);
+                pinfo[k] = qi < M ? make_int4(pi, qi, pi * ld, qi * ld) : make_int4(pi, -1, pi * ld, 0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < NBREG; ++j)
+                if (ab[j] >= 0) update_block(ab[j] & 0xffff, ab[j] >> 16);
+            // V <- V J: one warp per pair of columns, four rows per lane
+            for (int k = warp; k < half; k += nwarps) {
+                const float2 r = cs[k];
+                const int4 pk = pinfo[k];
+                if (r.y == 0.f || pk.y < 0 || !vlane) continue;
+                float4* Vp = reinterpret_cast<float4*>(V + pk.x * ldv) + lane;
+                float4* Vq = reinterpret_cast<float4*>(V + pk.y * ldv) + lane;
+                const float4 vp = *Vp, vq = *Vq;
+                const float2 c2 = f2(r.x, r.x), s2 = f2(r.y, r.y), ms2 = f2(-r.y, -r.y);
+                const float2 p01 = __ffma2_rn(c2, f2(vp.x, vp.y), __fmul2_rn(ms2, f2(vq.x, vq.y)));
+                const float2 p23 = __ffma2_rn(c2, f2(vp.z, vp.w), __fmul2_rn(ms2, f2(vq.z, vq.w)));
+                const float2 q01 = __ffma2_rn(s2, f2(vp.x, vp.y), __fmul2_rn(c2, f2(vq.x, vq.y)));
+                const float2 q23 = __ffma2_rn(s2, f2(vp.z, vp.w), __fmul2_rn(c2, f2(vq.z, vq.w)));
+                *Vp = make_float4(p01.x, p01.y, p23.x, p23.y);
+                *Vq = make_float4(q01.x, q01.y, q23.x, q23.y);
+            }
+            __syncthreads();
+        }
+        if (!s_rot) break;
+        __syncthreads();
+    }
+    // eigenvalues sorted decreasingly (rank counting)
+    for (int i = tid; i < M; i += nt) {
+        const double li = (double)A[i + i * ld];
+        int rk = 0;
+        for (int j = 0; j < M; ++j) {
+            const double lj = (double)A[j + j * ld];
+            if (lj > li || (lj == li && j < i)) ++rk;
+        }
+        ord[rk] = (short)i;
+        lam[rk] = li;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int s = truncation_rule<float>(p, lam, M, s_tr, m);
+        s_keep = s;
+        for (int i = 0; i < M; ++i) evals[i] = lam[i];
+        if (prof) {   // algorithmic work: the dense symmetric eigen-decomposition count 9 M^3; Gram in, S out
+            prof[2 * PK_EIG] += 9.0 * (double)M * M * M;
+            prof[2 * PK_EIG + 1] += (double)sizeof(float) * ((double)M * M + (double)M * s);
+            prof[2 * PK_SWEEPS] += nsweeps;
+            prof[2 * PK_SWEEPS + 1] += 1.0;
+        }
+    }
+    __syncthreads();
+    const int s = s_keep;
+    for (int c = 0; c < s; ++c)
+        for (int i = tid; i < M; i += nt) S[i + (long long)c * n] = V[i + ord[c] * ldv];
+}
+
 // shared-memory layout: A (M (M+1)) and V (M (M+1)) when both fit, else A only, else neither
 static size_t jacobi_smem_plan(int n, size_t elt, int* a_smem, int* v_smem) {
     const size_t limit = 190 * 1024;   // leaves room for the ~20 KB of static shared memory
@@ -613,6 +818,14 @@ int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int
         cjacobi_eig_kernel<T><<<CJ_C, CJ_THREADS, bytes, st>>>(plan, G, S, evals, m, 20, prof_dev());
         TPCG_CHECK_LAUNCH();
         return TPCG_OK;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (n <= JV_MAXM) {   // FP32 Grams up to 128: packed rotations, vectorised V update
+            TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_v_kernel), 6, 190 * 1024));
+            jacobi_eig_v_kernel<<<1, EIG_THREADS, jv_smem_bytes(n), st>>>(plan, G, S, evals, m, 20, prof_dev());
+            TPCG_CHECK_LAUNCH();
+            return TPCG_OK;
+        }
     }
     int a_smem = 0, v_smem = 0;
     const size_t bytes = jacobi_smem_plan(n, sizeof(T), &a_smem, &v_smem);
@@ -636,6 +849,7 @@ int eig_prepare() {
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<float, false>), 3, 190 * 1024));
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<double, true>), 4, 190 * 1024));
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<float, true>), 5, 190 * 1024));
+    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_v_kernel), 6, 190 * 1024));
     return TPCG_OK;
 }
 
