@@ -596,10 +596,16 @@ static bool use_cluster_eig(int n) {
 
 // ------------------------------------------------------------------------------------------------------------
 // FP32 Grams up to JV_MAXM with A and V resident in shared memory: the cyclic Jacobi of jacobi_eig_kernel (same
-// pair order, thresholds, rotation formula and truncation rule) with fewer instructions per step.  Each pair's
-// rotation is packed as float2 (c, s) and its indices as int4 (p, q, p ld, q ld); the 2 x 2 block products and
-// the V update use paired FP32 FMAs (__ffma2_rn / __fmul2_rn); V's columns are 16-byte aligned, so a warp
-// rotates a pair of V columns with one float4 load and store per lane and column.
+// pair order, thresholds and rotation formula; the truncation rule is shared) arranged for fewer instructions
+// and no idle warps per step:
+//  - the thread that computes a pair's rotation also writes the rotated 2 x 2 diagonal block
+//    (a_pp - t a_pq, a_qq + t a_pq, zero coupling), so the update phase has only the half (half - 1) / 2
+//    off-diagonal blocks: two per thread at M = 128, the same for every warp;
+//  - V <- V J of step s runs beside the rotations of step s + 1 (V is not read by them), on the warps that
+//    compute no rotation; the rotations are double-buffered by step parity;
+//  - each pair's rotation is packed as float2 (c, s) and its indices as int4 (p, q, p ld, q ld); the 2 x 2
+//    products and the V update use paired FP32 FMAs (__ffma2_rn / __fmul2_rn); V's columns are 16-byte
+//    aligned, one float4 of a column per lane.
 // ------------------------------------------------------------------------------------------------------------
 constexpr int JV_MAXM = 128;   // a V column is at most 32 float4 (one per lane)
 
@@ -622,8 +628,8 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
     const int ldv = (M + 3) & ~3;
     float* A = reinterpret_cast<float*>(jv_smem);
     float* V = A + ((M * ld + 3) & ~3);
-    __shared__ float2 cs[JV_MAXM / 2];
-    __shared__ int4 pinfo[JV_MAXM / 2];
+    __shared__ float2 cs[2][JV_MAXM / 2];
+    __shared__ int4 pinfo[2][JV_MAXM / 2];
     __shared__ double lam[JV_MAXM];
     __shared__ short ord[JV_MAXM];
     __shared__ int s_rot, s_keep;
@@ -658,27 +664,50 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
     const int P = Mp - 1;
     const float epsr = (float)jacobi_tau<float>();
     const float epsa = (float)(1.2e-7 * s_tr);
-    const int nblk = half * (half + 1) / 2;
-    constexpr int NBREG = 4;   // 2 x 2 blocks per thread: nblk <= 2080 <= 4 x 1024 for M <= 128
+    // off-diagonal blocks (a < b) of this thread: q = tid + j nt, q = b (b - 1) / 2 + a
+    const int nblk = half * (half - 1) / 2;
+    constexpr int NBREG = 2;   // nblk <= 2016 <= 2 x 1024 for M <= 128
     int ab[NBREG];
 #pragma unroll
     for (int j = 0; j < NBREG; ++j) {
         const int q = tid + j * nt;
         ab[j] = -1;
         if (q < nblk) {
-            int bb = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-            while ((bb + 1) * (bb + 2) / 2 <= q) ++bb;
-            while (bb * (bb + 1) / 2 > q) --bb;
-            ab[j] = (q - bb * (bb + 1) / 2) | (bb << 16);
+            int bb = (int)((1.0f + sqrtf(8.0f * (float)q + 1.0f)) * 0.5f);
+            while (bb * (bb - 1) / 2 > q) --bb;
+            while ((bb + 1) * bb / 2 <= q) ++bb;
+            ab[j] = (q - bb * (bb - 1) / 2) | (bb << 16);
         }
     }
-    const int warp = tid >> 5, lane = tid & 31, nwarps = nt >> 5;
+    // roles in the first phase of a step: the last `half` threads compute rotations, the warps below them
+    // rotate V by the previous step's rotations
+    const int krot = tid - (nt - half);
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nvw = (nt - half) >> 5;
     const bool vlane = 4 * lane < M;
-    // A <- J_a^T A J_b on the 2 x 2 block (pair a rows, pair b columns), mirrored for a < b
-    auto update_block = [&](int a, int b) {
-        const float2 ra = cs[a], rb = cs[b];
+    // V <- V J for the rotations in buffer b (one warp per pair of columns, four rows per lane)
+    auto update_v = [&](int b) {
+        for (int k = warp; k < half; k += nvw) {
+            const float2 r = cs[b][k];
+            const int4 pk = pinfo[b][k];
+            if (r.y == 0.f || pk.y < 0 || !vlane) continue;
+            float4* Vp = reinterpret_cast<float4*>(V + pk.x * ldv) + lane;
+            float4* Vq = reinterpret_cast<float4*>(V + pk.y * ldv) + lane;
+            const float4 vp = *Vp, vq = *Vq;
+            const float2 c2 = f2(r.x, r.x), s2 = f2(r.y, r.y), ms2 = f2(-r.y, -r.y);
+            const float2 p01 = __ffma2_rn(c2, f2(vp.x, vp.y), __fmul2_rn(ms2, f2(vq.x, vq.y)));
+            const float2 p23 = __ffma2_rn(c2, f2(vp.z, vp.w), __fmul2_rn(ms2, f2(vq.z, vq.w)));
+            const float2 q01 = __ffma2_rn(s2, f2(vp.x, vp.y), __fmul2_rn(c2, f2(vq.x, vq.y)));
+            const float2 q23 = __ffma2_rn(s2, f2(vp.z, vp.w), __fmul2_rn(c2, f2(vq.z, vq.w)));
+            *Vp = make_float4(p01.x, p01.y, p23.x, p23.y);
+            *Vq = make_float4(q01.x, q01.y, q23.x, q23.y);
+        }
+    };
+    // A <- J_a^T A J_b on the off-diagonal 2 x 2 block (pair a rows, pair b columns, a < b) and its mirror
+    auto update_block = [&](const float2* csb, const int4* pib, int a, int b) {
+        const float2 ra = csb[a], rb = csb[b];
         if (ra.y == 0.f && rb.y == 0.f) return;
-        const int4 ia = pinfo[a], ib = pinfo[b];
+        const int4 ia = pib[a], ib = pib[b];
         const float ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
         const int pa = ia.x, qa = ia.y, pb = ib.x, qb = ib.y;
         if (qa < 0 || qb < 0) {   // one side is the padding index (M odd): a single row / column pair
@@ -704,24 +733,25 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
         const float2 R1 = __ffma2_rn(f2(sa, sa), X0, __fmul2_rn(f2(ca, ca), X1));
         // columns: (J_a^T X) J_b, on (r00, r10) and (r01, r11)
         const float2 C0 = f2(R0.x, R1.x), C1 = f2(R0.y, R1.y);
-        float2 Y0 = __ffma2_rn(f2(cb, cb), C0, __fmul2_rn(f2(-sb, -sb), C1));   // (y00, y10)
-        float2 Y1 = __ffma2_rn(f2(sb, sb), C0, __fmul2_rn(f2(cb, cb), C1));     // (y01, y11)
-        if (a == b) { Y1.x = 0.f; Y0.y = 0.f; }   // the rotated pair is annihilated
+        const float2 Y0 = __ffma2_rn(f2(cb, cb), C0, __fmul2_rn(f2(-sb, -sb), C1));   // (y00, y10)
+        const float2 Y1 = __ffma2_rn(f2(sb, sb), C0, __fmul2_rn(f2(cb, cb), C1));     // (y01, y11)
         A[pa + cpb] = Y0.x; A[pa + cqb] = Y1.x;
         A[qa + cpb] = Y0.y; A[qa + cqb] = Y1.y;
-        if (a != b) {
-            const int cpa = ia.z, cqa = ia.w;
-            A[pb + cpa] = Y0.x; A[qb + cpa] = Y1.x;
-            A[pb + cqa] = Y0.y; A[qb + cqa] = Y1.y;
-        }
+        const int cpa = ia.z, cqa = ia.w;
+        A[pb + cpa] = Y0.x; A[qb + cpa] = Y1.x;
+        A[pb + cqa] = Y0.y; A[qb + cqa] = Y1.y;
     };
     int nsweeps = 0;
+    int g = 0;   // steps done: the rotations of step g are in buffer g & 1
     for (int sweep = 0; sweep < max_sweeps && M > 1; ++sweep) {
         ++nsweeps;
         if (tid == 0) s_rot = 0;
         __syncthreads();
-        for (int step = 0; step < P; ++step) {
-            for (int k = tid; k < half; k += nt) {
+        for (int step = 0; step < P; ++step, ++g) {
+            const int cur = g & 1;
+            // phase 1: rotations of this step (and their diagonal blocks); V by the previous step's rotations
+            if (krot >= 0) {
+                const int k = krot;
                 int a, b;
                 if (k == 0) {
                     a = P; b = step;
@@ -739,35 +769,30 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
                         const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
                         c = 1.f / sqrtf(t * t + 1.f);
                         s = t * c;
+                        A[pi + pi * ld] = app - t * apq;   // the rotated diagonal block: coupling annihilated
+                        A[qi + qi * ld] = aqq + t * apq;
+                        A[pi + qi * ld] = 0.f;
+                        A[qi + pi * ld] = 0.f;
                         s_rot = 1;
                     }
                 }
-                cs[k] = f2(c, s);
-                pinfo[k] = qi < M ? make_int4(pi, qi, pi * ld, qi * ld) : make_int4(pi, -1, pi * ld, 0);
+                cs[cur][k] = f2(c, s);
+                pinfo[cur][k] = qi < M ? make_int4(pi, qi, pi * ld, qi * ld) : make_int4(pi, -1, pi * ld, 0);
+            } else if (warp < nvw && g > 0) {
+                update_v(cur ^ 1);
             }
             __syncthreads();
+            // phase 2: the off-diagonal blocks
 #pragma unroll
             for (int j = 0; j < NBREG; ++j)
-                if (ab[j] >= 0) update_block(ab[j] & 0xffff, ab[j] >> 16);
-            // V <- V J: one warp per pair of columns, four rows per lane
-            for (int k = warp; k < half; k += nwarps) {
-                const float2 r = cs[k];
-                const int4 pk = pinfo[k];
-                if (r.y == 0.f || pk.y < 0 || !vlane) continue;
-                float4* Vp = reinterpret_cast<float4*>(V + pk.x * ldv) + lane;
-                float4* Vq = reinterpret_cast<float4*>(V + pk.y * ldv) + lane;
-                const float4 vp = *Vp, vq = *Vq;
-                const float2 c2 = f2(r.x, r.x), s2 = f2(r.y, r.y), ms2 = f2(-r.y, -r.y);
-                const float2 p01 = __ffma2_rn(c2, f2(vp.x, vp.y), __fmul2_rn(ms2, f2(vq.x, vq.y)));
-                const float2 p23 = __ffma2_rn(c2, f2(vp.z, vp.w), __fmul2_rn(ms2, f2(vq.z, vq.w)));
-                const float2 q01 = __ffma2_rn(s2, f2(vp.x, vp.y), __fmul2_rn(c2, f2(vq.x, vq.y)));
-                const float2 q23 = __ffma2_rn(s2, f2(vp.z, vp.w), __fmul2_rn(c2, f2(vq.z, vq.w)));
-                *Vp = make_float4(p01.x, p01.y, p23.x, p23.y);
-                *Vq = make_float4(q01.x, q01.y, q23.x, q23.y);
-            }
+                if (ab[j] >= 0) update_block(cs[cur], pinfo[cur], ab[j] & 0xffff, ab[j] >> 16);
             __syncthreads();
         }
         if (!s_rot) break;
+        __syncthreads();
+    }
+    if (g > 0) {   // V by the last step's rotations
+        if (warp < nvw) update_v((g - 1) & 1);
         __syncthreads();
     }
     // eigenvalues sorted decreasingly (rank counting)
