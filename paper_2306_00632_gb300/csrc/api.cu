@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -207,6 +208,7 @@ extern "C" void tpcg_ctx_destroy(tpcg_ctx c) {
     if (!c) return;
     if (c->lo) tpcg_ctx_destroy(c->lo);
     if (c->sync_ev) cudaEventDestroy(c->sync_ev);
+    if (c->hstage) cudaFreeHost(c->hstage);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     for (auto& g : c->rgraphs) cudaGraphExecDestroy(g.exec);
     for (void* p : c->owned) cudaFree(p);
@@ -237,13 +239,22 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
     tpcg_ctx c = new tpcg_ctx_s();
     c->lo = nullptr;
     c->sync_ev = nullptr;
+    c->hstage = nullptr;
     c->own_stream = nullptr;
-    if (cudaEventCreateWithFlags(&c->sync_ev, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         c->sync_ev = nullptr;
         set_error("tpcg_ctx_create: cudaEventCreateWithFlags failed");
         delete c;
         return TPCG_E_CUDA;
+    }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->hstage), TPCG_HSTAGE_BYTES, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->hstage = nullptr;
+        cudaEventDestroy(c->sync_ev);
+        set_error("tpcg_ctx_create: cudaHostAlloc of the staging buffer failed");
+        delete c;
+        return TPCG_E_NOMEM;
     }
     c->n = n;
     c->max_cols = max_cols;
@@ -707,11 +718,43 @@ int tpcg::ensure_tensors(tpcg_ctx c, int count) {
     return TPCG_OK;
 }
 
-// wait on the host for the work enqueued on s so far; the thread sleeps instead of spinning, so that many
-// solver threads can share the host cores
+// wait on the host for the work enqueued on s so far.  The thread polls an event: a few yields, then short
+// sleeps.  Neither spinning in the driver (one core per waiting solver thread) nor a blocking-sync wait
+// (woken through the driver's interrupt path, slow once tens of solver threads wait at once) shares the host
+// cores as well when many solves run concurrently.
 int tpcg::host_wait(tpcg_ctx c, cudaStream_t s) {
     TPCG_CUDA(cudaEventRecord(c->sync_ev, s));
-    TPCG_CUDA(cudaEventSynchronize(c->sync_ev));
+    for (int it = 0;; ++it) {
+        const cudaError_t e = cudaEventQuery(c->sync_ev);
+        if (e == cudaSuccess) return TPCG_OK;
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            set_error(std::string("host_wait: ") + cudaGetErrorString(e));
+            return TPCG_E_CUDA;
+        }
+        if (it < 16)
+            std::this_thread::yield();
+        else
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+int tpcg::fetch(tpcg_ctx c, cudaStream_t s, const D2H* items, int count) {
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        if (off + items[i].bytes > TPCG_HSTAGE_BYTES) {
+            set_error("fetch: staging buffer too small");
+            return TPCG_E_INVALID;
+        }
+        TPCG_CUDA(cudaMemcpyAsync(c->hstage + off, items[i].src, items[i].bytes, cudaMemcpyDeviceToHost, s));
+        off += (items[i].bytes + 7) & ~(size_t)7;
+    }
+    TPCG_TRY(host_wait(c, s));
+    off = 0;
+    for (int i = 0; i < count; ++i) {
+        memcpy(items[i].dst, c->hstage + off, items[i].bytes);
+        off += (items[i].bytes + 7) & ~(size_t)7;
+    }
     return TPCG_OK;
 }
 
@@ -722,8 +765,7 @@ static int true_residual(tpcg_problem pb, tpcg_ctx c, const tucker_t* x, tucker_
     double* d = c->scal + 130;
     TPCG_TRY(tensor_norm2<T>(c, work, d, s));
     double h = 0.0;
-    TPCG_CUDA(cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TPCG_TRY(host_wait(c, s));
+    TPCG_TRY(fetch(c, s, {{&h, d, sizeof(double)}}));
     *rel = pb->norm_f > 0 ? sqrt(std::max(h, 0.0)) / pb->norm_f : 0.0;
     return TPCG_OK;
 }
@@ -779,10 +821,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     const bool trace = tr && tr[0] == '1';
     for (;;) {
         int flags[2] = {0, 0};
-        TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
-        TPCG_CUDA(cudaMemcpyAsync(&flags[0], apply_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        TPCG_CUDA(cudaMemcpyAsync(&flags[1], fd_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        TPCG_TRY(host_wait(c, s));
+        TPCG_TRY(fetch(c, s, {{host, sc, sizeof(host)}, {&flags[0], apply_err, sizeof(int)}, {&flags[1], fd_err, sizeof(int)}}));
         if (flags[0] || flags[1]) {
             set_error(std::string("tpcg_solve: an unrounded ") + (flags[0] ? "operator product" : "preconditioner output") +
                       " exceeded the context's max_cols or the block limit");
@@ -820,8 +859,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
             launch_scalar(OP_DT, sc, dprm, s);
             ++trials_total;
             double done;
-            TPCG_CUDA(cudaMemcpyAsync(&done, sc + S_DONE, sizeof(double), cudaMemcpyDeviceToHost, s));
-            TPCG_TRY(host_wait(c, s));
+            TPCG_TRY(fetch(c, s, {{&done, sc + S_DONE, sizeof(double)}}));
             if (done != 0.0 || trial > 64) break;
         }
         std::swap(x, big2);
@@ -852,7 +890,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     // (the internal tensors all have the same capacities, so their roles need no restoring)
     int rk[3] = {0, 0, 0};
     int nb = 0;
-    TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
+    TPCG_TRY(fetch(c, s, {{host, sc, sizeof(host)}}));
     TPCG_TRY(tucker_get_ranks(xout, rk, &nb, s));
     if (st) {
         st->iters = k;
@@ -914,8 +952,7 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
         TPCG_TRY(apply_impl<double>(pb, xacc, big, true, s));
         TPCG_TRY(round_mixed(c, c32, big, r32, 0.1 * prm->inner_tol, nullptr, rc, abs_tol, info, s));
         double h[6];
-        TPCG_CUDA(cudaMemcpyAsync(h, info, sizeof(h), cudaMemcpyDeviceToHost, s));
-        TPCG_TRY(host_wait(c, s));
+        TPCG_TRY(fetch(c, s, {{h, info, sizeof(h)}}));
         rel = nf > 0 ? sqrt(std::max(h[0], 0.0)) / nf : 0.0;
         if (trace) fprintf(stderr, "mixed outer=%d true_res=%.3e r-rank=(%g,%g,%g)\n", outer, rel, h[2], h[3], h[4]);
         if (!(rel == rel)) { status = TPCG_E_BREAKDOWN; break; }

@@ -147,7 +147,8 @@ struct tpcg_ctx_s {
     int have_tens;       // solver tensors allocated so far
     int tens_cap;
     tpcg_ctx_s* lo;      // FP32 companion of a mixed-precision context (else null)
-    cudaEvent_t sync_ev; // blocking-sync event for the solver's host waits (the waiting thread sleeps)
+    cudaEvent_t sync_ev; // event the solver's host waits poll
+    unsigned char* hstage;   // pinned host staging for the solver's device-to-host reads (TPCG_HSTAGE_BYTES)
     cudaStream_t own_stream;   // created on first use by tpcg_solve_batch for NULL stream entries
     // captured roundings (CUDA graphs) of the solver tensors, keyed by tensor and tolerance source
     struct RoundGraph {

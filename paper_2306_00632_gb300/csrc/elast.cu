@@ -142,11 +142,9 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
     int k = 0, status = TPCG_OK, trials_total = 0;
     for (;;) {
         int flags[10] = {0};
-        TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
-        TPCG_CUDA(cudaMemcpyAsync(&flags[9], fd_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        for (int q9 = 0; q9 < 9; ++q9)
-            TPCG_CUDA(cudaMemcpyAsync(&flags[q9], e->blk[q9]->d_scal + 60, sizeof(int), cudaMemcpyDeviceToHost, s));
-        TPCG_TRY(host_wait(c, s));
+        D2H rd[11] = {{host, sc, sizeof(host)}, {&flags[9], fd_err, sizeof(int)}};
+        for (int q9 = 0; q9 < 9; ++q9) rd[2 + q9] = {&flags[q9], e->blk[q9]->d_scal + 60, sizeof(int)};
+        TPCG_TRY(fetch(c, s, rd, 11));
         bool over = false;
         for (int q9 = 0; q9 < 10; ++q9) over = over || flags[q9] != 0;
         if (over) {
@@ -170,8 +168,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
             launch_scalar(OP_DT, sc, dprm, s);
             ++trials_total;
             double done;
-            TPCG_CUDA(cudaMemcpyAsync(&done, sc + S_DONE, sizeof(double), cudaMemcpyDeviceToHost, s));
-            TPCG_TRY(host_wait(c, s));
+            TPCG_TRY(fetch(c, s, {{&done, sc + S_DONE, sizeof(double)}}));
             if (done != 0.0 || trial > 64) break;
         }
         bswap(x, big2);
@@ -204,8 +201,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
     TPCG_TRY(elast_apply_impl<T>(e, x, big, true, cap, s));
     for (int i = 0; i < 3; ++i) TPCG_TRY(tensor_norm2<T>(c, big[i], sc + 170 + i, s));
     double nr2[3];
-    TPCG_CUDA(cudaMemcpyAsync(nr2, sc + 170, sizeof(nr2), cudaMemcpyDeviceToHost, s));
-    TPCG_CUDA(cudaMemcpyAsync(host, sc, sizeof(host), cudaMemcpyDeviceToHost, s));
+    TPCG_TRY(fetch(c, s, {{nr2, sc + 170, sizeof(nr2)}, {host, sc, sizeof(host)}}));
     int rk[3][3], nb = 0;
     for (int i = 0; i < 3; ++i) TPCG_TRY(tucker_get_ranks(&xout[i], rk[i], &nb, s));   // synchronises
     if (st) {

@@ -1,6 +1,8 @@
 // Declarations of the templated device-side operations (one instantiation per compute dtype).
 #pragma once
 
+#include <initializer_list>
+
 #include "common.cuh"
 
 namespace tpcg {
@@ -60,7 +62,19 @@ void launch_scalar(int op, double* s, const double* prm, cudaStream_t st);
 int check_tensor(const tucker_t* t, int n, int dtype, const char* what);
 // allocate the first `count` solver tensors of the context (n x max_cols factors, rank_cap^3 core)
 int ensure_tensors(tpcg_ctx c, int count);
-// wait on the host for the work enqueued on s (blocking-sync event: the thread sleeps)
+// wait on the host for the work enqueued on s: polls an event, yielding and then sleeping between polls
 int host_wait(tpcg_ctx c, cudaStream_t s);
+// device-to-host reads of small values through the context's pinned staging buffer, then one host_wait:
+// copies into pageable memory would make the driver wait inside the copy call itself (spinning a core)
+constexpr size_t TPCG_HSTAGE_BYTES = 4096;
+struct D2H {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+int fetch(tpcg_ctx c, cudaStream_t s, const D2H* items, int count);
+inline int fetch(tpcg_ctx c, cudaStream_t s, std::initializer_list<D2H> items) {
+    return fetch(c, s, items.begin(), (int)items.size());
+}
 
 }  // namespace tpcg
