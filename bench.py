@@ -203,7 +203,7 @@ def _roofline(prof, dt_name, lib, step_ms_total):
     classes = ["zgemm", "zblk", "gram", "eig", "proj", "qr", "apply", "fd"]
     # DRAM bytes per launch of the FP32 eigensolver from one ncu capture of this workload (dram__bytes_read.sum +
     # dram__bytes_write.sum, mean of 3 launches); other kernels: no capture, traffic null
-    ncu_traffic = {"eig": 58539.0} if dt_name == "mixed" else {}
+    ncu_traffic = {"eig": 105216.0} if dt_name == "mixed" else {}
     dom = max(classes, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     per_launch_ms = d["ms"] / max(d["launches"], 1)
