@@ -15,8 +15,9 @@ Readings:
     (trapezoidal rule, step h, nodes s_k = s0 + k h), with (h, s0, R) chosen by a search so that
     E_R(M) <= eps_prec / M on a log grid of [1, M] (selection on 400 points, acceptance on 4000);
     R_P is the smallest such R found.
-    The search is not a best approximation, so R_P >= the paper's Table 1 values: parity unpinned
-    for R_P itself; the bound E_R(M_P) M_P <= eps_prec is pinned.
+    The search is not a best approximation, so this R_P is larger than the paper's Table 1 values; the
+    bound E_R(M_P) M_P <= eps_prec is pinned.  The best sums, whose R_P reproduces Table 1, are in
+    oracle/expsum.py; ApproxFD takes them through its `expsum` argument.
 """
 from __future__ import annotations
 

@@ -1,0 +1,58 @@
+"""Pins of the best exponential sums (oracle/expsum.py) against what the paper and the mathematics fix:
+Table 1's R_P (eq. estimate_prec_rel) computed from Table 1's own M_P, the alternation theorem that
+characterises a best approximation, Prop. 1's error bound, and the preconditioner bound eq. prec_bound with
+the sums in place."""
+import json
+import pathlib
+
+import numpy as np
+import pytest
+
+from oracle import expsum, fd
+
+TABLE1 = json.loads((pathlib.Path(__file__).parent / "golden" / "table1.json").read_text())
+
+
+@pytest.mark.parametrize("p", ["2", "3"])
+def test_rp_equals_table1_at_128_elements(p):
+    # Table 1, n_el = 128: M_P as printed (two digits) and R_P = 11 (p = 2), 12 (p = 3)
+    M = TABLE1["M_P"][p][0]
+    R, om, al, E, E_prev = expsum.rp_best(M, 0.1)
+    assert R == TABLE1["R_P"][p][0]
+    assert E * M <= 0.1 < E_prev * M          # R_P is the smallest R meeting eq. estimate_prec_rel
+    assert np.all(om > 0) and np.all(al > 0)  # Prop. 1: positive parameters
+
+
+@pytest.mark.parametrize("R,M", [(4, 100.0), (9, 5.0e3)])
+def test_error_equioscillates_at_2r_plus_1_points(R, M):
+    # alternation theorem: the best R-term sum's error reaches +-E_R(M) at 2R + 1 alternating points
+    om, al, E, ok = expsum.best_expsum(R, M)
+    assert ok
+    pts, ev, emax = expsum.alternants(om, al, M)
+    assert len(pts) >= 2 * R + 1
+    top = np.sort(np.abs(ev))[::-1][:2 * R + 1]
+    assert np.all(top >= (1 - 1e-6) * emax)
+    assert np.all(np.sign(ev[1:]) == -np.sign(ev[:-1]))
+
+
+@pytest.mark.parametrize("R,M", [(3, 50.0), (8, 2.0e3), (12, 2.3e4)])
+def test_below_prop1_bound_and_better_than_sinc(R, M):
+    om, al, E, ok = expsum.best_expsum(R, M)
+    assert ok
+    assert E <= 16.0 * np.exp(-R * np.pi ** 2 / np.log(8.0 * M))    # eq. estimate_approx_diag
+    # no R-term sinc-quadrature sum of the grid the FD setup searches does better than the best sum
+    best_sinc = min(fd.expsum_error(*fd.sinc_expsum(R, h, s0), M, 2000)
+                    for h in np.linspace(0.15, 1.6, 30) for s0 in np.linspace(-8.0, 4.0, 49))
+    assert E <= best_sinc
+
+
+def test_preconditioner_bound_with_best_sums():
+    # eq. prec_bound: ||D^-1||_inf ||D - D~||_inf <= eps_prec on the full diagonal, with R_P best terms
+    P0 = fd.ApproxFD(10, 3)
+    R, om, al, E, _ = expsum.rp_best(P0.MP, 0.1)
+    assert R < P0.RP                              # fewer terms than the sinc sums for the same bound
+    P = fd.ApproxFD(10, 3, expsum=(om, al))
+    lam = P.lam
+    L = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+    Dt = sum(P.omega[j] / P.lmin * np.einsum("i,j,k->ijk", P.diag(j), P.diag(j), P.diag(j)) for j in range(P.RP))
+    assert np.abs(1.0 / L - Dt).max() * L.max() <= 0.1
