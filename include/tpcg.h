@@ -274,7 +274,19 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   and argument group; 1..64 caps the grid and the kernel strides over the groups; default 2, measured best
  *   with 32 solves at once: 4.0 against 3.6 solves/s uncapped). */
 #define TPCG_OPT_GEMM_CTAS_PER_SM 1
+/*   TPCG_OPT_EXPSUM_BEST: which exponential sums (Prop. 1) tpcg_setup / tpcg_elast_setup build for the FD
+ *   preconditioner: 0 (default) the sinc-quadrature sums found by a search, R_P above Table 1's; 1 the best
+ *   sums of tpcg_expsum_best, whose R_P reproduces Table 1.  Problems set up earlier keep their sums. */
+#define TPCG_OPT_EXPSUM_BEST 2
 int tpcg_set_option(int key, long long value);
+
+/* Best exponential sum s_R(lambda) = sum_j omega_j exp(-alpha_j lambda) for 1/lambda on [1, M] in the maximum
+ * norm (Prop. 1, eq. estimate_approx_diag), with R the smallest number of terms meeting E_R(M) <= eps_prec / M
+ * (the R_P of eq. estimate_prec_rel when M = M_P).  Computed on the host (no GPU call) by the Remez exchange on
+ * the alternation points of the error.  omega, alpha: caller-owned host arrays of at least rmax entries;
+ * *R_out = R; *E_out (may be NULL) = E_R(M).  Returns TPCG_E_INVALID for a null output, rmax < 1, M < 1,
+ * eps_prec <= 0, or when no R <= rmax meets the bound.  Takes seconds for M up to ~1e6. */
+int tpcg_expsum_best(double M, double eps_prec, int rmax, double* omega, double* alpha, int* R_out, double* E_out);
 
 /* ------------------------------------------------------------------------------------ profiling */
 /* Kernel classes timed with CUDA events on the launching stream while profiling is on:

@@ -16,8 +16,9 @@ computes the best approximation itself:
   extrema of the new error, and the two steps repeat until the largest error equals |E|.
 * The exchange needs a start whose error already alternates 2R + 1 times. It comes from a weighted
   least-squares fit on a logarithmic grid, reweighted a few times towards the maximum norm (Lawson's
-  iteration). That fit starts from the (R - 1)-term best sum, its log alpha / log omega profile stretched to
-  R terms; R = 1 starts from omega = alpha = 1/2.
+  iteration); when the exchange does not converge from it, a longer and more heavily reweighted fit is
+  the second start. Both fits start from the (R - 1)-term best sum, its log alpha / log omega profile
+  stretched to R terms; R = 1 starts from omega = alpha = 1/2.
 
 R_P = min{R : E_R(M_P) <= eps_prec / M_P} (eq. estimate_prec_rel) is then found by increasing R.
 """
@@ -154,8 +155,12 @@ def best_sums(M: float, rmax: int, stop=None):
     for R in range(1, rmax + 1):
         if R > 1:
             omega, alpha = _stretch(omega, alpha)
-        omega, alpha = _least_squares_start(M, omega, alpha)
-        omega, alpha, E, ok = remez(M, omega, alpha)
+        o1, a1 = _least_squares_start(M, omega, alpha)
+        o1, a1, E, ok = remez(M, o1, a1)
+        if not ok:   # a start that did not lead to equioscillation: a longer, more heavily reweighted fit
+            o1, a1 = _least_squares_start(M, omega, alpha, npts=4000, lawson=6)
+            o1, a1, E, ok = remez(M, o1, a1)
+        omega, alpha = o1, a1
         yield R, omega, alpha, E, ok
         if stop is not None and stop(E):
             return

@@ -323,6 +323,22 @@ def max_cols_for(info, rank_cap: int, dtype: int) -> int:
     return max(info.R * rank_cap + rhs, info.RP * rank_cap, 2 * rank_cap)
 
 
+def expsum_best(M: float, eps_prec: float = 0.1, rmax: int = 60):
+    """tpcg_expsum_best: the best exponential sum for 1/lambda on [1, M] with the fewest terms meeting
+    E_R(M) <= eps_prec / M (Prop. 1, eq. estimate_prec_rel).  Host computation.  Returns (omega, alpha, E)."""
+    om = (C.c_double * rmax)()
+    al = (C.c_double * rmax)()
+    R = C.c_int(0)
+    E = C.c_double(0.0)
+    check(L.load().tpcg_expsum_best(M, eps_prec, rmax, om, al, C.byref(R), C.byref(E)), "tpcg_expsum_best")
+    return np.array(om[:R.value]), np.array(al[:R.value]), E.value
+
+
+def set_option(key: int, value: int):
+    """tpcg_set_option (process-wide)."""
+    check(L.load().tpcg_set_option(key, value), "tpcg_set_option")
+
+
 def tpcg_params(**kw):
     p = L.Params()
     L.load().tpcg_params_default(C.byref(p))

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libtpcg_gb300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["round.cu", "eig.cu", "ops.cu", "api.cu", "elast.cu", "prof.cu"]
-CXX_SOURCES = ["setup.cpp"]
+CXX_SOURCES = ["setup.cpp", "expsum.cpp"]
 
 
 def _digest() -> str:

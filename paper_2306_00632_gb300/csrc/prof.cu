@@ -116,11 +116,17 @@ extern "C" int tpcg_profile_get(int kind, double* ms_total, long long* count, do
 namespace tpcg {
 static std::atomic<int> g_gemm_ctas_per_sm{2};
 int gemm_ctas_per_sm() { return g_gemm_ctas_per_sm.load(std::memory_order_relaxed); }
+static std::atomic<int> g_expsum_kind{0};
+int expsum_kind() { return g_expsum_kind.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
     if (key == TPCG_OPT_GEMM_CTAS_PER_SM && value >= 0 && value <= 64) {
         tpcg::g_gemm_ctas_per_sm.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_EXPSUM_BEST && (value == 0 || value == 1)) {
+        tpcg::g_expsum_kind.store((int)value);
         return TPCG_OK;
     }
     tpcg::set_error("tpcg_set_option: unknown key or value out of range");

@@ -807,7 +807,8 @@ static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_p
     H.lambda_min = 3.0 * lmin;
     H.lambda_max = 3.0 * lmax;
     const double MP = H.lambda_max / H.lambda_min;
-    H.RP = expsum_sinc(MP, eps_prec, &H.omega, &H.alpha);
+    H.RP = expsum_kind() == 1 ? expsum_best(MP, eps_prec, 60, &H.omega, &H.alpha, nullptr)
+                              : expsum_sinc(MP, eps_prec, &H.omega, &H.alpha);
     if (H.RP < 1) {
         set_error("tpcg_setup: no exponential sum found");
         return TPCG_E_INVALID;

@@ -32,5 +32,10 @@ int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double 
 // pieces exposed for the exponential-sum search (also used by tests through the C ABI of the setup)
 double expsum_error(const double* omega, const double* alpha, int R, double M, int npts);
 int expsum_sinc(double M, double eps_prec, std::vector<double>* omega, std::vector<double>* alpha);
+// best sums by the Remez exchange (expsum.cpp): the smallest R <= rmax with E_R(M) <= eps_prec / M, or -1
+int expsum_best(double M, double eps_prec, int rmax, std::vector<double>* omega, std::vector<double>* alpha,
+                double* E_out);
+// which sums tpcg_setup uses: 0 the sinc-quadrature search, 1 best sums (tpcg_set_option)
+int expsum_kind();
 
 }  // namespace tpcg

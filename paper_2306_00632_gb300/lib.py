@@ -26,11 +26,13 @@ SYMBOLS = [
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
     "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_ctx_stream", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count", "tpcg_set_option",
+    "tpcg_expsum_best",
     "tpcg_elast_setup", "tpcg_elast_create", "tpcg_elast_get_info", "tpcg_elast_apply", "tpcg_elast_residual",
     "tpcg_elast_precond", "tpcg_elast_solve", "tpcg_elast_destroy",
 ]
 PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
               "round": 9}
+OPT_GEMM_CTAS_PER_SM, OPT_EXPSUM_BEST = 1, 2   # tpcg_set_option keys
 PROF_SWEEPS = 11   # one-CTA Jacobi: (sweeps, Grams) in the (flops, bytes) fields of this kind
 
 
@@ -121,6 +123,7 @@ def load(build_if_missing: bool = True):
         "tpcg_profile_get": (i, [i, C.POINTER(d), C.POINTER(C.c_longlong), C.POINTER(d), C.POINTER(d)]),
         "tpcg_launch_count": (C.c_longlong, []),
         "tpcg_set_option": (i, [i, C.c_longlong]),
+        "tpcg_expsum_best": (i, [d, d, i, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(d)]),
         "tpcg_version": (C.c_char_p, []),
         "tpcg_elast_setup": (i, [C.POINTER(Geometry), i, i, d, d, C.POINTER(d), i, C.POINTER(vp)]),
         "tpcg_elast_create": (i, [C.POINTER(ProblemArrays), d, d, C.POINTER(vp)]),

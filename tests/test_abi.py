@@ -33,3 +33,29 @@ def test_ctx_bytes_is_host_only_and_monotone():
     b = L.tpcg_ctx_bytes(128, 2048, 64, 0)
     c = L.tpcg_ctx_bytes(128, 2048, 64, 1)
     assert 0 < a < b and c < b
+
+
+def test_expsum_best_is_host_only_and_matches_the_oracle():
+    # tpcg_expsum_best (the setup's best sums, no GPU call) against the oracle's Remez exchange and Table 1:
+    # the best approximation is unique, so the two independent implementations agree to rounding
+    import json
+    import numpy as np
+    from oracle import expsum
+    from paper_2306_00632_gb300 import api
+    t1 = json.load(open(os.path.join(ROOT, "tests", "golden", "table1.json")))
+    for p in ("2", "3"):
+        M, want = t1["M_P"][p][0], t1["R_P"][p][0]
+        om, al, E = api.expsum_best(M, 0.1)
+        R, om_o, al_o, E_o, _ = expsum.rp_best(M, 0.1)
+        assert len(om) == R == want
+        a, b = np.argsort(al), np.argsort(al_o)
+        assert np.allclose(al[a], al_o[b], rtol=1e-8) and np.allclose(om[a], om_o[b], rtol=1e-8)
+        assert abs(E - E_o) <= 1e-8 * E_o and E * M <= 0.1
+    # invalid arguments are rejected before any work
+    import ctypes as C
+    from paper_2306_00632_gb300 import lib
+    L = lib.load()
+    buf = (C.c_double * 4)()
+    R = C.c_int(0)
+    assert L.tpcg_expsum_best(0.5, 0.1, 4, buf, buf, C.byref(R), None) == 1    # M < 1
+    assert L.tpcg_expsum_best(2.3e4, 0.1, 4, buf, buf, C.byref(R), None) == 1  # no R <= 4 meets the bound
