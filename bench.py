@@ -2,8 +2,9 @@
 """TPCG benchmark on GB300: solves/sec to relative residual 1e-6 (plus p50/p99 latency) for the
 single deformed-geometry Poisson workload (twisted quarter annulus, p = 3, n = 128 dofs per direction).
 
-One step = one complete TPCG solve (Alg. 5 with Alg. 1, 2, 4; every hot-path kernel) of the resident
-problem.  ``python bench.py --gpus N --steps K --warmup W`` prints one JSON line on rank 0.
+One step = ``--concurrent`` (default 32) complete TPCG solves (Alg. 5 with Alg. 1, 2, 4; every hot-path
+kernel) of resident problems of the same family (one seed each), run at once; the single-solve latency is
+measured separately.  ``python bench.py --gpus N --steps K --warmup W`` prints one JSON line on rank 0.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (a bounded sample).
 Multi-GPU: independent replicas (one solve stream per GPU, no collective), weak scaling.
 """
