@@ -124,10 +124,12 @@ class ClockSampler:
 def oracle_sample(iters_for_scale: int, n=N_DOF, p=DEGREE, sample_iters=20):
     """Time `sample_iters` iterations of the oracle's Alg. 5 on the same workload (setup excluded) and
     scale to solves/sec with the iteration count of a full solve."""
-    from oracle import fd, lowrank, tpcg as otp
+    from oracle import expsum, fd, lowrank, tpcg as otp
     terms = lowrank.operator_terms("twist", AMP, n, p)
     f = lowrank.rhs_tucker("twist", AMP, n, p)
-    P = fd.ApproxFD(n, p)
+    # the preconditioner with the best exponential sums for this M_P, as the library's setup builds it
+    _, om, al, _, _ = expsum.rp_best(fd.mp_value(n, p), 0.1)
+    P = fd.ApproxFD(n, p, expsum=(om, al))
     t0 = time.perf_counter()
     _, info = otp.tpcg(terms, f, P.apply, otp.Params(tol=TOL, max_it=sample_iters))
     dt = time.perf_counter() - t0

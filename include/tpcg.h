@@ -275,8 +275,9 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   with 32 solves at once: 4.0 against 3.6 solves/s uncapped). */
 #define TPCG_OPT_GEMM_CTAS_PER_SM 1
 /*   TPCG_OPT_EXPSUM_BEST: which exponential sums (Prop. 1) tpcg_setup / tpcg_elast_setup build for the FD
- *   preconditioner: 0 (default) the sinc-quadrature sums found by a search, R_P above Table 1's; 1 the best
- *   sums of tpcg_expsum_best, whose R_P reproduces Table 1.  Problems set up earlier keep their sums. */
+ *   preconditioner: 1 (default) the best sums of tpcg_expsum_best, whose R_P reproduces Table 1; 0 the
+ *   sinc-quadrature sums found by a search (R_P about twice Table 1's).  Problems set up earlier keep their
+ *   sums. */
 #define TPCG_OPT_EXPSUM_BEST 2
 int tpcg_set_option(int key, long long value);
 

@@ -116,7 +116,7 @@ extern "C" int tpcg_profile_get(int kind, double* ms_total, long long* count, do
 namespace tpcg {
 static std::atomic<int> g_gemm_ctas_per_sm{2};
 int gemm_ctas_per_sm() { return g_gemm_ctas_per_sm.load(std::memory_order_relaxed); }
-static std::atomic<int> g_expsum_kind{0};
+static std::atomic<int> g_expsum_kind{1};
 int expsum_kind() { return g_expsum_kind.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 

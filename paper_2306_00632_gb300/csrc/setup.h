@@ -35,7 +35,7 @@ int expsum_sinc(double M, double eps_prec, std::vector<double>* omega, std::vect
 // best sums by the Remez exchange (expsum.cpp): the smallest R <= rmax with E_R(M) <= eps_prec / M, or -1
 int expsum_best(double M, double eps_prec, int rmax, std::vector<double>* omega, std::vector<double>* alpha,
                 double* E_out);
-// which sums tpcg_setup uses: 0 the sinc-quadrature search, 1 best sums (tpcg_set_option)
+// which sums tpcg_setup uses: 1 best sums (default), 0 the sinc-quadrature search (tpcg_set_option)
 int expsum_kind();
 
 }  // namespace tpcg

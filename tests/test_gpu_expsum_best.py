@@ -1,6 +1,6 @@
-"""The setup with best exponential sums (tpcg_set_option(TPCG_OPT_EXPSUM_BEST, 1)): R_P and the sums equal the
-oracle's Remez exchange, the FD preconditioner built from them equals the oracle's Alg. 4 with the same sums,
-and TPCG converges with it."""
+"""The setup's best exponential sums (the default, tpcg_set_option(TPCG_OPT_EXPSUM_BEST, 1)): R_P and the sums
+equal the oracle's Remez exchange, the FD preconditioner built from them equals the oracle's Alg. 4 with the
+same sums, TPCG converges with it, and the sinc-search setup (option 0) needs more terms."""
 import numpy as np
 import pytest
 
@@ -25,11 +25,7 @@ def mods():
 def test_setup_with_best_sums(mods):
     api, lib = mods
     n, p, amp = 20, 3, 0.2
-    api.set_option(lib.OPT_EXPSUM_BEST, 1)
-    try:
-        pb = api.tpcg_setup(lib.GEOM_TWIST, amp, p, n)
-    finally:
-        api.set_option(lib.OPT_EXPSUM_BEST, 0)
+    pb = api.tpcg_setup(lib.GEOM_TWIST, amp, p, n)
     info = pb.info
     ex = pb.export()
     R, om, al, E, E_prev = expsum.rp_best(info.MP, 0.1)
@@ -37,8 +33,13 @@ def test_setup_with_best_sums(mods):
     a, b = np.argsort(np.asarray(ex["alpha"])), np.argsort(al)
     assert np.allclose(np.asarray(ex["alpha"])[a], al[b], rtol=1e-8)
     assert np.allclose(np.asarray(ex["omega"])[a], om[b], rtol=1e-8)
-    # fewer terms than the default setup of the same problem
-    assert info.RP < api.tpcg_setup(lib.GEOM_TWIST, amp, p, n).info.RP
+    # fewer terms than the sinc-search setup of the same problem
+    api.set_option(lib.OPT_EXPSUM_BEST, 0)
+    try:
+        rp_sinc = api.tpcg_setup(lib.GEOM_TWIST, amp, p, n).info.RP
+    finally:
+        api.set_option(lib.OPT_EXPSUM_BEST, 1)
+    assert info.RP < rp_sinc
     # Alg. 4 on the GPU with these sums against the oracle's Alg. 4 with the same sums
     P = fd.ApproxFD(n, p, expsum=(np.asarray(ex["omega"]), np.asarray(ex["alpha"])))
     S = synth.random_tucker((n, n, n), (2, 3, 2), seed=31)
