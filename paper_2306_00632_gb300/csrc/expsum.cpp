@@ -14,7 +14,10 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/tpcg.h"
@@ -288,8 +291,8 @@ void stretch(Vec& om, Vec& al) {
 
 }  // namespace
 
-int expsum_best(double M, double eps_prec, int rmax, std::vector<double>* omega, std::vector<double>* alpha,
-                double* E_out) {
+static int expsum_best_compute(double M, double eps_prec, int rmax, std::vector<double>* omega,
+                               std::vector<double>* alpha, double* E_out) {
     if (!(M >= 1.0) || !(eps_prec > 0.0) || rmax < 1) return -1;
     Vec om{0.5}, al{0.5};
     for (int R = 1; R <= rmax; ++R) {
@@ -305,6 +308,40 @@ int expsum_best(double M, double eps_prec, int rmax, std::vector<double>* omega,
         }
     }
     return -1;
+}
+
+// M_P depends only on n, p and the direction weights, not on the geometry, so many setups share it: results
+// are kept per (M, eps_prec, rmax) for the life of the process (at most 256 entries)
+int expsum_best(double M, double eps_prec, int rmax, std::vector<double>* omega, std::vector<double>* alpha,
+                double* E_out) {
+    using Key = std::tuple<double, double, int>;
+    struct Entry {
+        int R;
+        Vec om, al;
+        double E;
+    };
+    static std::mutex mu;
+    static std::map<Key, Entry> cache;
+    const Key key{M, eps_prec, rmax};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *omega = it->second.om;
+            *alpha = it->second.al;
+            if (E_out) *E_out = it->second.E;
+            return it->second.R;
+        }
+    }
+    double E = 0;
+    const int R = expsum_best_compute(M, eps_prec, rmax, omega, alpha, &E);
+    if (E_out) *E_out = E;
+    if (R > 0) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (cache.size() >= 256) cache.clear();
+        cache[key] = Entry{R, *omega, *alpha, E};
+    }
+    return R;
 }
 
 }  // namespace tpcg
