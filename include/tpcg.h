@@ -79,9 +79,10 @@ typedef struct {
 
 /* Host FP64 setup (App. A, App. B, Prop. 1) followed by upload: B-spline matrices, low-rank Chebyshev
  * approximation of Q(eta) and omega(eta) folded into a Kronecker sum A~ = sum_j w_j K3^j (x) K2^j (x) K1^j,
- * the Tucker rhs f~ (rounded losslessly), and the low-rank FD tables.  n dofs per direction, degree p,
- * n_el = n - p + 2 > p.  dtype selects the precision of the device copies.  *out is owned by the caller
- * and released with tpcg_problem_destroy. */
+ * the Tucker rhs f~ (rounded losslessly), and the low-rank FD tables with the exponential sums chosen by
+ * TPCG_OPT_EXPSUM_BEST (by default the best sums, R_P of eq. estimate_prec_rel as in Table 1).  n dofs per
+ * direction, degree p, n_el = n - p + 2 > p.  dtype selects the precision of the device copies.  *out is
+ * owned by the caller and released with tpcg_problem_destroy. */
 int tpcg_setup(const tpcg_geometry* geo, int degree, int n, int dtype, tpcg_problem* out);
 
 /* Problem from explicit host arrays (all double, column-major):
