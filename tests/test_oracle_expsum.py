@@ -56,3 +56,33 @@ def test_preconditioner_bound_with_best_sums():
     L = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
     Dt = sum(P.omega[j] / P.lmin * np.einsum("i,j,k->ijk", P.diag(j), P.diag(j), P.diag(j)) for j in range(P.RP))
     assert np.abs(1.0 / L - Dt).max() * L.max() <= 0.1
+
+
+def _stored_sweep():
+    p = pathlib.Path(__file__).parent / "golden" / "rp_best_table1.json"
+    return json.loads(p.read_text())
+
+
+def test_stored_sweep_reproduces_table1():
+    # rp_best_table1.json is written by tests/golden/make_rp_best.py (oracle only) for the 16 printed M_P of
+    # Table 1: R_P meets eq. estimate_prec_rel and R_P - 1 does not; R_P equals Table 1 except at most two
+    # entries where the best sum sits just under the threshold and R_P is one below Table 1's
+    g = _stored_sweep()
+    same = 0
+    for p in ("2", "3", "4", "5"):
+        for i in range(4):
+            R, want = g["R_P"][p][i], TABLE1["R_P"][p][i]
+            assert g["EM_at_RP"][p][i] <= 0.1 < g["EM_at_RP_minus_1"][p][i]
+            if R == want:
+                same += 1
+            else:
+                assert R == want - 1 and g["EM_at_RP"][p][i] > 0.09
+    assert same >= 14
+
+
+def test_stored_sweep_entry_recomputes():
+    g = _stored_sweep()
+    M = TABLE1["M_P"]["2"][1]                   # p = 2, n_el = 256
+    R, _, _, E, E_prev = expsum.rp_best(M, 0.1)
+    assert R == g["R_P"]["2"][1]
+    assert abs(E * M - g["EM_at_RP"]["2"][1]) <= 1e-5
