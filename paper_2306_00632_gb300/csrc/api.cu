@@ -821,7 +821,8 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     const bool trace = tr && tr[0] == '1';
     for (;;) {
         int flags[2] = {0, 0};
-        TPCG_TRY(fetch(c, s, {{host, sc, sizeof(host)}, {&flags[0], apply_err, sizeof(int)}, {&flags[1], fd_err, sizeof(int)}}));
+        TPCG_TRY(fetch(c, s, {{host, sc, sizeof(host)}, {&flags[0], apply_err, sizeof(int)},
+                              {&flags[1], fd_err, sizeof(int)}}));
         if (flags[0] || flags[1]) {
             set_error(std::string("tpcg_solve: an unrounded ") + (flags[0] ? "operator product" : "preconditioner output") +
                       " exceeded the context's max_cols or the block limit");

@@ -857,10 +857,13 @@ int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int
     T* Aw = reinterpret_cast<T*>(w.Aw);
     T* Vw = reinterpret_cast<T*>(w.Vw);
     if (a_smem && v_smem) {
-        TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T, true>), sizeof(T) == 8 ? 4 : 5, 190 * 1024));
-        jacobi_eig_kernel<T, true><<<1, EIG_THREADS, bytes, st>>>(plan, G, Aw, Vw, S, evals, m, 1, 1, 20, prof_dev());
+        TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T, true>), sizeof(T) == 8 ? 4 : 5,
+                            190 * 1024));
+        jacobi_eig_kernel<T, true><<<1, EIG_THREADS, bytes, st>>>(plan, G, Aw, Vw, S, evals, m, 1, 1, 20,
+                                                                 prof_dev());
     } else {
-        TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T, false>), sizeof(T) == 8 ? 2 : 3, 190 * 1024));
+        TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<T, false>), sizeof(T) == 8 ? 2 : 3,
+                            190 * 1024));
         jacobi_eig_kernel<T, false><<<1, EIG_THREADS, bytes, st>>>(plan, G, Aw, Vw, S, evals, m, a_smem, v_smem, 20,
                                                                   prof_dev());
     }
