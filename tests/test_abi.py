@@ -53,6 +53,13 @@ def test_expsum_best_is_host_only_and_matches_the_oracle():
         assert abs(E - E_o) <= 1e-8 * E_o and E * M <= 0.1
         om2, al2, E2 = api.expsum_best(M, 0.1)   # served from the per-M cache: the same sums
         assert np.array_equal(om, om2) and np.array_equal(al, al2) and E2 == E
+    # small M (few terms): the same best sums from both implementations
+    for M in (3.0, 40.0, 700.0, 5.0e3):
+        om, al, E = api.expsum_best(M, 0.1)
+        R, om_o, al_o, E_o, _ = expsum.rp_best(M, 0.1)
+        assert len(om) == R
+        a, b = np.argsort(al), np.argsort(al_o)
+        assert np.allclose(al[a], al_o[b], rtol=1e-7) and np.allclose(om[a], om_o[b], rtol=1e-7)
     # invalid arguments are rejected before any work
     import ctypes as C
     from paper_2306_00632_gb300 import lib
