@@ -186,3 +186,41 @@ def test_tpcg_twist_against_direct_solve():
     lmin = scipy.sparse.linalg.eigsh(A, k=1, which="SA", return_eigenvectors=False)[0]
     assert np.linalg.norm(xv - xe) <= 2e-6 * np.linalg.norm(fv) / lmin
     assert 5 <= info["iters"] <= 60
+
+
+def test_thick_quarter_annulus_ranks_and_tpcg_matches_exact_pcg():
+    # Sec. 5.2: the untwisted annulus is the paper's thick quarter annulus. Its coefficient ranks are (1, 1, 1)
+    # on the diagonal blocks and 0 off them, so A~ has R = 3 Kronecker terms. With the paper's manufactured
+    # solution u = (x^2 + y^2 - 1)(x^2 + y^2 - 4) sin(pi z) sin(7 x y), TPCG (Alg. 5 with the relaxed
+    # truncations of eq. rel_tol_iterates) needs no more iterations than textbook PCG with the same
+    # preconditioner on the assembled system: the truncation costs no convergence
+    sp = pytest.importorskip("sympy")
+    from oracle import bspline, expsum
+    x, y, z = sp.symbols("x y z")
+    u = (x ** 2 + y ** 2 - 1) * (x ** 2 + y ** 2 - 4) * sp.sin(sp.pi * z) * sp.sin(7 * x * y)
+    fx = sp.lambdify((x, y, z), -(sp.diff(u, x, 2) + sp.diff(u, y, 2) + sp.diff(u, z, 2)), "numpy")
+    n_el, p = 16, 2
+    n = n_el + p - 2
+    terms = lowrank.operator_terms("twist", 0.0, n, p)
+    assert len(terms) == 3
+    # load: det J f(F(eta)) (App. A) on the polar map rho = 1 + eta1, theta = pi eta2 / 2, z = eta3
+    xc = lowrank.cheb_points()
+    e1, e2, e3 = np.meshgrid(xc, xc, xc, indexing="ij")
+    rho, th = 1.0 + e1, 0.5 * np.pi * e2
+    core, U = lowrank.tucker_of_samples(0.5 * np.pi * rho * fx(rho * np.cos(th), rho * np.sin(th), e3), 1e-8)
+    xs, ws = bspline.quadrature(n_el, p)
+    B0 = bspline.dirichlet_basis(n_el, p, xs, 0)
+    F = (core, [(B0 * ws) @ lowrank.cheb_eval(U[t], xs) for t in range(3)])
+    P0 = fd.ApproxFD(n, p)
+    _, om, al, _, _ = expsum.rp_best(P0.MP, 0.1)
+    P = fd.ApproxFD(n, p, expsum=(om, al))
+    _, info = tpcg.tpcg(terms, F, P.apply, tpcg.Params(tol=1e-6))
+    A = fullcg.assemble(terms)
+    b = tucker.vec(tucker.full(F))
+
+    def prec(r):
+        R = tucker.unvec(r, (n, n, n))
+        return tucker.vec(tucker.full(P.apply((R, [np.eye(n)] * 3))))
+
+    _, it_full = fullcg.pcg(A, b, prec, tol=1e-6)
+    assert abs(info["iters"] - it_full) <= 1
