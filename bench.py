@@ -35,9 +35,16 @@ AMP = synth.amp_from_seed(SEED)
 TOL = 1e-6
 WORKLOAD = f"twisted quarter annulus Poisson, p={DEGREE}, n={N_DOF}/direction, amp={AMP:.4f} (seed {SEED})"
 METRIC = "TPCG solves/sec to rel-residual 1e-6"
-# iterations of the FP64 Alg. 5 on this workload (the FP64 GPU form takes 30 for seed 7): the CPU oracle's
-# per-iteration time is scaled by this count
-ORACLE_ITERS = 30
+# the oracle's own solution of this workload (tol 1e-10, rounded to 1e-9) and its iteration count at tol 1e-6,
+# written by tests/golden/make_ref_twist128.py (oracle only)
+REF_FILE = os.path.join(ROOT, "tests", "golden", "ref_twist128_seed7.npz")
+
+
+def oracle_reference():
+    """The stored oracle data of the workload: iteration count at tol 1e-6 and the reference solution."""
+    z = np.load(REF_FILE)
+    return {"iters": int(z["iters_tol6"]), "core": z["core"], "U": [z["U0"], z["U1"], z["U2"]], "mass": z["mass"],
+            "tol_ref": float(z["tol_ref"])}
 
 
 def parse():
@@ -52,12 +59,16 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=2e-2, help="mixed form: inner FP32 solve tolerance")
     ap.add_argument("--refine-keep", type=float, default=3e-2, help="mixed form: accuracy kept of each correction")
     ap.add_argument("--gemm-ctas-per-sm", type=int, default=2, help="grouped-GEMM CTA budget per SM (0: uncapped)")
+    ap.add_argument("--eig", type=int, default=1, choices=[0, 1],
+                    help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
     ap.add_argument("--serve", type=float, default=0.0,
                     help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
     ap.add_argument("--requests", type=int, default=48, help="requests in the --serve stream")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement beside the mixed one")
+    ap.add_argument("--fp64-concurrent", type=int, default=32, help="FP64 form: solves at once (0: single only)")
     return ap.parse_args()
 
 
@@ -121,40 +132,82 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------- CPU oracle
-def oracle_sample(iters_for_scale: int, n=N_DOF, p=DEGREE, sample_iters=20):
-    """Time `sample_iters` iterations of the oracle's Alg. 5 on the same workload (setup excluded) and
-    scale to solves/sec with the iteration count of a full solve."""
-    from oracle import expsum, fd, lowrank, tpcg as otp
-    terms = lowrank.operator_terms("twist", AMP, n, p)
-    f = lowrank.rhs_tucker("twist", AMP, n, p)
+def _oracle_setup(n=N_DOF, p=DEGREE, amp=AMP):
+    from oracle import expsum, fd, lowrank
+    terms = lowrank.operator_terms("twist", amp, n, p)
+    f = lowrank.rhs_tucker("twist", amp, n, p)
     # the preconditioner with the best exponential sums for this M_P, as the library's setup builds it
     _, om, al, _, _ = expsum.rp_best(fd.mp_value(n, p), 0.1)
-    P = fd.ApproxFD(n, p, expsum=(om, al))
+    return terms, f, fd.ApproxFD(n, p, expsum=(om, al))
+
+
+class _Stamps(list):
+    """A record list for the oracle's Alg. 5 that stamps the wall clock as each iteration ends."""
+
+    def append(self, item):
+        item["t"] = time.perf_counter()
+        super().append(item)
+
+
+def oracle_iterations(max_it: int, setup=None):
+    """Run the oracle's Alg. 5 on the workload for at most max_it iterations; returns (start time, per-iteration
+    end stamps, info)."""
+    from oracle import tpcg as otp
+    terms, f, P = setup or _oracle_setup()
+    rec = _Stamps()
     t0 = time.perf_counter()
-    _, info = otp.tpcg(terms, f, P.apply, otp.Params(tol=TOL, max_it=sample_iters))
-    dt = time.perf_counter() - t0
-    per_iter = dt / max(info["iters"], 1)
-    iters = max(iters_for_scale, 1)
+    _, info = otp.tpcg(terms, f, P.apply, otp.Params(tol=TOL, max_it=max_it), record=rec)
+    return t0, [r["t"] for r in rec], info
+
+
+def oracle_sample(sample_iters=20):
+    """Time the first `sample_iters` iterations of the oracle's Alg. 5 on the same workload (setup excluded)
+    and scale to solves/sec with the oracle's own iteration count to convergence (stored)."""
+    iters = oracle_reference()["iters"]
+    t0, stamps, info = oracle_iterations(sample_iters)
+    dt = stamps[-1] - t0
+    per_iter = dt / max(len(stamps), 1)
     return {"value": 1.0 / (per_iter * iters), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{info['iters']} TPCG iterations of the {n}^3 p={p} twisted-annulus solve in {dt:.1f}s "
-                      f"(setup excluded), scaled to a {iters}-iteration solve"}
+            "sample": f"the first {len(stamps)} TPCG iterations of the {N_DOF}^3 p={DEGREE} twisted-annulus solve "
+                      f"in {dt:.1f}s (setup excluded), scaled to the oracle's {iters}-iteration solve"}
 
 
 def run_reference(args):
+    """The oracle on the host cores: Alg. 5 runs on the workload timed in steps of CHUNK consecutive
+    iterations (a run that converges is restarted until K steps are timed; W untimed warm-up iterations
+    first).  value = 1 / (mean time per iteration x the oracle's iteration count to convergence);
+    ms_per_step is the mean measured time of a step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
+    CHUNK = 2
     K = max(args.steps, 1)
-    vals = []
-    for _ in range(K):
-        vals.append(oracle_sample(ORACLE_ITERS, sample_iters=2)["value"])
-    v = statistics.median(vals)
+    iters = oracle_reference()["iters"]
+    setup = _oracle_setup()
+    if args.warmup > 0:
+        oracle_iterations(args.warmup, setup)
+    steps, runs, converged = [], 0, False
+    while len(steps) < K:
+        t0, stamps, info = oracle_iterations((K - len(steps)) * CHUNK, setup)
+        runs += 1
+        converged = converged or bool(info["res"] <= TOL)
+        marks = [t0] + stamps
+        for k in range(0, len(stamps) - CHUNK + 1, CHUNK):
+            steps.append(marks[k + CHUNK] - marks[k])
+        if len(stamps) < CHUNK:
+            break
+    steps = steps[:K]
+    per_iter = sum(steps) / (CHUNK * len(steps))
+    v = 1.0 / (per_iter * iters)
+    sample = (f"{len(steps)} steps of {CHUNK} consecutive oracle Alg. 5 iterations in {runs} run(s) "
+              f"({sum(steps):.1f}s, setup excluded; a run reached tol: {converged}), "
+              f"scaled to the oracle's {iters}-iteration solve")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": K, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": len(steps), "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "tol": TOL},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"2 TPCG iterations per step, scaled to a {ORACLE_ITERS}-iteration solve"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -229,6 +282,111 @@ def _roofline(prof, dt_name, lib, step_ms_total):
     return roof
 
 
+# ------------------------------------------------------------------------------------------- solution error
+def _band_matrix_product(bands, j, t, Q, p):
+    """K_t^j Q for the banded matrix stored as bands[j, t, d, i] = K_t^j[i, i + d - p]."""
+    n = Q.shape[0]
+    out = np.zeros_like(Q)
+    for d in range(2 * p + 1):
+        o = d - p
+        lo, hi = max(0, -o), min(n, n - o)
+        out[lo:hi] += bands[j, t, d, lo:hi, None] * Q[lo + o:hi + o]
+    return out
+
+
+def _quad(Z, mats):
+    """<Z, Z x_1 M_1 x_2 M_2 x_3 M_3> for a dense core Z and symmetric matrices M_t."""
+    Y = np.einsum("ia,ajk->ijk", mats[0], Z, optimize=True)
+    Y = np.einsum("jb,ibk->ijk", mats[1], Y, optimize=True)
+    Y = np.einsum("kc,ijc->ijk", mats[2], Y, optimize=True)
+    return float(np.sum(Z * Y))
+
+
+def _norms(core, U, w, bands, p, mass):
+    """Coefficient 2-norm, parametric L2 norm and energy norm of a Tucker vector given by core and factors
+    with orthonormal-izable columns: a QR of every factor moves it into the core first, so a difference of two
+    close solutions is formed entry by entry in the small core (no cancellation in the quadratic forms)."""
+    Q, Z = [], core
+    for t in range(3):
+        q, r = np.linalg.qr(U[t])
+        Q.append(q)
+        Z = np.moveaxis(np.tensordot(r, Z, axes=(1, t)), 0, t)
+    l2c = float(np.linalg.norm(Z))
+    l2 = _quad(Z, [q.T @ mass @ q for q in Q])
+    en = 0.0
+    for j in range(len(w)):
+        en += w[j] * _quad(Z, [Q[t].T @ _band_matrix_product(bands, j, t, Q[t], p) for t in range(3)])
+    return l2c, np.sqrt(max(l2, 0.0)), np.sqrt(max(en, 0.0))
+
+
+def solution_error(X, ex, info, ref):
+    """Relative errors of a solution X = (core, factors) against the oracle's stored solution of the same
+    workload: coefficient 2-norm, L2 norm of the discrete function on the parametric cube (B-spline mass
+    matrix), and energy norm x^T A x with the library's operator."""
+    n, p, R = info.n, info.p, info.R
+    bands = np.asarray(ex["bands"]).reshape(R, 3, 2 * p + 1, n)
+    w = np.asarray(ex["w"])
+    core_x, Ux = X
+    core_r, Ur = ref["core"], ref["U"]
+    r1, r2 = core_x.shape, core_r.shape
+    G = np.zeros(tuple(a + b for a, b in zip(r1, r2)))
+    G[:r1[0], :r1[1], :r1[2]] = core_x
+    G[r1[0]:, r1[1]:, r1[2]:] = -core_r
+    e = _norms(G, [np.hstack([Ux[t], Ur[t]]) for t in range(3)], w, bands, p, ref["mass"])
+    r = _norms(core_r, Ur, w, bands, p, ref["mass"])
+    return {"rel_l2_coeff": e[0] / r[0], "rel_l2_param": e[1] / r[1], "rel_energy": e[2] / r[2],
+            "reference": f"oracle FP64 Alg. 5 at tol {ref['tol_ref']:g} (stored), seed {SEED}"}
+
+
+# ------------------------------------------------------------------------------------------- FP64 arm
+def fp64_arm(api, lib, pbs, rc, args, flush):
+    """The plain FP64 form on the same problems: a single solve alone (the comparison arm), then
+    args.fp64_concurrent solves at once; FP64 problems are re-created from the setup's exported tables."""
+    import torch
+    main = torch.cuda.current_stream()
+    B = min(max(args.fp64_concurrent, 1), len(pbs))
+    exs = []
+    for pb in pbs[:B]:
+        ex = pb.export()
+        ex["v2u2"] = ex["v2u2"][: pb.info.n * pb.info.n2]
+        exs.append((ex, pb.info))
+    pb64 = [api.problem_from_export(ex, info, dtype=lib.F64, pinned=False) for ex, info in exs]
+    ctx64 = [_ctx_for(api, p.info, lib.F64, rc) for p in pb64]
+    x64 = [api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=lib.F64) for _ in range(B)]
+    kw = dict(tol=TOL, rank_cap=rc)
+    api.tpcg_solve(pb64[0], ctx64[0], x64[0], **kw)     # warm-up (graphs captured)
+    torch.cuda.synchronize()
+    lat, sts = [], []
+    for _ in range(2):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        sts.append(api.tpcg_solve(pb64[0], ctx64[0], x64[0], **kw))
+        b.record(main)
+        torch.cuda.synchronize()
+        lat.append(a.elapsed_time(b))
+    out = {"single_solve_ms": float(np.median(lat)), "single_solves_per_s": 1000.0 / float(np.median(lat)),
+           "single_true_rel_res": float(sts[-1].true_rel_res), "single_iters": int(sts[-1].iters),
+           "single_status": int(sts[-1].status)}
+    x_single = x64[0].to_numpy()
+    if args.fp64_concurrent > 1:
+        streams = [None] * B
+        api.tpcg_solve_batch(pb64, ctx64, x64, streams, **kw)   # warm-up of every context
+        torch.cuda.synchronize()
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(main)
+        codes, bst = api.tpcg_solve_batch(pb64, ctx64, x64, streams, **kw)
+        b.record(main)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out.update({"concurrent": B, "batch_ms": ms, "batch_solves_per_s": B * 1000.0 / ms,
+                    "batch_status": [int(c) for c in codes],
+                    "batch_true_rel_res_max": float(max(s.true_rel_res for s in bst))})
+    return out, x_single, exs[0]
+
+
 def _make_problem(api, lib, dt, seed):
     return api.tpcg_setup(lib.GEOM_TWIST, synth.amp_from_seed(seed), DEGREE, N_DOF, dt)
 
@@ -259,7 +417,8 @@ def run_gpu(args):
     if args.torch_streams and B > 32:
         raise SystemExit("--torch-streams: torch's pool has 32 streams per priority; concurrent solves need their own")
     streams = [torch.cuda.Stream() for _ in range(B)] if args.torch_streams else [None] * B
-    lib.check(L.tpcg_set_option(1, args.gemm_ctas_per_sm), "tpcg_set_option")
+    lib.check(L.tpcg_set_option(lib.OPT_GEMM_CTAS_PER_SM, args.gemm_ctas_per_sm), "tpcg_set_option")
+    lib.check(L.tpcg_set_option(lib.OPT_EIG, args.eig), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     main = torch.cuda.current_stream()
 
@@ -324,7 +483,7 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
-                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm,
+                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig,
                       "refine_keep": args.refine_keep,
                       "seeds": f"{seeds[0]}..{seeds[-1]} on rank 0, disjoint ranges per rank (amp from seed)",
                       "tol": TOL, "rank_cap": rc,
@@ -341,11 +500,28 @@ def run_gpu(args):
            "kernel_ms_single": {k: round(v["ms"], 3) for k, v in prof.items()},
            "clocks": clk}
 
+    # the solution of seed SEED (problem 0) from the last timed step, against the oracle's stored solution
+    x_main = xs[0].to_numpy()
+    if rank == 0 and not args.no_fp64 and args.dtype != "f64":
+        fp64, x64, (ex0, info0) = fp64_arm(api, lib, pbs, rc, args, flush)
+        out["fp64"] = fp64
+    else:
+        ex0 = pbs[0].export()
+        info0, x64 = pbs[0].info, None
+    if rank == 0:
+        try:
+            ref = oracle_reference()
+            err = {args.dtype: solution_error(x_main, ex0, info0, ref)}
+            if x64 is not None:
+                err["f64"] = solution_error(x64, ex0, info0, ref)
+            out["error_vs_oracle"] = err
+        except Exception as e:   # the error report must not hide the GPU line
+            out["error_vs_oracle"] = {"error": str(e)[:200]}
     if rank == 0 and not args.no_e2e:
         out["e2e"] = e2e(api, lib, pbs, dt, ctxs, xs, streams, kw, args)
     if rank == 0 and not args.no_cpu and ws == 1:
         try:
-            out["cpu_baseline"] = oracle_sample(ORACLE_ITERS)
+            out["cpu_baseline"] = oracle_sample()
         except Exception as e:   # the baseline must not hide the GPU line
             out["cpu_baseline"] = {"value": None, "error": str(e)[:200]}
     if rank == 0:

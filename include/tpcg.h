@@ -115,6 +115,7 @@ typedef struct {
     double lambda_min;
 } tpcg_problem_arrays;
 
+/* Returns TPCG_E_INVALID, before any device work, for inconsistent sizes or a NaN/Inf in any table. */
 int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* out);
 
 typedef struct {
@@ -156,12 +157,16 @@ int tucker_residual(tpcg_problem pb, const tucker_t* x, tucker_t* y, void* strea
  * or, when a_dev / b_dev are non-NULL, device doubles read at execution time. */
 int tucker_axpby(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev,
                  const tucker_t* y, tucker_t* z, void* stream);
-/* *out_dev = <x, y> (Sec. 2.3 scalar product), both plain.  out_dev: device double. */
+/* *out_dev = <x, y> (Sec. 2.3 scalar product), both plain.  out_dev: device double.  Outside a stream capture
+ * the call reads both descriptors (synchronising the stream) and returns TPCG_E_INVALID for a block
+ * (unrounded) tensor or a rank above the context's rank_cap; inside a capture it cannot, and writes NaN for
+ * such inputs instead. */
 int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, void* stream);
 /* <x, y> exactly as tucker_dot, without a context and without allocating device memory (the paper has no
  * counterpart: this serves callers that may not allocate, e.g. code running under another party's stream
  * capture or inside allocator callbacks).  Its scratch is one fixed device array of about 4.3 MB inside the
- * library, sized for ranks <= 64: x->cap or y->cap above 64 returns TPCG_E_INVALID (nothing launched).
+ * library, sized for ranks <= 64: x->cap or y->cap above 64 returns TPCG_E_INVALID (nothing launched); block tensors are refused as in
+ * tucker_dot (outside a capture).
  * x, y: plain tensors of the same n and dtype (TPCG_F64 or TPCG_F32); out_dev: device double.
  * The first call on a device looks up the array's address (cudaGetSymbolAddress); make that call before
  * any stream capture that is to contain it.  All callers share the array: calls that overlap on the
@@ -207,6 +212,16 @@ typedef struct {
 
 void tpcg_params_default(tpcg_params* p);
 
+/* Per-iteration scalars of the last Alg. 5 run on context c (no counterpart in the paper; for inspection and
+ * tests).  Row k (k = 0 the state after the set-up steps of Alg. 5, k >= 1 after iteration k) holds
+ * TPCG_HIST_COLS doubles: ||r_k|| / ||f~||, omega_{k-1}, beta_{k-1}, xi_k = p_k . q_k, the dynamic-truncation
+ * tolerance eps_new after the Alg. 2 call of iteration k, the last update ratio v of that call, the number
+ * of Alg. 2 truncations in iteration k, and eta_k of eq. rel_tol_iterates.  Up to max_rows rows are copied
+ * to out (host, row-major); *rows receives the number recorded.  In the mixed form the inner FP32 solves
+ * run on the context's FP32 companion, so c records nothing for them. */
+#define TPCG_HIST_COLS 8
+int tpcg_ctx_history(tpcg_ctx c, double* out, int max_rows, int* rows);
+
 /* Alg. 5 with x_0 = 0: x receives the low-rank solution (plain, caller buffers with cap >= rank_cap and
  * core_cap >= rank_cap^3).  Synchronises the stream once per iteration for the stopping test.
  * Mixed form (problem and context created with TPCG_MIXED; x is FP64): iterative refinement around Alg. 5.
@@ -224,7 +239,7 @@ int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* x,
  * tpcg_solve(pbs[i], ctxs[i], &prms[i], &xs[i], &sts[i], streams[i]) on a host thread of its own, so the
  * solves' kernels overlap on the device.  Every solve needs its own context and its own stream; a NULL
  * entry runs that solve on a non-blocking stream owned by its context (created on first use).  Problems may be
- * shared (read-only during a solve, apart from a capacity-error flag).  statuses[i] receives each
+ * shared: a solve only reads its problem (its capacity-error flags live in its own context).  statuses[i] receives each
  * solve's status; the return value is TPCG_OK, else the first hard error, else TPCG_E_NOT_CONVERGED.
  * Results do not depend on what runs beside them (no shared scratch).  Turn profiling off first. */
 /* The non-blocking stream owned by a context (created on first use, destroyed with the context; no counterpart
@@ -280,6 +295,11 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   sinc-quadrature sums found by a search (R_P about twice Table 1's).  Problems set up earlier keep their
  *   sums. */
 #define TPCG_OPT_EXPSUM_BEST 2
+/*   TPCG_OPT_EIG: eigensolver of the FP32 mode Grams of ST-HOSVD (Alg. 1 step 3) up to 128 x 128: 1 (default) a
+ *   pivoted Cholesky G = L L^T followed by one-sided Jacobi on the columns of L, whose normalised columns are the
+ *   eigenvectors (the pivoted Cholesky of G = Z Z^T is the column-pivoted QR of Z^T, the preconditioner of
+ *   Drmac and Veselic's one-sided Jacobi SVD); 0 the two-sided cyclic Jacobi on G with accumulated rotations. */
+#define TPCG_OPT_EIG 3
 int tpcg_set_option(int key, long long value);
 
 /* Best exponential sum s_R(lambda) = sum_j omega_j exp(-alpha_j lambda) for 1/lambda on [1, M] in the maximum

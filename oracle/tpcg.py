@@ -50,7 +50,7 @@ def tpcg(terms, f, prec, prm: Params, record=None):
     while nr > prm.tol * nf and k < prm.max_it:
         omega = tucker.dot(r, p) / xi
         x_tilde = tucker.add(x, tucker.scale(p, omega))
-        x, eps, _ = rounding.t_dt(x, x_tilde, eps, prm.alpha, eps_min, prm.delta, prm.caps)
+        x, eps, trials = rounding.t_dt(x, x_tilde, eps, prm.alpha, eps_min, prm.delta, prm.caps)
         r = rounding.t_rel(tucker.add(f, tucker.scale(A(x), -1.0)), eta, prm.caps)
         nr = tucker.norm(r)
         eta = prm.beta_trunc * prm.tol * nf / nr
@@ -63,5 +63,5 @@ def tpcg(terms, f, prec, prm: Params, record=None):
         hist.append(nr / nf)
         if record is not None:
             record.append({"k": k, "omega": omega, "beta": beta_k, "xi": xi, "eps": eps, "eta": eta,
-                           "rank_x": tucker.ranks(x), "res": nr / nf})
+                           "rank_x": tucker.ranks(x), "res": nr / nf, "trials": trials})
     return x, {"iters": k, "res": nr / nf, "hist": hist}

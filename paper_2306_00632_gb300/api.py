@@ -356,6 +356,20 @@ def tpcg_solve(pb: Problem, ctx: Ctx, x: Tucker, stream=None, **kw):
     return st
 
 
+HIST_FIELDS = ("res", "omega", "beta", "xi", "eps", "v", "trials", "eta")
+
+
+def ctx_history(ctx: "Ctx", max_rows: int = 4096):
+    """tpcg_ctx_history: per-iteration scalars of the last Alg. 5 run on ctx, as a list of dicts (row 0 is the
+    state after the set-up steps, row k >= 1 the state after iteration k)."""
+    buf = np.zeros((max_rows, L.HIST_COLS))
+    rows = C.c_int(0)
+    check(L.load().tpcg_ctx_history(ctx.h, buf.ctypes.data_as(C.POINTER(C.c_double)), max_rows, C.byref(rows)),
+          "tpcg_ctx_history")
+    m = min(rows.value, max_rows)
+    return [dict(zip(HIST_FIELDS, buf[k])) for k in range(m)]
+
+
 def ctx_stream(ctx: "Ctx"):
     """The context's own CUDA stream as a torch stream (tpcg_ctx_stream): a stream no other solve shares."""
     h = C.c_void_p()

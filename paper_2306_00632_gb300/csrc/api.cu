@@ -1,5 +1,6 @@
 // C ABI entry points: contexts, problems, Tucker operations and the TPCG driver (Alg. 5).
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -410,6 +411,25 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
             set_error("tpcg_problem_create: invalid rhs");
             return TPCG_E_INVALID;
         }
+    {   // every table must be finite: a NaN or Inf is refused here, before anything reaches the device
+        const int bw = 2 * p + 1;
+        const int nnz = a->w_rowptr[n];
+        auto finite = [](const double* v, size_t cnt) {
+            for (size_t i = 0; i < cnt; ++i)
+                if (!std::isfinite(v[i])) return false;
+            return true;
+        };
+        bool ok = nnz >= 0 && (nnz == 0 || a->w_val) && std::isfinite(a->lambda_min) &&
+                  finite(a->w, a->R) && finite(a->bands, (size_t)a->R * 3 * bw * n) &&
+                  finite(a->f_core, (size_t)a->rf[0] * a->rf[1] * a->rf[2]) && finite(a->lam, n) &&
+                  finite(a->mu, a->n1) && finite(a->omega, a->RP) && finite(a->alpha, a->RP) &&
+                  (nnz == 0 || finite(a->w_val, nnz)) && (a->n2 == 0 || !a->v2u2 || finite(a->v2u2, (size_t)n * a->n2));
+        for (int t = 0; t < 3 && ok; ++t) ok = finite(a->f_U[t], (size_t)n * a->rf[t]);
+        if (!ok) {
+            set_error("tpcg_problem_create: a table holds a NaN or an Inf");
+            return TPCG_E_INVALID;
+        }
+    }
     tpcg_problem pb = new tpcg_problem_s();
     pb->lo = nullptr;
     memset(pb->d_f_store, 0, sizeof(pb->d_f_store));
@@ -644,10 +664,38 @@ extern "C" int tucker_axpby(double a, const double* a_dev, const tucker_t* x, do
     });
 }
 
+// Outside a stream capture, the public scalar products read both descriptors (16 bytes each, synchronising
+// the stream) and refuse a block tensor or a rank above the scratch limit with TPCG_E_INVALID.  Inside a
+// capture nothing can be read back: the kernels then write NaN for such inputs.
+static int check_dot_inputs(const tucker_t* x, const tucker_t* y, int max_rank, cudaStream_t st, const char* what) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    TPCG_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return TPCG_OK;
+    int h[2][4];
+    TPCG_CUDA(cudaMemcpyAsync(h[0], x->desc, sizeof(h[0]), cudaMemcpyDeviceToHost, st));
+    TPCG_CUDA(cudaMemcpyAsync(h[1], y->desc, sizeof(h[1]), cudaMemcpyDeviceToHost, st));
+    TPCG_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < 2; ++q) {
+        if (h[q][0] != 1) {
+            set_error(std::string(what) + ": " + (q ? "y" : "x") + " is not a plain tensor (" + std::to_string(h[q][0]) +
+                      " core blocks); round it first");
+            return TPCG_E_INVALID;
+        }
+        for (int t = 0; t < 3; ++t)
+            if (h[q][1 + t] > max_rank) {
+                set_error(std::string(what) + ": rank " + std::to_string(h[q][1 + t]) + " exceeds the limit " +
+                          std::to_string(max_rank));
+                return TPCG_E_INVALID;
+            }
+    }
+    return TPCG_OK;
+}
+
 extern "C" int tucker_dot(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev, void* stream) {
     if (!c || !out_dev) return TPCG_E_INVALID;
     TPCG_TRY(check_tensor(x, c->n, c->dtype, "tucker_dot x"));
     TPCG_TRY(check_tensor(y, c->n, c->dtype, "tucker_dot y"));
+    TPCG_TRY(check_dot_inputs(x, y, c->rank_cap, S(stream), "tucker_dot"));
     return by_dtype(c->dtype, [&](auto z) { return dot_impl<decltype(z)>(c, x, y, out_dev, S(stream)); });
 }
 
@@ -668,6 +716,7 @@ extern "C" int tucker_dot_static(const tucker_t* x, const tucker_t* y, double* o
                   " exceeds the fixed scratch limit of rank " + std::to_string(mr));
         return TPCG_E_INVALID;
     }
+    TPCG_TRY(check_dot_inputs(x, y, mr, S(stream), "tucker_dot_static"));
     return by_dtype(x->dtype, [&](auto z) { return dot_static_impl<decltype(z)>(x, y, out_dev, S(stream)); });
 }
 
@@ -761,7 +810,7 @@ int tpcg::fetch(tpcg_ctx c, cudaStream_t s, const D2H* items, int count) {
 // ||f - A x|| / ||f|| of a solution x, in the working precision of the problem (no truncation)
 template <typename T>
 static int true_residual(tpcg_problem pb, tpcg_ctx c, const tucker_t* x, tucker_t* work, double* rel, cudaStream_t s) {
-    TPCG_TRY(apply_impl<T>(pb, x, work, true, s));
+    TPCG_TRY(apply_impl<T>(pb, x, work, true, s, nullptr, reinterpret_cast<int*>(c->scal + 232)));
     double* d = c->scal + 130;
     TPCG_TRY(tensor_norm2<T>(c, work, d, s));
     double h = 0.0;
@@ -781,8 +830,9 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     double* dprm = c->scal + 100;
     double hp[P_COUNT] = {prm->tol, prm->eps0, prm->eps_min, prm->alpha, prm->delta, prm->beta_trunc};
     TPCG_CUDA(cudaMemcpyAsync(dprm, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
-    // capacity flags of the operator apply (problem) and of the preconditioner (context), read every iteration
-    int* apply_err = reinterpret_cast<int*>(pb->d_scal + 60);
+    // capacity flags of the operator apply and of the preconditioner, read every iteration.  Both live in this
+    // context: solves that share the problem never clear or raise each other's flags
+    int* apply_err = reinterpret_cast<int*>(sc + 232);
     int* fd_err = reinterpret_cast<int*>(sc + 230);
     TPCG_CUDA(cudaMemsetAsync(apply_err, 0, sizeof(int), s));
     TPCG_CUDA(cudaMemsetAsync(fd_err, 0, sizeof(int), s));
@@ -809,7 +859,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     TPCG_TRY(fd_impl<T>(pb, c, r, big, s));
     TPCG_TRY(round_to(z, eta));
     TPCG_TRY(copy_tensor_impl<T>(z, p, c->n, c->max_cols, s));
-    TPCG_TRY(apply_impl<T>(pb, p, big, false, s));
+    TPCG_TRY(apply_impl<T>(pb, p, big, false, s, nullptr, apply_err));
     TPCG_TRY(round_to(q, eta));
     TPCG_TRY(dot_cached<T>(c, p, q, sc + S_XI, s));
     launch_scalar(OP_XI, sc, dprm, s);
@@ -819,10 +869,20 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     int trials_total = 0;
     const char* tr = getenv("TPCG_TRACE");
     const bool trace = tr && tr[0] == '1';
+    c->hist.clear();
+    int trials_prev = 0;
     for (;;) {
         int flags[2] = {0, 0};
         TPCG_TRY(fetch(c, s, {{host, sc, sizeof(host)}, {&flags[0], apply_err, sizeof(int)},
                               {&flags[1], fd_err, sizeof(int)}}));
+        {   // the scalars after iteration k (the row of k = 0 holds the initial state)
+            const double nf = host[S_NF] > 0 ? host[S_NF] : 1.0;
+            const double row[TPCG_HIST_COLS] = {host[S_NR] / nf, k ? host[S_OMEGA] : 0.0, k ? host[S_BETA] : 0.0,
+                                                host[S_XI], host[S_EPS], k ? host[S_V] : 1.0,
+                                                (double)(trials_total - trials_prev), host[S_ETA]};
+            c->hist.insert(c->hist.end(), row, row + TPCG_HIST_COLS);
+            trials_prev = trials_total;
+        }
         if (flags[0] || flags[1]) {
             set_error(std::string("tpcg_solve: an unrounded ") + (flags[0] ? "operator product" : "preconditioner output") +
                       " exceeded the context's max_cols or the block limit");
@@ -865,7 +925,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         }
         std::swap(x, big2);
         // r_{k+1} = T(f - A x_{k+1}, eta_k); eta_{k+1}
-        TPCG_TRY(apply_impl<T>(pb, x, big, true, s, rhs));
+        TPCG_TRY(apply_impl<T>(pb, x, big, true, s, rhs, apply_err));
         TPCG_TRY(round_to(r, eta));
         TPCG_TRY(dot_cached<T>(c, r, r, sc + S_RR, s));
         launch_scalar(OP_RES, sc, dprm, s);
@@ -878,7 +938,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         TPCG_TRY(axpby_impl<T>(1.0, nullptr, z, 0.0, sc + S_BETA, p, big, nullptr, s));
         TPCG_TRY(round_to(p, eta));
         // q_{k+1} = T(A p_{k+1}, eta_{k+1});  xi_{k+1} = p_{k+1} . q_{k+1}
-        TPCG_TRY(apply_impl<T>(pb, p, big, false, s));
+        TPCG_TRY(apply_impl<T>(pb, p, big, false, s, nullptr, apply_err));
         TPCG_TRY(round_to(q, eta));
         TPCG_TRY(dot_cached<T>(c, p, q, sc + S_XI, s));
         launch_scalar(OP_XI, sc, dprm, s);
@@ -940,6 +1000,8 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
     double* dd = c->scal + 140;
     double* xx = c->scal + 141;
     double* xeps = c->scal + 142;
+    int* apply_err = reinterpret_cast<int*>(c->scal + 232);   // capacity flag of the FP64 residual (this context)
+    TPCG_CUDA(cudaMemsetAsync(apply_err, 0, sizeof(int), s));
     const char* tr = getenv("TPCG_TRACE");
     const bool trace = tr && tr[0] == '1';
     TPCG_TRY(set_zero(xacc, s));
@@ -950,10 +1012,16 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
     double rel = 1.0;
     for (outer = 0; outer <= max_outer; ++outer) {
         // r = f - A x in FP64 (exact ||r|| from Z), truncated to 0.1 inner_tol (relative) or abs_tol in FP32
-        TPCG_TRY(apply_impl<double>(pb, xacc, big, true, s));
+        TPCG_TRY(apply_impl<double>(pb, xacc, big, true, s, nullptr, apply_err));
         TPCG_TRY(round_mixed(c, c32, big, r32, 0.1 * prm->inner_tol, nullptr, rc, abs_tol, info, s));
         double h[6];
-        TPCG_TRY(fetch(c, s, {{h, info, sizeof(h)}}));
+        int over = 0;
+        TPCG_TRY(fetch(c, s, {{h, info, sizeof(h)}, {&over, apply_err, sizeof(int)}}));
+        if (over) {
+            set_error("tpcg_solve: the FP64 residual exceeded the context's max_cols or the block limit");
+            status = TPCG_E_INVALID;
+            break;
+        }
         rel = nf > 0 ? sqrt(std::max(h[0], 0.0)) / nf : 0.0;
         if (trace) fprintf(stderr, "mixed outer=%d true_res=%.3e r-rank=(%g,%g,%g)\n", outer, rel, h[2], h[3], h[4]);
         if (!(rel == rel)) { status = TPCG_E_BREAKDOWN; break; }
@@ -1035,6 +1103,18 @@ extern "C" int tpcg_solve(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, t
     }
     if (pb->lo) return solve_mixed(pb, c, prm, x, st, S(stream));
     return by_dtype(pb->dtype, [&](auto z) { return solve_impl<decltype(z)>(pb, c, prm, x, st, S(stream)); });
+}
+
+extern "C" int tpcg_ctx_history(tpcg_ctx c, double* out, int max_rows, int* rows) {
+    if (!c || !rows || max_rows < 0 || (max_rows > 0 && !out)) {
+        set_error("tpcg_ctx_history: invalid arguments");
+        return TPCG_E_INVALID;
+    }
+    const int have = (int)(c->hist.size() / TPCG_HIST_COLS);
+    *rows = have;
+    const int m = std::min(have, max_rows);
+    if (m > 0) memcpy(out, c->hist.data(), (size_t)m * TPCG_HIST_COLS * sizeof(double));
+    return TPCG_OK;
 }
 
 // Many independent solves at once: one host thread per solve, each on its own stream and context, so

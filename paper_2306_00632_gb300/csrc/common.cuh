@@ -160,6 +160,8 @@ struct tpcg_ctx_s {
         long long nkern;
     };
     std::vector<RoundGraph> rgraphs;
+    // per-iteration scalars of the last Alg. 5 run on this context (TPCG_HIST_COLS doubles per iteration)
+    std::vector<double> hist;
 };
 
 struct tpcg_problem_s {

@@ -25,6 +25,10 @@
 
 namespace tpcg {
 
+// key of the decreasing rank-counting sorts: a NaN eigenvalue sorts last, so that the ranks of any input
+// (including NaN data) form a permutation and every index written through them stays in range
+__device__ __forceinline__ double sort_key(double v) { return v == v ? v : -INFINITY; }
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -43,14 +47,22 @@ constexpr int EIG_THREADS = 1024;
 // parity level (1e-12) and the FP32 ones well inside FP32 truncation accuracy (3e-5)
 template <typename T>
 __host__ __device__ constexpr double jacobi_tau() { return sizeof(T) == 8 ? 1e-12 : 3e-5; }
+// one-sided Jacobi (FP32): a pair is orthogonal once |a_p . a_q| <= HJ_TAU |a_p| |a_q|.  The normalised columns
+// are then eigenvectors orthonormal to about HJ_TAU; the FP32 dot product itself resolves about 4e-7 at 128 rows.
+constexpr float HJ_TAU = 2e-6f;
 
 template <typename T>
 __device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double trace, int m) {
     int s = M;
     if (sizeof(T) == 8) {
+        // each eigenvalue of an FP64 Gram is known only to about eps trace (the Gram squares the singular
+        // values, so sigma_i below sqrt(eps) sigma_max is unresolved): a direction is discarded only if its
+        // clamped eigenvalue plus that uncertainty still fits the budget.  With a budget below the noise level
+        // the truncation is then lossless instead of dropping directions whose energy it cannot see.
+        const double unc = 4.0 * 2.220446049250313e-16 * trace;
         double tail = 0.0;
         for (int i = M - 1; i >= 0; --i) {
-            const double li = lam[i] > 0.0 ? lam[i] : 0.0;
+            const double li = (lam[i] > 0.0 ? lam[i] : 0.0) + unc;
             if (tail + li <= p.budget) { tail += li; s = i; } else break;
         }
     } else {
@@ -256,10 +268,10 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
     }
     // eigenvalues sorted decreasingly (rank counting)
     for (int i = tid; i < M; i += nt) {
-        const double li = (double)A[i + (long long)i * ld];
+        const double li = sort_key((double)A[i + (long long)i * ld]);
         int rk = 0;
         for (int j = 0; j < M; ++j) {
-            const double lj = (double)A[j + (long long)j * ld];
+            const double lj = sort_key((double)A[j + (long long)j * ld]);
             if (lj > li || (lj == li && j < i)) ++rk;
         }
         ord[rk] = (short)i;
@@ -533,10 +545,10 @@ __global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
     if (crank == 0) {
         // decreasing order by rank counting (ties by index), then the truncation rule
         for (int i = tid; i < M; i += nt) {
-            const double li = lam_all[i];
+            const double li = sort_key(lam_all[i]);
             int rk = 0;
             for (int j = 0; j < M; ++j) {
-                const double lj = lam_all[j];
+                const double lj = sort_key(lam_all[j]);
                 if (lj > li || (lj == li && j < i)) ++rk;
             }
             lam[rk] = li;
@@ -797,10 +809,10 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
     }
     // eigenvalues sorted decreasingly (rank counting)
     for (int i = tid; i < M; i += nt) {
-        const double li = (double)A[i + i * ld];
+        const double li = sort_key((double)A[i + i * ld]);
         int rk = 0;
         for (int j = 0; j < M; ++j) {
-            const double lj = (double)A[j + j * ld];
+            const double lj = sort_key((double)A[j + j * ld]);
             if (lj > li || (lj == li && j < i)) ++rk;
         }
         ord[rk] = (short)i;
@@ -824,6 +836,295 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
         for (int i = tid; i < M; i += nt) S[i + (long long)c * n] = V[i + ord[c] * ldv];
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// FP32 Grams up to HJ_MAXM: pivoted Cholesky, then one-sided (Hestenes) Jacobi on the Cholesky factor.
+//
+//  1. G = sum_k l_k l_k^T by the outer-product Cholesky with diagonal pivoting (pivots chosen by index, no
+//     row swaps, so L = [l_1 .. l_rc] satisfies G = L L^T in G's own index order); it stops once every
+//     remaining diagonal entry is below 1e-9 trace(G), the remainder being counted as discarded energy by
+//     the truncation rule (trace minus kept eigenvalues).  The pivoted Cholesky of G = Z Z^T is the
+//     column-pivoted QR of Z^T (L = R^T up to the row order), the preconditioning step of Drmac and
+//     Veselic's one-sided Jacobi SVD, after which few sweeps are needed.
+//  2. One-sided Jacobi makes the columns of L mutually orthogonal by plane rotations from the right:
+//     L J = U Sigma, so the normalised columns are eigenvectors of G and their squared norms its
+//     eigenvalues; no rotation matrix is accumulated.  Pair (a_p, a_q) with alpha = |a_p|^2, beta = |a_q|^2,
+//     gamma = a_p . a_q rotates when |gamma| > tau sqrt(alpha beta): zeta = (beta - alpha) / (2 gamma),
+//     t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), a_p <- c a_p - s a_q, a_q <- s a_p + c a_q, and the
+//     norms follow as alpha - t gamma, beta + t gamma (recomputed exactly at every sweep start).
+//  3. The 128 columns are the players of a round-robin tournament (circle method, one fixed player): 64 pair
+//     slots, four per warp, every lane holding four rows of each of its warp's eight columns in registers.
+//     A step computes the four pair products of a warp with one packed butterfly (each lane ends with the
+//     full gamma of one slot), rotates in registers, then moves every column but the fixed one to the next
+//     position of the ring: inside a warp this is a register move, and only the two columns at a warp's
+//     ends cross to the neighbouring warps, through double-buffered shared memory (one barrier per step).
+// ------------------------------------------------------------------------------------------------------------
+constexpr int HJ_WARPS = 16;
+constexpr int HJ_THREADS = 32 * HJ_WARPS;
+constexpr int HJ_SLOTS = 4;                                  // pair slots per warp
+constexpr int HJ_PLAYERS = 2 * HJ_SLOTS * HJ_WARPS;          // columns in the ring (128)
+constexpr int HJ_MAXM = 128;                                 // rows: four per lane
+constexpr int HJ_LDA = HJ_MAXM + 1;
+static_assert(HJ_PLAYERS == HJ_MAXM && (HJ_MAXM * HJ_LDA) % 4 == 0, "ring and row layout");
+
+static inline size_t hj_smem_bytes() {
+    return ((size_t)HJ_MAXM * HJ_LDA + (size_t)HJ_MAXM * HJ_MAXM + (size_t)2 * 2 * HJ_WARPS * HJ_MAXM) * sizeof(float);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* plan, const float* __restrict__ G,
+                                                                  float* __restrict__ S, double* evals, int m,
+                                                                  int max_sweeps, float tau, double* prof) {
+    RoundPlan& p = *plan;
+    const int M = p.gM;
+    const int n = p.n;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char hj_smem[];
+    float* A = reinterpret_cast<float*>(hj_smem);            // Cholesky working matrix, ld HJ_LDA
+    float* L = A + HJ_MAXM * HJ_LDA;                         // factor columns, ld HJ_MAXM
+    float* X = L + HJ_MAXM * HJ_MAXM;                        // ring exchange [buffer][direction][warp][row]
+    __shared__ float dg[HJ_MAXM];
+    __shared__ float wbest[HJ_WARPS];
+    __shared__ int wbi[HJ_WARPS];
+    __shared__ float xa[2][2][HJ_WARPS];
+    __shared__ double lam[HJ_PLAYERS];                        // squared column norms, by column
+    __shared__ double lsort[HJ_PLAYERS];                      // the same, decreasing
+    __shared__ short ord[HJ_PLAYERS];
+    __shared__ int s_keep;
+    __shared__ double s_tr;
+    if (M <= 0) {
+        if (tid == 0) {
+            p.s[m] = 0;
+            if (m == 0) { p.norm2 = 0; p.budget = 0; }
+        }
+        return;
+    }
+    for (int j = warp; j < M; j += HJ_WARPS)
+        for (int i = lane; i < M; i += 32) A[i + j * HJ_LDA] = G[i + (long long)j * M];
+    for (int e = tid; e < HJ_MAXM * HJ_MAXM / 4; e += HJ_THREADS)
+        reinterpret_cast<float4*>(L)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < HJ_MAXM; i += HJ_THREADS) dg[i] = (i < M) ? G[i + (long long)i * M] : -1.f;
+    if (tid == 0) {
+        double t = 0.0;
+        for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
+        s_tr = t;
+        if (m == 0) {
+            p.norm2 = t;
+            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+        }
+    }
+    __syncthreads();
+    const float tr = (float)s_tr;
+    // ---- 1. pivoted Cholesky, G = sum_k l_k l_k^T
+    const float thr = 1e-9f * tr;
+    for (int k = 0; k < M; ++k) {
+        {   // the largest remaining diagonal entry (ties: the lowest index): 8 entries per warp, then 16 warps
+            const int i = warp * 8 + (lane & 7);
+            float v = lane < 8 ? dg[i] : -2.f;
+            int bi = i;
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(FULL, v, o);
+                const int b2 = __shfl_xor_sync(FULL, bi, o);
+                if (v2 > v || (v2 == v && b2 < bi)) { v = v2; bi = b2; }
+            }
+            if (lane == 0) { wbest[warp] = v; wbi[warp] = bi; }
+        }
+        __syncthreads();
+        float dmax = -2.f;
+        int piv = 0;
+        for (int w = 0; w < HJ_WARPS; ++w)
+            if (wbest[w] > dmax) { dmax = wbest[w]; piv = wbi[w]; }
+        if (!(dmax > thr)) break;   // the same decision in every thread (a NaN stops the factorisation)
+        const float r = sqrtf(dmax);
+        if (tid < M) L[tid + k * HJ_MAXM] = (tid == piv) ? r : A[tid + piv * HJ_LDA] / r;
+        __syncthreads();
+        const float* lk = L + k * HJ_MAXM;
+        for (int j = warp; j < M; j += HJ_WARPS) {
+            const float lj = lk[j];
+            for (int i = lane; i < M; i += 32) {
+                const float a = (i == piv || j == piv) ? 0.f : fmaf(-lk[i], lj, A[i + j * HJ_LDA]);
+                A[i + j * HJ_LDA] = a;
+                if (i == j) dg[i] = (i == piv) ? -1.f : a;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- 2. one-sided Jacobi on the columns of L: slot k of warp w (k = 4 w + j) starts with columns k and 64 + k
+    constexpr int H = HJ_PLAYERS / 2;
+    float T[HJ_SLOTS][4], B[HJ_SLOTS][4], aT[HJ_SLOTS], aB[HJ_SLOTS];
+#pragma unroll
+    for (int j = 0; j < HJ_SLOTS; ++j) {
+        const int k = HJ_SLOTS * warp + j;
+        const float4 t = ld4(L + k * HJ_MAXM + 4 * lane), b = ld4(L + (H + k) * HJ_MAXM + 4 * lane);
+        T[j][0] = t.x; T[j][1] = t.y; T[j][2] = t.z; T[j][3] = t.w;
+        B[j][0] = b.x; B[j][1] = b.y; B[j][2] = b.z; B[j][3] = b.w;
+    }
+    const int pj = (lane >> 3) & 3;         // the slot whose rotation this lane computes
+    const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
+    const float floor_g = 1e-12f * tr;      // products below this are rounding noise of the factor
+    int nsweeps = 0, buf = 0;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        ++nsweeps;
+#pragma unroll
+        for (int j = 0; j < HJ_SLOTS; ++j) {   // exact squared norms
+            float st = 0.f, sb = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { st = fmaf(T[j][q], T[j][q], st); sb = fmaf(B[j][q], B[j][q], sb); }
+            aT[j] = warp_sum(st);
+            aB[j] = warp_sum(sb);
+        }
+        int rot = 0;
+        for (int step = 0; step < HJ_PLAYERS - 1; ++step) {
+            float g[HJ_SLOTS];
+#pragma unroll
+            for (int j = 0; j < HJ_SLOTS; ++j) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc = fmaf(T[j][q], B[j][q], acc);
+                g[j] = acc;
+            }
+            // packed butterfly: after it, every lane holds the full product of slot pj
+            const float x0 = __shfl_xor_sync(FULL, b4 ? g[0] : g[2], 16);
+            const float x1 = __shfl_xor_sync(FULL, b4 ? g[1] : g[3], 16);
+            const float u0 = (b4 ? g[2] : g[0]) + x0;
+            const float u1 = (b4 ? g[3] : g[1]) + x1;
+            const float y = __shfl_xor_sync(FULL, b3 ? u0 : u1, 8);
+            float gm = (b3 ? u1 : u0) + y;
+            gm += __shfl_xor_sync(FULL, gm, 4);
+            gm += __shfl_xor_sync(FULL, gm, 2);
+            gm += __shfl_xor_sync(FULL, gm, 1);
+            const float al = pj == 0 ? aT[0] : pj == 1 ? aT[1] : pj == 2 ? aT[2] : aT[3];
+            const float be = pj == 0 ? aB[0] : pj == 1 ? aB[1] : pj == 2 ? aB[2] : aB[3];
+            float c = 1.f, s = 0.f, tg = 0.f;
+            if (fabsf(gm) > tau * sqrtf(al) * sqrtf(be) && fabsf(gm) > floor_g) {
+                const float zeta = (be - al) / (2.f * gm);
+                const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+                c = 1.f / sqrtf(fmaf(t, t, 1.f));
+                s = c * t;
+                tg = t * gm;
+                rot = 1;
+            }
+#pragma unroll
+            for (int j = 0; j < HJ_SLOTS; ++j) {
+                const float cj = __shfl_sync(FULL, c, 8 * j), sj = __shfl_sync(FULL, s, 8 * j);
+                const float tgj = __shfl_sync(FULL, tg, 8 * j);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float tp = T[j][q], bq = B[j][q];
+                    T[j][q] = fmaf(cj, tp, -sj * bq);
+                    B[j][q] = fmaf(sj, tp, cj * bq);
+                }
+                aT[j] -= tgj;
+                aB[j] += tgj;
+            }
+            // ring move: top[k] -> top[k+1] (top[0] fixed), top[63] -> bottom[63], bottom[k] -> bottom[k-1],
+            // bottom[0] -> top[1]; the two columns at a warp's ends go through shared memory
+            float* xt = X + ((buf * 2 + 0) * HJ_WARPS) * HJ_MAXM;
+            float* xb = X + ((buf * 2 + 1) * HJ_WARPS) * HJ_MAXM;
+            if (warp < HJ_WARPS - 1) {
+                st4(xt + warp * HJ_MAXM + 4 * lane, T[HJ_SLOTS - 1]);
+                if (lane == 0) xa[buf][0][warp] = aT[HJ_SLOTS - 1];
+            }
+            if (warp > 0) {
+                st4(xb + warp * HJ_MAXM + 4 * lane, B[0]);
+                if (lane == 0) xa[buf][1][warp] = aB[0];
+            }
+            __syncthreads();
+            float oB0[4], oT3[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { oB0[q] = B[0][q]; oT3[q] = T[HJ_SLOTS - 1][q]; }
+            const float oaB0 = aB[0], oaT3 = aT[HJ_SLOTS - 1];
+#pragma unroll
+            for (int j = 0; j < HJ_SLOTS - 1; ++j) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) B[j][q] = B[j + 1][q];
+                aB[j] = aB[j + 1];
+            }
+            if (warp == HJ_WARPS - 1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) B[HJ_SLOTS - 1][q] = oT3[q];
+                aB[HJ_SLOTS - 1] = oaT3;
+            } else {
+                const float4 v = ld4(xb + (warp + 1) * HJ_MAXM + 4 * lane);
+                B[HJ_SLOTS - 1][0] = v.x; B[HJ_SLOTS - 1][1] = v.y; B[HJ_SLOTS - 1][2] = v.z; B[HJ_SLOTS - 1][3] = v.w;
+                aB[HJ_SLOTS - 1] = xa[buf][1][warp + 1];
+            }
+#pragma unroll
+            for (int j = HJ_SLOTS - 1; j >= 2; --j) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) T[j][q] = T[j - 1][q];
+                aT[j] = aT[j - 1];
+            }
+            if (warp == 0) {   // top[0] stays; bottom[0] enters the top row at slot 1
+#pragma unroll
+                for (int q = 0; q < 4; ++q) T[1][q] = oB0[q];
+                aT[1] = oaB0;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) T[1][q] = T[0][q];
+                aT[1] = aT[0];
+                const float4 v = ld4(xt + (warp - 1) * HJ_MAXM + 4 * lane);
+                T[0][0] = v.x; T[0][1] = v.y; T[0][2] = v.z; T[0][3] = v.w;
+                aT[0] = xa[buf][0][warp - 1];
+            }
+            buf ^= 1;
+        }
+        if (!__syncthreads_or(rot)) break;
+    }
+    // ---- 3. eigenvalues (exact squared norms), decreasing order, truncation rule, normalised kept columns
+    __syncthreads();
+    float* C = A;   // the columns, ld HJ_MAXM (the Cholesky matrix is no longer needed)
+#pragma unroll
+    for (int j = 0; j < HJ_SLOTS; ++j) {
+        const int k = HJ_SLOTS * warp + j;
+        st4(C + k * HJ_MAXM + 4 * lane, T[j]);
+        st4(C + (H + k) * HJ_MAXM + 4 * lane, B[j]);
+        float st = 0.f, sb = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { st = fmaf(T[j][q], T[j][q], st); sb = fmaf(B[j][q], B[j][q], sb); }
+        st = warp_sum(st);
+        sb = warp_sum(sb);
+        if (lane == 0) { lam[k] = (double)st; lam[H + k] = (double)sb; }
+    }
+    __syncthreads();
+    for (int i = tid; i < HJ_PLAYERS; i += HJ_THREADS) {
+        const double li = sort_key(lam[i]);
+        int rk = 0;
+        for (int j = 0; j < HJ_PLAYERS; ++j) {
+            const double lj = sort_key(lam[j]);
+            if (lj > li || (lj == li && j < i)) ++rk;
+        }
+        ord[rk] = (short)i;
+        lsort[rk] = lam[i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int s = truncation_rule<float>(p, lsort, M, s_tr, m);
+        while (s > 0 && !(lsort[s - 1] > 0.0)) --s;   // a zero column is never kept (its energy is already
+        p.s[m] = s;                                   // counted as discarded)
+        s_keep = s;
+        for (int i = 0; i < M; ++i) evals[i] = lsort[i];
+        if (prof) {
+            prof[2 * PK_EIG] += 9.0 * (double)M * M * M;
+            prof[2 * PK_EIG + 1] += (double)sizeof(float) * ((double)M * M + (double)M * s);
+            prof[2 * PK_SWEEPS] += nsweeps;
+            prof[2 * PK_SWEEPS + 1] += 1.0;
+        }
+    }
+    __syncthreads();
+    const int s = s_keep;
+    for (int c = warp; c < s; c += HJ_WARPS) {
+        const int col = ord[c];
+        const float inv = (float)(1.0 / sqrt(lam[col]));
+        for (int i = lane; i < M; i += 32) S[i + (long long)c * n] = C[i + col * HJ_MAXM] * inv;
+    }
+}
+
 // shared-memory layout: A (M (M+1)) and V (M (M+1)) when both fit, else A only, else neither
 static size_t jacobi_smem_plan(int n, size_t elt, int* a_smem, int* v_smem) {
     const size_t limit = 190 * 1024;   // leaves room for the ~20 KB of static shared memory
@@ -845,6 +1146,13 @@ int launch_eig(RoundPlan* plan, const T* G, EigWork& w, T* S, double* evals, int
         return TPCG_OK;
     }
     if constexpr (sizeof(T) == 4) {
+        if (n <= HJ_MAXM && eig_kind() == 1) {   // FP32 Grams up to 128: pivoted Cholesky + one-sided Jacobi
+            TPCG_TRY(smem_optin(reinterpret_cast<const void*>(hestenes_eig_kernel), 7, (int)hj_smem_bytes()));
+            hestenes_eig_kernel<<<1, HJ_THREADS, hj_smem_bytes(), st>>>(plan, G, S, evals, m, 30, HJ_TAU,
+                                                                        prof_dev());
+            TPCG_CHECK_LAUNCH();
+            return TPCG_OK;
+        }
         if (n <= JV_MAXM) {   // FP32 Grams up to 128: packed rotations, vectorised V update
             TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_v_kernel), 6, 190 * 1024));
             jacobi_eig_v_kernel<<<1, EIG_THREADS, jv_smem_bytes(n), st>>>(plan, G, S, evals, m, 20, prof_dev());
@@ -878,6 +1186,7 @@ int eig_prepare() {
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<double, true>), 4, 190 * 1024));
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_kernel<float, true>), 5, 190 * 1024));
     TPCG_TRY(smem_optin(reinterpret_cast<const void*>(jacobi_eig_v_kernel), 6, 190 * 1024));
+    TPCG_TRY(smem_optin(reinterpret_cast<const void*>(hestenes_eig_kernel), 7, (int)hj_smem_bytes()));
     return TPCG_OK;
 }
 

@@ -16,6 +16,8 @@ struct EigWork {
 };
 
 size_t eig_work_bytes(int n);
+// eigensolver of FP32 Grams up to 128 (TPCG_OPT_EIG): 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi
+int eig_kind();
 // shared-memory opt-ins of the eigensolver kernels on the current device (before any stream capture)
 int eig_prepare();
 int eig_work_alloc(EigWork* w, int n, std::vector<void*>* owned);

@@ -42,10 +42,12 @@ static int elast_check_block(tpcg_elast e, const tucker_t* x, const char* what) 
     return TPCG_OK;
 }
 
-// y_i = (f_i if residual) -/+ sum_j A_ij x_j for i = 0, 1, 2 (unrounded; x_j may be block tensors)
+// y_i = (f_i if residual) -/+ sum_j A_ij x_j for i = 0, 1, 2 (unrounded; x_j may be block tensors).
+// err: nine device ints, block (i, j) sets err[3 i + j] when its product does not fit y_i; the solver passes
+// flags of its own context (null: the blocks' problem flags, for standalone calls)
 template <typename T>
 static int elast_apply_impl(tpcg_elast e, tucker_t* const* x, tucker_t* const* y, bool residual, int cap,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* err = nullptr) {
     for (int i = 0; i < 3; ++i) {
         if (residual)
             TPCG_TRY(copy_tensor_impl<T>(&e->blk[4 * i]->f, y[i], e->n, cap, st));
@@ -53,7 +55,9 @@ static int elast_apply_impl(tpcg_elast e, tucker_t* const* x, tucker_t* const* y
             set_empty_kernel<<<1, 1, 0, st>>>(static_cast<TuckerDesc*>(y[i]->desc));
             TPCG_CHECK_LAUNCH();
         }
-        for (int j = 0; j < 3; ++j) TPCG_TRY(apply_append_impl<T>(e->blk[3 * i + j], x[j], y[i], residual ? -1.0 : 1.0, st));
+        for (int j = 0; j < 3; ++j)
+            TPCG_TRY(apply_append_impl<T>(e->blk[3 * i + j], x[j], y[i], residual ? -1.0 : 1.0, st,
+                                          err ? err + 3 * i + j : nullptr));
     }
     return TPCG_OK;
 }
@@ -119,10 +123,12 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
         return TPCG_OK;
     };
     double* eta = sc + S_ETA;
-    // capacity flags of the nine block products and of the preconditioner, read every iteration
+    // capacity flags of the nine block products and of the preconditioner, read every iteration; they live in
+    // this context, so solves that share the elasticity object never see each other's flags
     int* fd_err = reinterpret_cast<int*>(sc + 230);
+    int* apply_err = reinterpret_cast<int*>(sc + 240);   // 9 ints
     TPCG_CUDA(cudaMemsetAsync(fd_err, 0, sizeof(int), s));
-    for (int q9 = 0; q9 < 9; ++q9) TPCG_CUDA(cudaMemsetAsync(e->blk[q9]->d_scal + 60, 0, sizeof(int), s));
+    TPCG_CUDA(cudaMemsetAsync(apply_err, 0, 9 * sizeof(int), s));
     // x_0 = 0, r_0 = f
     for (int i = 0; i < 3; ++i) TPCG_TRY(set_zero(x[i], s));
     for (int i = 0; i < 3; ++i) TPCG_TRY(copy_tensor_impl<T>(&e->blk[4 * i]->f, r[i], n, cap, s));
@@ -133,7 +139,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
     TPCG_TRY(bround(big, eta));
     bswap(z, big);
     TPCG_TRY(bcopy(z, p));
-    TPCG_TRY(elast_apply_impl<T>(e, p, big, false, cap, s));
+    TPCG_TRY(elast_apply_impl<T>(e, p, big, false, cap, s, apply_err));
     TPCG_TRY(bround(big, eta));
     bswap(q, big);
     TPCG_TRY(elast_dot_impl<T>(c, p, q, sc + S_XI, s));
@@ -143,7 +149,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
     for (;;) {
         int flags[10] = {0};
         D2H rd[11] = {{host, sc, sizeof(host)}, {&flags[9], fd_err, sizeof(int)}};
-        for (int q9 = 0; q9 < 9; ++q9) rd[2 + q9] = {&flags[q9], e->blk[q9]->d_scal + 60, sizeof(int)};
+        for (int q9 = 0; q9 < 9; ++q9) rd[2 + q9] = {&flags[q9], apply_err + q9, sizeof(int)};
         TPCG_TRY(fetch(c, s, rd, 11));
         bool over = false;
         for (int q9 = 0; q9 < 10; ++q9) over = over || flags[q9] != 0;
@@ -173,7 +179,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
         }
         bswap(x, big2);
         // r_{k+1} = T(f - A x_{k+1}, eta_k)
-        TPCG_TRY(elast_apply_impl<T>(e, x, big, true, cap, s));
+        TPCG_TRY(elast_apply_impl<T>(e, x, big, true, cap, s, apply_err));
         TPCG_TRY(bround(big, eta));
         bswap(r, big);
         TPCG_TRY(elast_dot_impl<T>(c, r, r, sc + S_RR, s));
@@ -189,7 +195,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
         TPCG_TRY(bround(big, eta));
         bswap(p, big);
         // q_{k+1} = T(A p_{k+1}, eta_{k+1}); xi_{k+1} = p_{k+1} . q_{k+1}
-        TPCG_TRY(elast_apply_impl<T>(e, p, big, false, cap, s));
+        TPCG_TRY(elast_apply_impl<T>(e, p, big, false, cap, s, apply_err));
         TPCG_TRY(bround(big, eta));
         bswap(q, big);
         TPCG_TRY(elast_dot_impl<T>(c, p, q, sc + S_XI, s));
@@ -198,7 +204,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
     }
     for (int i = 0; i < 3; ++i) TPCG_TRY(copy_tensor_impl<T>(x[i], &xout[i], n, xout[i].cap, s));
     // true residual ||f - A x|| (Z formation per component, no truncation)
-    TPCG_TRY(elast_apply_impl<T>(e, x, big, true, cap, s));
+    TPCG_TRY(elast_apply_impl<T>(e, x, big, true, cap, s, apply_err));
     for (int i = 0; i < 3; ++i) TPCG_TRY(tensor_norm2<T>(c, big[i], sc + 170 + i, s));
     double nr2[3];
     TPCG_TRY(fetch(c, s, {{nr2, sc + 170, sizeof(nr2)}, {host, sc, sizeof(host)}}));

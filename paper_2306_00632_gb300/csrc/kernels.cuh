@@ -21,12 +21,16 @@ template <typename T>
 int tensor_norm2(tpcg_ctx c, tucker_t* y, double* out_dev, cudaStream_t st);
 // copy a plain FP32 tensor into an FP64 tensor (factors, core, descriptor)
 int promote_tensor(const tucker_t* src32, tucker_t* dst64, cudaStream_t st);
+// err: device int set to 1 when the product does not fit y (capacity or block limit).  Solvers pass a flag of
+// their own context, so that solves sharing a problem never see each other's flags; null selects the problem's
+// flag (standalone calls).
 template <typename T>
 int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st,
-               const tucker_t* rhs = nullptr);
+               const tucker_t* rhs = nullptr, int* err = nullptr);
 // y <- y + sign A x with the new blocks appended to y's block list
 template <typename T>
-int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st);
+int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st,
+                      int* err = nullptr);
 template <typename T>
 int axpby_impl(double a, const double* a_dev, const tucker_t* x, double b, const double* b_dev, const tucker_t* y,
                tucker_t* z, int* err_dev, cudaStream_t st);

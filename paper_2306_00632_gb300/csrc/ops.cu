@@ -115,8 +115,10 @@ __global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const doubl
 }
 
 template <typename T>
-int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st, const tucker_t* rhs) {
+int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st, const tucker_t* rhs,
+               int* err) {
     const int n = pb->n;
+    if (!err) err = reinterpret_cast<int*>(pb->d_scal + 60);
     dim3 grid((n + 127) / 128, pb->R + (residual ? 1 : 0), 3);
     const tucker_t* f = rhs ? rhs : &pb->f;
     prof_begin(PK_APPLY, st);
@@ -132,8 +134,8 @@ int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, c
     apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R,
                                         residual ? -1.0 : 1.0,
                                         residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
-                                        static_cast<TuckerDesc*>(y->desc), y->cap, reinterpret_cast<int*>(pb->d_scal + 60),
-                                        prof_dev(), n, pb->p, (int)sizeof(T));
+                                        static_cast<TuckerDesc*>(y->desc), y->cap, err, prof_dev(), n, pb->p,
+                                        (int)sizeof(T));
     TPCG_CHECK_LAUNCH();
     prof_end(PK_APPLY, st);
     return TPCG_OK;
@@ -141,8 +143,9 @@ int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, c
 // y <- y + sign A x: the R new blocks and their factor columns are appended after y's own (block sums of
 // operators, e.g. y_i = sum_j A_ij x_j of the elasticity system)
 template <typename T>
-int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st) {
+int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st, int* err) {
     const int n = pb->n;
+    if (!err) err = reinterpret_cast<int*>(pb->d_scal + 60);
     dim3 grid((n + 127) / 128, pb->R, 3);
     prof_begin(PK_APPLY, st);
     apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
@@ -154,17 +157,16 @@ int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double si
     TPCG_CHECK_LAUNCH();
     apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R, sign,
                                         static_cast<const TuckerDesc*>(y->desc), static_cast<TuckerDesc*>(y->desc),
-                                        y->cap, reinterpret_cast<int*>(pb->d_scal + 60), prof_dev(), n, pb->p,
-                                        (int)sizeof(T));
+                                        y->cap, err, prof_dev(), n, pb->p, (int)sizeof(T));
     TPCG_CHECK_LAUNCH();
     prof_end(PK_APPLY, st);
     return TPCG_OK;
 }
-template int apply_append_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, double, cudaStream_t);
-template int apply_append_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, double, cudaStream_t);
+template int apply_append_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, double, cudaStream_t, int*);
+template int apply_append_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, double, cudaStream_t, int*);
 
-template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*);
-template int apply_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*);
+template int apply_impl<double>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*, int*);
+template int apply_impl<float>(tpcg_problem, const tucker_t*, tucker_t*, bool, cudaStream_t, const tucker_t*, int*);
 
 // --------------------------------------------------------------------------------------------------
 // z = a x + b y: concatenated factors, block lists shifted and scaled (Sec. 2.3, sum).

@@ -118,6 +118,8 @@ static std::atomic<int> g_gemm_ctas_per_sm{2};
 int gemm_ctas_per_sm() { return g_gemm_ctas_per_sm.load(std::memory_order_relaxed); }
 static std::atomic<int> g_expsum_kind{1};
 int expsum_kind() { return g_expsum_kind.load(std::memory_order_relaxed); }
+static std::atomic<int> g_eig_kind{1};
+int eig_kind() { return g_eig_kind.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
@@ -127,6 +129,10 @@ extern "C" int tpcg_set_option(int key, long long value) {
     }
     if (key == TPCG_OPT_EXPSUM_BEST && (value == 0 || value == 1)) {
         tpcg::g_expsum_kind.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_EIG && (value == 0 || value == 1)) {
+        tpcg::g_eig_kind.store((int)value);
         return TPCG_OK;
     }
     tpcg::set_error("tpcg_set_option: unknown key or value out of range");

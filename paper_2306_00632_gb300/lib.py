@@ -17,6 +17,7 @@ MAX_BLOCKS = 128
 DESC_BYTES = 8192
 STATUS = {0: "OK", 1: "E_INVALID", 2: "E_NOMEM", 3: "E_NOT_CONVERGED", 4: "E_RANK_CAP", 5: "E_TIMEOUT",
           6: "E_CUDA", 7: "E_BREAKDOWN"}
+STATUS_CODES = {name: code for code, name in STATUS.items()}
 
 # the exported symbols declared in include/tpcg.h
 SYMBOLS = [
@@ -24,7 +25,7 @@ SYMBOLS = [
     "tpcg_problem_destroy",
     "tpcg_ctx_create", "tpcg_ctx_bytes", "tpcg_ctx_destroy", "tucker_set_plain", "tucker_get_ranks",
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
-    "tpcg_params_default", "tpcg_solve", "tpcg_solve_batch", "tpcg_ctx_stream", "tpcg_last_error", "tpcg_version",
+    "tpcg_params_default", "tpcg_solve", "tpcg_ctx_history", "tpcg_solve_batch", "tpcg_ctx_stream", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count", "tpcg_set_option",
     "tpcg_expsum_best",
     "tpcg_elast_setup", "tpcg_elast_create", "tpcg_elast_get_info", "tpcg_elast_apply", "tpcg_elast_residual",
@@ -32,7 +33,8 @@ SYMBOLS = [
 ]
 PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
               "round": 9}
-OPT_GEMM_CTAS_PER_SM, OPT_EXPSUM_BEST = 1, 2   # tpcg_set_option keys
+OPT_GEMM_CTAS_PER_SM, OPT_EXPSUM_BEST, OPT_EIG = 1, 2, 3   # tpcg_set_option keys
+HIST_COLS = 8   # TPCG_HIST_COLS: columns of a tpcg_ctx_history row
 PROF_SWEEPS = 11   # one-CTA Jacobi: (sweeps, Grams) in the (flops, bytes) fields of this kind
 
 
@@ -115,6 +117,7 @@ def load(build_if_missing: bool = True):
         "fd_precond_apply": (i, [vp, vp, PT, PT, vp]),
         "tpcg_params_default": (None, [C.POINTER(Params)]),
         "tpcg_solve": (i, [vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp]),
+        "tpcg_ctx_history": (i, [vp, C.POINTER(d), i, C.POINTER(C.c_int)]),
         "tpcg_ctx_stream": (i, [vp, C.POINTER(vp)]),
         "tpcg_solve_batch": (i, [i, vp, vp, C.POINTER(Params), PT, C.POINTER(Stats), vp, C.POINTER(C.c_int)]),
         "tpcg_last_error": (C.c_char_p, []),

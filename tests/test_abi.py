@@ -68,3 +68,23 @@ def test_expsum_best_is_host_only_and_matches_the_oracle():
     R = C.c_int(0)
     assert L.tpcg_expsum_best(0.5, 0.1, 4, buf, buf, C.byref(R), None) == 1    # M < 1
     assert L.tpcg_expsum_best(2.3e4, 0.1, 4, buf, buf, C.byref(R), None) == 1  # no R <= 4 meets the bound
+
+
+def test_problem_create_refuses_non_finite_tables_on_the_host():
+    # a NaN in the right-hand side (or an Inf in a band) is refused by the host-side check of
+    # tpcg_problem_create before any device call, so this runs without a GPU
+    import numpy as np
+    import pytest
+    from paper_2306_00632_gb300 import api, lib
+    from tests.gpu_helpers import oracle_problem
+    n, p = 8, 2
+    terms, f, P, tables = oracle_problem("cube", 0.0, n, p)
+    core = np.array(f[0], dtype=float)
+    core.flat[0] = np.nan
+    with pytest.raises(lib.TpcgError, match="NaN or an Inf") as e:
+        api.tpcg_problem_create(n, p, terms, core, f[1], tables)
+    assert e.value.code == lib.STATUS_CODES["E_INVALID"]
+    bad = [(w, [m.copy() for m in mats]) for w, mats in terms]
+    bad[1][1][2][3, 3] = np.inf
+    with pytest.raises(lib.TpcgError, match="NaN or an Inf"):
+        api.tpcg_problem_create(n, p, bad, f[0], f[1], tables)

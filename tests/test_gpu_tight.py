@@ -1,0 +1,78 @@
+"""FP64 TPCG (Alg. 5 with Alg. 1, 2 and 4) against the oracle under tight settings, iteration by iteration.
+
+With tol = 1e-12 and eps_min = 1e-14 every truncation of eq. rel_tol_iterates is close to lossless, so the
+CUDA path and the oracle run the same algorithm to FP64 rounding: the solution must agree to 1e-10
+relative, the iteration count exactly, and every iteration's CG scalars (omega, beta, xi), Alg. 2's trial
+count and its final tolerance eps_new.  The seeded twisted annulus at n = 16, p = 3 takes 45 iterations
+and exercises Alg. 2 with 1 to 5 trials per iteration; its smallest margin |v - 1| against delta is 3%,
+far above FP64 rounding, so the trial decisions are not near-ties."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import tucker
+from tests.gpu_helpers import gpu_problem, oracle_problem, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_00632_gb300 import api as a
+    from paper_2306_00632_gb300 import lib
+    lib.load()
+    return a
+
+
+def test_tpcg_fp64_tight_matches_oracle_per_iteration(api):
+    from oracle import tpcg as otp
+    n, p = 16, 3
+    amp = synth.amp_from_seed(7)
+    terms, f, P, _ = oracle_problem("twist", amp, n, p)
+    rec = []
+    xo, info = otp.tpcg(terms, f, P.apply, otp.Params(tol=1e-12, eps_min=1e-14), record=rec)
+    pb = gpu_problem("twist", amp, n, p)
+    ctx = api.Ctx(n, max(len(terms) * n + max(f[0].shape), P.RP * n, 2 * n), n)
+    x = api.Tucker(n, cap=n, core_cap=n ** 3)
+    st = api.tpcg_solve(pb, ctx, x, tol=1e-12, eps_min=1e-14)
+    torch.cuda.synchronize()
+    assert st.status == 0
+    assert st.iters == info["iters"]
+    assert rel(tucker.full(x.to_numpy()), tucker.full(xo)) < 1e-10
+    hist = api.ctx_history(ctx)
+    assert len(hist) == info["iters"] + 1
+    assert st.dt_trials == sum(r["trials"] for r in rec)
+    for k, r in enumerate(rec, start=1):
+        h = hist[k]
+        assert int(h["trials"]) == r["trials"], f"iteration {k}: Alg. 2 trials"
+        assert h["eps"] == pytest.approx(r["eps"], rel=1e-14), f"iteration {k}: eps_new"
+        assert h["omega"] == pytest.approx(r["omega"], rel=1e-8), f"iteration {k}: omega"
+        assert h["beta"] == pytest.approx(r["beta"], rel=1e-8, abs=1e-12), f"iteration {k}: beta"
+        assert h["xi"] == pytest.approx(r["xi"], rel=1e-8), f"iteration {k}: xi"
+        assert h["eta"] == pytest.approx(r["eta"], rel=1e-6), f"iteration {k}: eta"
+        assert h["res"] == pytest.approx(r["res"], rel=1e-6), f"iteration {k}: ||r_k|| / ||f||"
+
+
+def test_alg2_trials_and_eps_at_default_tolerance(api):
+    # the paper's default settings (tol 1e-6, eps_min = tol ||f|| / 10): the dynamic truncation makes the
+    # same decisions as the oracle in every iteration, so trial counts and eps_new agree exactly
+    from oracle import tpcg as otp
+    n, p = 16, 3   # 22 iterations, 1 to 5 trials each, smallest margin |v - 1| against delta 3%
+    amp = synth.amp_from_seed(7)
+    terms, f, P, _ = oracle_problem("twist", amp, n, p)
+    rec = []
+    xo, info = otp.tpcg(terms, f, P.apply, otp.Params(tol=1e-6), record=rec)
+    pb = gpu_problem("twist", amp, n, p)
+    ctx = api.Ctx(n, max(len(terms) * n + max(f[0].shape), P.RP * n, 2 * n), n)
+    x = api.Tucker(n, cap=n, core_cap=n ** 3)
+    st = api.tpcg_solve(pb, ctx, x, tol=1e-6)
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.iters == info["iters"]
+    hist = api.ctx_history(ctx)
+    assert [int(h["trials"]) for h in hist[1:]] == [r["trials"] for r in rec]
+    assert np.allclose([h["eps"] for h in hist[1:]], [r["eps"] for r in rec], rtol=1e-14)
+    assert rel(tucker.full(x.to_numpy()), tucker.full(xo)) < 1e-6

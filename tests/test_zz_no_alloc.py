@@ -42,6 +42,14 @@ def test_dot_static_matches_dot(api, dtype, tol):
     assert np.all(np.abs(got - ref) <= tol * scale)
     xx = api.tucker_dot_static(x, x).item()
     assert abs(xx - api.tucker_dot(ctx, x, x).item()) <= tol * tucker.norm(X) ** 2
+    # nothing is allocated on the device by further calls: free device memory is unchanged across them
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for q in range(2):
+        api.tucker_dot_static(x, y, out=out[q:q + 1])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= tol * scale)
 
 
 def test_dot_static_rejects_ranks_above_limit(api):
