@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--gemm-ctas-per-sm", type=int, default=2, help="grouped-GEMM CTA budget per SM (0: uncapped)")
     ap.add_argument("--eig", type=int, default=1, choices=[0, 1],
                     help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
+    ap.add_argument("--dst", type=int, default=1, choices=[0, 1], help="FD sine transforms: 1 FFT, 0 dense")
+    ap.add_argument("--qr", type=int, default=1, choices=[0, 1],
+                    help="Alg. 1 step 1: 1 QR only below n/2 columns, 0 QR whenever k < n")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
     ap.add_argument("--serve", type=float, default=0.0,
                     help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
@@ -236,7 +239,7 @@ def rank_seeds(rank: int, solves_per_step: int):
 def _profile(L, lib):
     import ctypes as C
     prof = {}
-    for name, kind in lib.PROF_KINDS.items():
+    for name, kind in list(lib.PROF_KINDS.items()) + [("sweeps", lib.PROF_SWEEPS)]:
         ms, cnt, fl, by = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
         L.tpcg_profile_get(kind, C.byref(ms), C.byref(cnt), C.byref(fl), C.byref(by))
         prof[name] = {"ms": ms.value, "launches": cnt.value, "flops": fl.value, "bytes": by.value}
@@ -419,6 +422,8 @@ def run_gpu(args):
     streams = [torch.cuda.Stream() for _ in range(B)] if args.torch_streams else [None] * B
     lib.check(L.tpcg_set_option(lib.OPT_GEMM_CTAS_PER_SM, args.gemm_ctas_per_sm), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_EIG, args.eig), "tpcg_set_option")
+    lib.check(L.tpcg_set_option(lib.OPT_DST, args.dst), "tpcg_set_option")
+    lib.check(L.tpcg_set_option(lib.OPT_QR, args.qr), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     main = torch.cuda.current_stream()
 
@@ -483,7 +488,8 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
-                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig,
+                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig, "dst": args.dst,
+                      "qr": args.qr,
                       "refine_keep": args.refine_keep,
                       "seeds": f"{seeds[0]}..{seeds[-1]} on rank 0, disjoint ranges per rank (amp from seed)",
                       "tol": TOL, "rank_cap": rc,
@@ -497,7 +503,8 @@ def run_gpu(args):
                      "rank": [list(s.rank) for s in last]},
            "single": {"iters": [int(s.iters) for s in single], "true_rel_res": [float(s.true_rel_res) for s in single]},
            "gpu_launches": int(launches), "roofline": roof,
-           "kernel_ms_single": {k: round(v["ms"], 3) for k, v in prof.items()},
+           "kernel_ms_single": {k: round(v["ms"], 3) for k, v in prof.items() if k != "sweeps"},
+           "eig_sweeps_per_gram": prof["sweeps"]["flops"] / max(prof["sweeps"]["bytes"], 1.0),
            "clocks": clk}
 
     # the solution of seed SEED (problem 0) from the last timed step, against the oracle's stored solution

@@ -300,6 +300,14 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   eigenvectors (the pivoted Cholesky of G = Z Z^T is the column-pivoted QR of Z^T, the preconditioner of
  *   Drmac and Veselic's one-sided Jacobi SVD); 0 the two-sided cyclic Jacobi on G with accumulated rotations. */
 #define TPCG_OPT_EIG 3
+/*   TPCG_OPT_DST: how the preconditioner applies the sine block U_dft of App. B (Alg. 4): 1 (default) batched FFTs,
+ *   O(n1 log n1) per column, by Bluestein's chirp-z identity for any n1 <= 1024 (power-of-two FFTs of size
+ *   >= 2 n1 - 1 in shared memory); 0 the dense n1 x n1 product with the stored sine matrix. */
+#define TPCG_OPT_DST 4
+/*   TPCG_OPT_QR: when Alg. 1 step 1 factors Y_t = Q_t R_t.  Any orthonormal Q_t whose span contains the columns of
+ *   Y_t gives the same truncation, Q_t = I (R_t = Y_t) included; the QR only shrinks Z from n to k_t in mode t.
+ *   1 (default): QR only when k_t < n / 2, else Q_t = I; 0: QR whenever k_t < n. */
+#define TPCG_OPT_QR 5
 int tpcg_set_option(int key, long long value);
 
 /* Best exponential sum s_R(lambda) = sum_j omega_j exp(-alpha_j lambda) for 1/lambda on [1, M] in the maximum

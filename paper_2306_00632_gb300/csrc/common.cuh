@@ -105,6 +105,7 @@ struct RoundPlan {
     long long ldR[3];
     int kz3;           // total K of the fused last-mode GEMM
     int status;
+    int strict;        // FP64 rule: charge every discarded Gram eigenvalue its rounding uncertainty
 };
 
 // ------------------------------------------------------------------------------------ host objects
@@ -164,6 +165,13 @@ struct tpcg_ctx_s {
     std::vector<double> hist;
 };
 
+namespace tpcg {
+// FFT sizes of the chirp-z sine transforms of the preconditioner (dst.cu)
+struct ChirpInfo {
+    int L = 0, Mf = 0, logMf = 0;
+};
+}  // namespace tpcg
+
 struct tpcg_problem_s {
     int n, p, R, RP, n1, n2, dtype;
     int rf[3];
@@ -186,6 +194,8 @@ struct tpcg_problem_s {
     void* d_wtval;
     void* d_v2u2;        // n * n2
     void* d_dst;         // n1 x n1 sine matrix sqrt2 sin(j pi x_l)
+    void* d_chirp;       // chirp-z tables of the FFT sine transforms (complex pairs), null if n1 > 1024
+    tpcg::ChirpInfo chirp;
     double* d_omega;     // RP
     double* d_alpha;     // RP
     double* d_scal;      // problem scalars (lambda_min, ...)

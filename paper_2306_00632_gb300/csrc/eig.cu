@@ -56,10 +56,11 @@ __device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double tr
     int s = M;
     if (sizeof(T) == 8) {
         // each eigenvalue of an FP64 Gram is known only to about eps trace (the Gram squares the singular
-        // values, so sigma_i below sqrt(eps) sigma_max is unresolved): a direction is discarded only if its
-        // clamped eigenvalue plus that uncertainty still fits the budget.  With a budget below the noise level
-        // the truncation is then lossless instead of dropping directions whose energy it cannot see.
-        const double unc = 4.0 * 2.220446049250313e-16 * trace;
+        // values, so sigma_i below sqrt(eps) sigma_max is unresolved).  In strict mode (tolerances below what
+        // the Gram resolves) a direction is discarded only if its clamped eigenvalue plus that uncertainty
+        // still fits the budget, so the truncation stays lossless instead of dropping directions whose energy
+        // it cannot see; otherwise the clamped eigenvalues are used as they are.
+        const double unc = p.strict ? 4.0 * 2.220446049250313e-16 * trace : 0.0;
         double tail = 0.0;
         for (int i = M - 1; i >= 0; --i) {
             const double li = (lam[i] > 0.0 ? lam[i] : 0.0) + unc;
@@ -840,34 +841,36 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
 // FP32 Grams up to HJ_MAXM: pivoted Cholesky, then one-sided (Hestenes) Jacobi on the Cholesky factor.
 //
 //  1. G = sum_k l_k l_k^T by the outer-product Cholesky with diagonal pivoting (pivots chosen by index, no
-//     row swaps, so L = [l_1 .. l_rc] satisfies G = L L^T in G's own index order); it stops once every
-//     remaining diagonal entry is below 1e-9 trace(G), the remainder being counted as discarded energy by
-//     the truncation rule (trace minus kept eigenvalues).  The pivoted Cholesky of G = Z Z^T is the
-//     column-pivoted QR of Z^T (L = R^T up to the row order), the preconditioning step of Drmac and
-//     Veselic's one-sided Jacobi SVD, after which few sweeps are needed.
+//     row swaps, so L = [l_1 .. l_rc] satisfies G = L L^T in G's own index order), with G held in registers
+//     (32 entries per thread).  It stops once the remaining diagonal (the trace of the Schur complement) is
+//     at most 1% of this mode's truncation budget, or every remaining pivot is below 1e-9 trace(G): the
+//     remainder is then energy the truncation discards anyway, and the truncation rule (trace minus kept
+//     eigenvalues) counts it.  The pivoted Cholesky of G = Z Z^T is the column-pivoted QR of Z^T (L = R^T up
+//     to the row order), the preconditioning step of Drmac and Veselic's one-sided Jacobi SVD, after which few
+//     sweeps are needed.
 //  2. One-sided Jacobi makes the columns of L mutually orthogonal by plane rotations from the right:
 //     L J = U Sigma, so the normalised columns are eigenvectors of G and their squared norms its
 //     eigenvalues; no rotation matrix is accumulated.  Pair (a_p, a_q) with alpha = |a_p|^2, beta = |a_q|^2,
-//     gamma = a_p . a_q rotates when |gamma| > tau sqrt(alpha beta): zeta = (beta - alpha) / (2 gamma),
+//     gamma = a_p . a_q rotates when gamma^2 > tau^2 alpha beta: zeta = (beta - alpha) / (2 gamma),
 //     t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), a_p <- c a_p - s a_q, a_q <- s a_p + c a_q, and the
 //     norms follow as alpha - t gamma, beta + t gamma (recomputed exactly at every sweep start).
-//  3. The 128 columns are the players of a round-robin tournament (circle method, one fixed player): 64 pair
-//     slots, four per warp, every lane holding four rows of each of its warp's eight columns in registers.
-//     A step computes the four pair products of a warp with one packed butterfly (each lane ends with the
-//     full gamma of one slot), rotates in registers, then moves every column but the fixed one to the next
-//     position of the ring: inside a warp this is a register move, and only the two columns at a warp's
-//     ends cross to the neighbouring warps, through double-buffered shared memory (one barrier per step).
+//  3. The columns are the players of a round-robin tournament (circle method, one fixed player) on 8 NWA
+//     players, NWA in {2, 4, 8, 16} the fewest warps whose ring holds the rc columns of L: four pair slots per
+//     warp, every lane holding four rows of each of its warp's eight columns in registers.  A step computes
+//     the four pair products of a warp with one packed butterfly (each lane ends with the full gamma of one
+//     slot), rotates in registers, then moves every column but the fixed one to the next position of the
+//     ring: inside a warp this is a register move, and only the two columns at a warp's ends cross to the
+//     neighbouring warps, through double-buffered shared memory (one barrier per step).
 // ------------------------------------------------------------------------------------------------------------
 constexpr int HJ_WARPS = 16;
 constexpr int HJ_THREADS = 32 * HJ_WARPS;
 constexpr int HJ_SLOTS = 4;                                  // pair slots per warp
-constexpr int HJ_PLAYERS = 2 * HJ_SLOTS * HJ_WARPS;          // columns in the ring (128)
+constexpr int HJ_PLAYERS = 2 * HJ_SLOTS * HJ_WARPS;          // columns of the largest ring (128)
 constexpr int HJ_MAXM = 128;                                 // rows: four per lane
-constexpr int HJ_LDA = HJ_MAXM + 1;
-static_assert(HJ_PLAYERS == HJ_MAXM && (HJ_MAXM * HJ_LDA) % 4 == 0, "ring and row layout");
+static_assert(HJ_PLAYERS == HJ_MAXM, "ring and row layout");
 
 static inline size_t hj_smem_bytes() {
-    return ((size_t)HJ_MAXM * HJ_LDA + (size_t)HJ_MAXM * HJ_MAXM + (size_t)2 * 2 * HJ_WARPS * HJ_MAXM) * sizeof(float);
+    return ((size_t)HJ_MAXM * HJ_MAXM + (size_t)2 * 2 * HJ_WARPS * HJ_MAXM) * sizeof(float);
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -884,11 +887,10 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr unsigned FULL = 0xffffffffu;
     extern __shared__ __align__(16) unsigned char hj_smem[];
-    float* A = reinterpret_cast<float*>(hj_smem);            // Cholesky working matrix, ld HJ_LDA
-    float* L = A + HJ_MAXM * HJ_LDA;                         // factor columns, ld HJ_MAXM
+    float* L = reinterpret_cast<float*>(hj_smem);            // factor columns, then the rotated columns; ld 128
     float* X = L + HJ_MAXM * HJ_MAXM;                        // ring exchange [buffer][direction][warp][row]
     __shared__ float dg[HJ_MAXM];
-    __shared__ float wbest[HJ_WARPS];
+    __shared__ float wbest[HJ_WARPS], wsum[HJ_WARPS];
     __shared__ int wbi[HJ_WARPS];
     __shared__ float xa[2][2][HJ_WARPS];
     __shared__ double lam[HJ_PLAYERS];                        // squared column norms, by column
@@ -903,8 +905,17 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
         }
         return;
     }
-    for (int j = warp; j < M; j += HJ_WARPS)
-        for (int i = lane; i < M; i += 32) A[i + j * HJ_LDA] = G[i + (long long)j * M];
+    // G in registers: entry (i, j) with j = warp + 16 a, i = lane + 32 b
+    float Ar[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int j = warp + 16 * a;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = lane + 32 * b;
+            Ar[a][b] = (i < M && j < M) ? G[i + (long long)j * M] : 0.f;
+        }
+    }
     for (int e = tid; e < HJ_MAXM * HJ_MAXM / 4; e += HJ_THREADS)
         reinterpret_cast<float4*>(L)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = tid; i < HJ_MAXM; i += HJ_THREADS) dg[i] = (i < M) ? G[i + (long long)i * M] : -1.f;
@@ -919,56 +930,91 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
     }
     __syncthreads();
     const float tr = (float)s_tr;
-    // ---- 1. pivoted Cholesky, G = sum_k l_k l_k^T
+    // ---- 1. pivoted Cholesky, G = sum_k l_k l_k^T, until the Schur complement is negligible for this mode
     const float thr = 1e-9f * tr;
+    const float stop_rem = fmaxf(thr, 0.01f * (float)p.budget);
+    int rc = 0;
     for (int k = 0; k < M; ++k) {
-        {   // the largest remaining diagonal entry (ties: the lowest index): 8 entries per warp, then 16 warps
+        {   // the largest remaining diagonal entry (ties: the lowest index) and the remaining trace
             const int i = warp * 8 + (lane & 7);
             float v = lane < 8 ? dg[i] : -2.f;
+            float sm = lane < 8 ? fmaxf(dg[i], 0.f) : 0.f;
             int bi = i;
 #pragma unroll
             for (int o = 4; o > 0; o >>= 1) {
                 const float v2 = __shfl_xor_sync(FULL, v, o);
                 const int b2 = __shfl_xor_sync(FULL, bi, o);
+                sm += __shfl_xor_sync(FULL, sm, o);
                 if (v2 > v || (v2 == v && b2 < bi)) { v = v2; bi = b2; }
             }
-            if (lane == 0) { wbest[warp] = v; wbi[warp] = bi; }
+            if (lane == 0) { wbest[warp] = v; wbi[warp] = bi; wsum[warp] = sm; }
         }
         __syncthreads();
-        float dmax = -2.f;
+        float dmax = -2.f, rem = 0.f;
         int piv = 0;
-        for (int w = 0; w < HJ_WARPS; ++w)
+        for (int w = 0; w < HJ_WARPS; ++w) {
+            rem += wsum[w];
             if (wbest[w] > dmax) { dmax = wbest[w]; piv = wbi[w]; }
-        if (!(dmax > thr)) break;   // the same decision in every thread (a NaN stops the factorisation)
+        }
+        // the same decision in every thread (a NaN stops the factorisation)
+        if (!(dmax > thr) || !(rem > stop_rem)) break;
         const float r = sqrtf(dmax);
-        if (tid < M) L[tid + k * HJ_MAXM] = (tid == piv) ? r : A[tid + piv * HJ_LDA] / r;
-        __syncthreads();
-        const float* lk = L + k * HJ_MAXM;
-        for (int j = warp; j < M; j += HJ_WARPS) {
-            const float lj = lk[j];
-            for (int i = lane; i < M; i += 32) {
-                const float a = (i == piv || j == piv) ? 0.f : fmaf(-lk[i], lj, A[i + j * HJ_LDA]);
-                A[i + j * HJ_LDA] = a;
-                if (i == j) dg[i] = (i == piv) ? -1.f : a;
+        if (warp == (piv & 15)) {   // the warp holding column piv writes l_k = G_k[:, piv] / sqrt(d_piv)
+            const int ap = piv >> 4;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float a = 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a = (q == ap) ? Ar[q][b] : a;
+                const int i = lane + 32 * b;
+                if (i < M) L[i + k * HJ_MAXM] = (i == piv) ? r : a / r;
             }
         }
         __syncthreads();
+        const float* lk = L + k * HJ_MAXM;
+        float li[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) li[b] = lk[lane + 32 * b];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int j = warp + 16 * a;
+            const float lj = lk[j];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = lane + 32 * b;
+                const float v = (i == piv || j == piv) ? 0.f : fmaf(-li[b], lj, Ar[a][b]);
+                Ar[a][b] = v;
+                if (i == j && i < M) dg[i] = (i == piv) ? -1.f : v;
+            }
+        }
+        __syncthreads();
+        rc = k + 1;
     }
-    // ---- 2. one-sided Jacobi on the columns of L: slot k of warp w (k = 4 w + j) starts with columns k and 64 + k
-    constexpr int H = HJ_PLAYERS / 2;
+    // ---- 2. one-sided Jacobi on the rc columns of L: a ring of 8 NWA players
+    const int NWA = rc <= 16 ? 2 : (rc <= 32 ? 4 : (rc <= 64 ? 8 : 16));
+    const int H = HJ_SLOTS * NWA;                  // pair slots; slot k starts with columns k and H + k
+    const int P = 2 * H;
+    const bool active = warp < NWA;
     float T[HJ_SLOTS][4], B[HJ_SLOTS][4], aT[HJ_SLOTS], aB[HJ_SLOTS];
 #pragma unroll
     for (int j = 0; j < HJ_SLOTS; ++j) {
         const int k = HJ_SLOTS * warp + j;
-        const float4 t = ld4(L + k * HJ_MAXM + 4 * lane), b = ld4(L + (H + k) * HJ_MAXM + 4 * lane);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f), b = t;
+        if (active) {
+            t = ld4(L + k * HJ_MAXM + 4 * lane);
+            b = ld4(L + (H + k) * HJ_MAXM + 4 * lane);
+        }
         T[j][0] = t.x; T[j][1] = t.y; T[j][2] = t.z; T[j][3] = t.w;
         B[j][0] = b.x; B[j][1] = b.y; B[j][2] = b.z; B[j][3] = b.w;
+        aT[j] = 0.f;
+        aB[j] = 0.f;
     }
     const int pj = (lane >> 3) & 3;         // the slot whose rotation this lane computes
     const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
     const float floor_g = 1e-12f * tr;      // products below this are rounding noise of the factor
+    const float tau2 = tau * tau;
     int nsweeps = 0, buf = 0;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps && rc > 1; ++sweep) {
         ++nsweeps;
 #pragma unroll
         for (int j = 0; j < HJ_SLOTS; ++j) {   // exact squared norms
@@ -979,98 +1025,105 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
             aB[j] = warp_sum(sb);
         }
         int rot = 0;
-        for (int step = 0; step < HJ_PLAYERS - 1; ++step) {
-            float g[HJ_SLOTS];
+        for (int step = 0; step < P - 1; ++step) {
+            if (active) {
+                float g[HJ_SLOTS];
 #pragma unroll
-            for (int j = 0; j < HJ_SLOTS; ++j) {
-                float acc = 0.f;
+                for (int j = 0; j < HJ_SLOTS; ++j) {
+                    float acc = 0.f;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc = fmaf(T[j][q], B[j][q], acc);
-                g[j] = acc;
-            }
-            // packed butterfly: after it, every lane holds the full product of slot pj
-            const float x0 = __shfl_xor_sync(FULL, b4 ? g[0] : g[2], 16);
-            const float x1 = __shfl_xor_sync(FULL, b4 ? g[1] : g[3], 16);
-            const float u0 = (b4 ? g[2] : g[0]) + x0;
-            const float u1 = (b4 ? g[3] : g[1]) + x1;
-            const float y = __shfl_xor_sync(FULL, b3 ? u0 : u1, 8);
-            float gm = (b3 ? u1 : u0) + y;
-            gm += __shfl_xor_sync(FULL, gm, 4);
-            gm += __shfl_xor_sync(FULL, gm, 2);
-            gm += __shfl_xor_sync(FULL, gm, 1);
-            const float al = pj == 0 ? aT[0] : pj == 1 ? aT[1] : pj == 2 ? aT[2] : aT[3];
-            const float be = pj == 0 ? aB[0] : pj == 1 ? aB[1] : pj == 2 ? aB[2] : aB[3];
-            float c = 1.f, s = 0.f, tg = 0.f;
-            if (fabsf(gm) > tau * sqrtf(al) * sqrtf(be) && fabsf(gm) > floor_g) {
-                const float zeta = (be - al) / (2.f * gm);
-                const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
-                c = 1.f / sqrtf(fmaf(t, t, 1.f));
-                s = c * t;
-                tg = t * gm;
-                rot = 1;
-            }
-#pragma unroll
-            for (int j = 0; j < HJ_SLOTS; ++j) {
-                const float cj = __shfl_sync(FULL, c, 8 * j), sj = __shfl_sync(FULL, s, 8 * j);
-                const float tgj = __shfl_sync(FULL, tg, 8 * j);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float tp = T[j][q], bq = B[j][q];
-                    T[j][q] = fmaf(cj, tp, -sj * bq);
-                    B[j][q] = fmaf(sj, tp, cj * bq);
+                    for (int q = 0; q < 4; ++q) acc = fmaf(T[j][q], B[j][q], acc);
+                    g[j] = acc;
                 }
-                aT[j] -= tgj;
-                aB[j] += tgj;
-            }
-            // ring move: top[k] -> top[k+1] (top[0] fixed), top[63] -> bottom[63], bottom[k] -> bottom[k-1],
-            // bottom[0] -> top[1]; the two columns at a warp's ends go through shared memory
-            float* xt = X + ((buf * 2 + 0) * HJ_WARPS) * HJ_MAXM;
-            float* xb = X + ((buf * 2 + 1) * HJ_WARPS) * HJ_MAXM;
-            if (warp < HJ_WARPS - 1) {
-                st4(xt + warp * HJ_MAXM + 4 * lane, T[HJ_SLOTS - 1]);
-                if (lane == 0) xa[buf][0][warp] = aT[HJ_SLOTS - 1];
-            }
-            if (warp > 0) {
-                st4(xb + warp * HJ_MAXM + 4 * lane, B[0]);
-                if (lane == 0) xa[buf][1][warp] = aB[0];
+                // packed butterfly: after it, every lane holds the full product of slot pj
+                const float x0 = __shfl_xor_sync(FULL, b4 ? g[0] : g[2], 16);
+                const float x1 = __shfl_xor_sync(FULL, b4 ? g[1] : g[3], 16);
+                const float u0 = (b4 ? g[2] : g[0]) + x0;
+                const float u1 = (b4 ? g[3] : g[1]) + x1;
+                const float y = __shfl_xor_sync(FULL, b3 ? u0 : u1, 8);
+                float gm = (b3 ? u1 : u0) + y;
+                gm += __shfl_xor_sync(FULL, gm, 4);
+                gm += __shfl_xor_sync(FULL, gm, 2);
+                gm += __shfl_xor_sync(FULL, gm, 1);
+                const float al = pj == 0 ? aT[0] : pj == 1 ? aT[1] : pj == 2 ? aT[2] : aT[3];
+                const float be = pj == 0 ? aB[0] : pj == 1 ? aB[1] : pj == 2 ? aB[2] : aB[3];
+                float c = 1.f, s = 0.f, tg = 0.f;
+                if (gm * gm > tau2 * al * be && fabsf(gm) > floor_g) {
+                    const float zeta = (be - al) * __frcp_rn(2.f * gm);
+                    const float t = copysignf(__frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f))), zeta);
+                    c = __frsqrt_rn(fmaf(t, t, 1.f));
+                    s = c * t;
+                    tg = t * gm;
+                    rot = 1;
+                }
+#pragma unroll
+                for (int j = 0; j < HJ_SLOTS; ++j) {
+                    const float cj = __shfl_sync(FULL, c, 8 * j), sj = __shfl_sync(FULL, s, 8 * j);
+                    const float tgj = __shfl_sync(FULL, tg, 8 * j);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float tp = T[j][q], bq = B[j][q];
+                        T[j][q] = fmaf(cj, tp, -sj * bq);
+                        B[j][q] = fmaf(sj, tp, cj * bq);
+                    }
+                    aT[j] -= tgj;
+                    aB[j] += tgj;
+                }
+                // ring move: top[k] -> top[k+1] (top[0] fixed), top[H-1] -> bottom[H-1], bottom[k] -> bottom[k-1],
+                // bottom[0] -> top[1]; the two columns at a warp's ends go through shared memory
+                float* xt = X + ((buf * 2 + 0) * HJ_WARPS) * HJ_MAXM;
+                float* xb = X + ((buf * 2 + 1) * HJ_WARPS) * HJ_MAXM;
+                if (warp < NWA - 1) {
+                    st4(xt + warp * HJ_MAXM + 4 * lane, T[HJ_SLOTS - 1]);
+                    if (lane == 0) xa[buf][0][warp] = aT[HJ_SLOTS - 1];
+                }
+                if (warp > 0) {
+                    st4(xb + warp * HJ_MAXM + 4 * lane, B[0]);
+                    if (lane == 0) xa[buf][1][warp] = aB[0];
+                }
             }
             __syncthreads();
-            float oB0[4], oT3[4];
+            if (active) {
+                const float* xt = X + ((buf * 2 + 0) * HJ_WARPS) * HJ_MAXM;
+                const float* xb = X + ((buf * 2 + 1) * HJ_WARPS) * HJ_MAXM;
+                float oB0[4], oT3[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { oB0[q] = B[0][q]; oT3[q] = T[HJ_SLOTS - 1][q]; }
-            const float oaB0 = aB[0], oaT3 = aT[HJ_SLOTS - 1];
+                for (int q = 0; q < 4; ++q) { oB0[q] = B[0][q]; oT3[q] = T[HJ_SLOTS - 1][q]; }
+                const float oaB0 = aB[0], oaT3 = aT[HJ_SLOTS - 1];
 #pragma unroll
-            for (int j = 0; j < HJ_SLOTS - 1; ++j) {
+                for (int j = 0; j < HJ_SLOTS - 1; ++j) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) B[j][q] = B[j + 1][q];
-                aB[j] = aB[j + 1];
-            }
-            if (warp == HJ_WARPS - 1) {
+                    for (int q = 0; q < 4; ++q) B[j][q] = B[j + 1][q];
+                    aB[j] = aB[j + 1];
+                }
+                if (warp == NWA - 1) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) B[HJ_SLOTS - 1][q] = oT3[q];
-                aB[HJ_SLOTS - 1] = oaT3;
-            } else {
-                const float4 v = ld4(xb + (warp + 1) * HJ_MAXM + 4 * lane);
-                B[HJ_SLOTS - 1][0] = v.x; B[HJ_SLOTS - 1][1] = v.y; B[HJ_SLOTS - 1][2] = v.z; B[HJ_SLOTS - 1][3] = v.w;
-                aB[HJ_SLOTS - 1] = xa[buf][1][warp + 1];
-            }
+                    for (int q = 0; q < 4; ++q) B[HJ_SLOTS - 1][q] = oT3[q];
+                    aB[HJ_SLOTS - 1] = oaT3;
+                } else {
+                    const float4 v = ld4(xb + (warp + 1) * HJ_MAXM + 4 * lane);
+                    B[HJ_SLOTS - 1][0] = v.x; B[HJ_SLOTS - 1][1] = v.y;
+                    B[HJ_SLOTS - 1][2] = v.z; B[HJ_SLOTS - 1][3] = v.w;
+                    aB[HJ_SLOTS - 1] = xa[buf][1][warp + 1];
+                }
 #pragma unroll
-            for (int j = HJ_SLOTS - 1; j >= 2; --j) {
+                for (int j = HJ_SLOTS - 1; j >= 2; --j) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) T[j][q] = T[j - 1][q];
-                aT[j] = aT[j - 1];
-            }
-            if (warp == 0) {   // top[0] stays; bottom[0] enters the top row at slot 1
+                    for (int q = 0; q < 4; ++q) T[j][q] = T[j - 1][q];
+                    aT[j] = aT[j - 1];
+                }
+                if (warp == 0) {   // top[0] stays; bottom[0] enters the top row at slot 1
 #pragma unroll
-                for (int q = 0; q < 4; ++q) T[1][q] = oB0[q];
-                aT[1] = oaB0;
-            } else {
+                    for (int q = 0; q < 4; ++q) T[1][q] = oB0[q];
+                    aT[1] = oaB0;
+                } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) T[1][q] = T[0][q];
-                aT[1] = aT[0];
-                const float4 v = ld4(xt + (warp - 1) * HJ_MAXM + 4 * lane);
-                T[0][0] = v.x; T[0][1] = v.y; T[0][2] = v.z; T[0][3] = v.w;
-                aT[0] = xa[buf][0][warp - 1];
+                    for (int q = 0; q < 4; ++q) T[1][q] = T[0][q];
+                    aT[1] = aT[0];
+                    const float4 v = ld4(xt + (warp - 1) * HJ_MAXM + 4 * lane);
+                    T[0][0] = v.x; T[0][1] = v.y; T[0][2] = v.z; T[0][3] = v.w;
+                    aT[0] = xa[buf][0][warp - 1];
+                }
             }
             buf ^= 1;
         }
@@ -1078,29 +1131,35 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
     }
     // ---- 3. eigenvalues (exact squared norms), decreasing order, truncation rule, normalised kept columns
     __syncthreads();
-    float* C = A;   // the columns, ld HJ_MAXM (the Cholesky matrix is no longer needed)
+    float* C = L;   // the rotated columns, ld HJ_MAXM (L is no longer needed)
+    if (active) {
 #pragma unroll
-    for (int j = 0; j < HJ_SLOTS; ++j) {
-        const int k = HJ_SLOTS * warp + j;
-        st4(C + k * HJ_MAXM + 4 * lane, T[j]);
-        st4(C + (H + k) * HJ_MAXM + 4 * lane, B[j]);
-        float st = 0.f, sb = 0.f;
+        for (int j = 0; j < HJ_SLOTS; ++j) {
+            const int k = HJ_SLOTS * warp + j;
+            st4(C + k * HJ_MAXM + 4 * lane, T[j]);
+            st4(C + (H + k) * HJ_MAXM + 4 * lane, B[j]);
+            float st = 0.f, sb = 0.f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { st = fmaf(T[j][q], T[j][q], st); sb = fmaf(B[j][q], B[j][q], sb); }
-        st = warp_sum(st);
-        sb = warp_sum(sb);
-        if (lane == 0) { lam[k] = (double)st; lam[H + k] = (double)sb; }
+            for (int q = 0; q < 4; ++q) { st = fmaf(T[j][q], T[j][q], st); sb = fmaf(B[j][q], B[j][q], sb); }
+            st = warp_sum(st);
+            sb = warp_sum(sb);
+            if (lane == 0) { lam[k] = (double)st; lam[H + k] = (double)sb; }
+        }
     }
     __syncthreads();
     for (int i = tid; i < HJ_PLAYERS; i += HJ_THREADS) {
-        const double li = sort_key(lam[i]);
-        int rk = 0;
-        for (int j = 0; j < HJ_PLAYERS; ++j) {
-            const double lj = sort_key(lam[j]);
-            if (lj > li || (lj == li && j < i)) ++rk;
+        if (i < P) {
+            const double li = sort_key(lam[i]);
+            int rk = 0;
+            for (int j = 0; j < P; ++j) {
+                const double lj = sort_key(lam[j]);
+                if (lj > li || (lj == li && j < i)) ++rk;
+            }
+            ord[rk] = (short)i;
+            lsort[rk] = lam[i];
+        } else {
+            lsort[i] = 0.0;   // eigenvalues past the ring: zero (the Cholesky remainder is discarded energy)
         }
-        ord[rk] = (short)i;
-        lsort[rk] = lam[i];
     }
     __syncthreads();
     if (tid == 0) {

@@ -7,9 +7,10 @@
 
 namespace tpcg {
 
+// strict_mode: -1 automatic (the FP64 rule charges the Gram's rounding uncertainty when eps < 1e-7), 0 off, 1 on
 template <typename T>
 int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
-               cudaStream_t st);
+               cudaStream_t st, int strict_mode = -1);
 // FP64 Z formation, FP32 ST-HOSVD into out32; the discarded energy may also reach abs_tol^2 (absolute norm floor)
 // round_impl(c, y, 0, eps_dev, cap) replayed from a per-context CUDA graph (captured on first use)
 template <typename T>
@@ -48,6 +49,16 @@ template <typename T>
 int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStream_t st, const double* wdir = nullptr);
 template <typename T>
 int copy_tensor_impl(const tucker_t* src, tucker_t* dst, int n, int cap, cudaStream_t st);
+
+// chirp-z (Bluestein) FFT sine transforms of App. B (dst.cu): host tables for length n1 and degree p (complex
+// pairs: twiddles, then forward and inverse pre/post chirps and filter spectra), and the batched transform of
+// the columns c < mult rank_t of every mode t (kind 0: U_dft^T x, kind 1: U_dft x)
+int chirp_tables(int n1, int p, ChirpInfo* info, std::vector<double>* out);
+template <typename T>
+int launch_chirp(tpcg_problem pb, int kind, const TuckerDesc* sd, int mult, int rp_guard, int vcap, int maxcols,
+                 const T* const* X, T* const* Y, int ldx, int ldy, cudaStream_t st);
+int dst_kind();   // TPCG_OPT_DST: 1 FFT sine transforms, 0 dense sine matrix
+int qr_kind();    // TPCG_OPT_QR: 1 QR of a factor only below n/2 columns, 0 whenever it has fewer than n
 
 int set_plain(tucker_t* t, int r1, int r2, int r3, cudaStream_t st);
 int set_zero(tucker_t* t, cudaStream_t st);

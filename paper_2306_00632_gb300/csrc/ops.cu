@@ -617,14 +617,25 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
                                         static_cast<T*>(v->U[0]), static_cast<T*>(v->U[1]),
                                         static_cast<T*>(v->U[2]), ga, counts, v->cap, err);
     TPCG_CHECK_LAUNCH();
-    TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, n1, rc, st)));
+    const bool fft = pb->d_chirp != nullptr && dst_kind() == 1;
+    const T* fx[3] = {buf[0][0], buf[1][0], buf[2][0]};
+    T* fy[3] = {buf[0][1], buf[1][1], buf[2][1]};
+    if (fft)   // u_t = U_dft^T T_t by FFTs
+        TPCG_TRY(launch_chirp<T>(pb, 0, sd, 1, RP, v->cap, rc, fx, fy, n1, n1, st));
+    else
+        TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, n1, rc, st)));
     if (n2 > 0) TPCG_TRY((launch_gemm<T, true, false>(ga + 3, counts, 3, 1, n2, rc, st)));
     dim3 g2(2, RP * rc, 3);
     fd_scale_kernel<T><<<g2, 256, 0, st>>>(sd, buf[0][1], buf[1][1], buf[2][1], static_cast<const T*>(pb->d_lam),
                                            static_cast<const T*>(pb->d_mu), pb->d_alpha, lmin, cw[0], cw[1], cw[2], n1, n2, RP,
                                            buf[0][2], buf[1][2], buf[2][2], v->cap);
     TPCG_CHECK_LAUNCH();
-    TPCG_TRY((launch_gemm<T, false, false>(ga + 6, counts, 3, 1, n1, RP * rc, st)));
+    const T* ex[3] = {buf[0][2], buf[1][2], buf[2][2]};
+    T* ey[3] = {buf[0][3], buf[1][3], buf[2][3]};
+    if (fft)   // A_t = U_dft E_t by FFTs
+        TPCG_TRY(launch_chirp<T>(pb, 1, sd, RP, RP, v->cap, RP * rc, ex, ey, n1, n1, st));
+    else
+        TPCG_TRY((launch_gemm<T, false, false>(ga + 6, counts, 3, 1, n1, RP * rc, st)));
     dim3 g3((n + 127) / 128, RP * rc, 3);
     fd_scatter_kernel<T><<<g3, 128, 0, st>>>(sd, buf[0][3], buf[1][3], buf[2][3], pb->d_wrow, pb->d_wcol,
                                              static_cast<const T*>(pb->d_wval), n, n1, RP, static_cast<T*>(v->U[0]),

@@ -120,6 +120,10 @@ static std::atomic<int> g_expsum_kind{1};
 int expsum_kind() { return g_expsum_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_eig_kind{1};
 int eig_kind() { return g_eig_kind.load(std::memory_order_relaxed); }
+static std::atomic<int> g_dst_kind{1};
+int dst_kind() { return g_dst_kind.load(std::memory_order_relaxed); }
+static std::atomic<int> g_qr_kind{1};
+int qr_kind() { return g_qr_kind.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
@@ -133,6 +137,14 @@ extern "C" int tpcg_set_option(int key, long long value) {
     }
     if (key == TPCG_OPT_EIG && (value == 0 || value == 1)) {
         tpcg::g_eig_kind.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_DST && (value == 0 || value == 1)) {
+        tpcg::g_dst_kind.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_QR && (value == 0 || value == 1)) {
+        tpcg::g_qr_kind.store((int)value);
         return TPCG_OK;
     }
     tpcg::set_error("tpcg_set_option: unknown key or value out of range");

@@ -31,7 +31,7 @@ template <typename T>
 __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* plan, GemmArgs* ga, int n,
                                   int cap, double eps_host, const double* eps_dev, void* Rq0, void* Rq1,
                                   void* Rq2, const void* U0, const void* U1, const void* U2, T* T1, T* Wm,
-                                  int* counts, long long t1cap, double* prof) {
+                                  int* counts, long long t1cap, double* prof, int strict_mode, int qr_below) {
     if (threadIdx.x != 0) return;
     RoundPlan p;
     p.n = n;
@@ -40,8 +40,10 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
     const void* U[3] = {U0, U1, U2};
     for (int t = 0; t < 3; ++t) {
         p.k[t] = d->rank[t];
-        p.useQ[t] = (p.k[t] < n) ? 1 : 0;
-        p.kp[t] = p.k[t] < n ? p.k[t] : n;
+        // any orthonormal Q_t spanning the columns of Y_t serves Alg. 1 exactly; Q_t = I (R_t = Y_t, Z of size n
+        // in mode t) avoids the QR, which only pays when it shrinks mode t well below n (k_t < qr_below)
+        p.useQ[t] = (p.k[t] < qr_below) ? 1 : 0;
+        p.kp[t] = p.useQ[t] ? p.k[t] : n;
         p.Rp[t] = p.useQ[t] ? (const void*)Rq[t] : U[t];
         p.ldR[t] = n;
         p.s[t] = 0;
@@ -54,6 +56,9 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
     p.budget = 0.0;
     p.abs2 = 0.0;
     p.status = 0;
+    // below eps ~ 1e-7 the budget eps^2 ||Z||^2 / 3 is under what an FP64 Gram resolves (the Gram squares the
+    // singular values): the rule then keeps every direction it cannot certify as small enough
+    p.strict = strict_mode >= 0 ? strict_mode : (p.eps < 1e-7 ? 1 : 0);
     p.kz3 = p.k[2];
     p.nsplit = 0;
     const int kp1 = p.kp[0], kp2 = p.kp[1];
@@ -382,7 +387,8 @@ __global__ void final_copy_kernel(const RoundPlan* __restrict__ plan, const T* S
 // --------------------------------------------------------------------------------------------------
 // Alg. 1 steps 1-2 (planner, QR of the factors, Z formation) into c->Z0 and c->plan.
 template <typename T>
-int round_stage12(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rc, cudaStream_t st) {
+int round_stage12(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rc, cudaStream_t st,
+                  int strict_mode = -1) {
     const int n = c->n;
     GemmArgs* ga = c->gargs;
     int* counts = reinterpret_cast<int*>(c->scal + 200);   // 8 ints of scratch in the scalar area
@@ -391,7 +397,8 @@ int round_stage12(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, in
     plan_round_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(y->desc), c->plan, ga, n, rc, eps, eps_dev,
                                            c->Rq[0], c->Rq[1], c->Rq[2], y->U[0], y->U[1], y->U[2],
                                            static_cast<T*>(c->T1), static_cast<T*>(c->Wm), counts,
-                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev());
+                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev(), strict_mode,
+                                           qr_kind() == 1 ? (n + 1) / 2 : n);
     TPCG_CHECK_LAUNCH();
     set_c_kernel<<<1, 32, 0, st>>>(ga + 2 * TPCG_MAX_BLOCKS, Z0);
     TPCG_CHECK_LAUNCH();
@@ -482,10 +489,10 @@ int round_stage34(tpcg_ctx c, tucker_t* y, double* info_dev, cudaStream_t st) {
 
 template <typename T>
 int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int cap, double* info_dev,
-               cudaStream_t st) {
+               cudaStream_t st, int strict_mode) {
     const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
     prof_begin(PK_ROUND, st);
-    TPCG_TRY(round_stage12<T>(c, y, eps, eps_dev, rc, st));
+    TPCG_TRY(round_stage12<T>(c, y, eps, eps_dev, rc, st, strict_mode));
     TPCG_TRY(round_stage34<T>(c, y, info_dev, st));
     prof_end(PK_ROUND, st);
     return TPCG_OK;
@@ -602,7 +609,7 @@ int tensor_norm2(tpcg_ctx c, tucker_t* y, double* out_dev, cudaStream_t st) {
 template int tensor_norm2<double>(tpcg_ctx, tucker_t*, double*, cudaStream_t);
 template int tensor_norm2<float>(tpcg_ctx, tucker_t*, double*, cudaStream_t);
 
-template int round_impl<double>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t);
-template int round_impl<float>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t);
+template int round_impl<double>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t, int);
+template int round_impl<float>(tpcg_ctx, tucker_t*, double, const double*, int, double*, cudaStream_t, int);
 
 }  // namespace tpcg

@@ -41,7 +41,9 @@ def test_results_same_alone_and_in_the_mix(mods, dtype_name):
     for a, b in zip(alone, mix):
         assert a.request == b.request
         assert a.status == b.status == 0
-        assert b.true_rel_res <= 1e-6
+        # the mixed form stops on the true FP64 residual; FP64 Alg. 5 stops on the truncated residual, which
+        # the true one may exceed by the last truncations (eta_k of eq. rel_tol_iterates)
+        assert b.true_rel_res <= (1e-6 if dtype == lib.MIXED else 2e-6)
         assert (a.iters, a.outer_iters, a.rank) == (b.iters, b.outer_iters, b.rank)
         assert rel(tucker.full((b.core, b.factors)), tucker.full((a.core, a.factors))) < 1e-13
     # in the mix requests overlapped: some were admitted before an earlier one had finished
