@@ -62,8 +62,6 @@ def parse():
     ap.add_argument("--eig", type=int, default=1, choices=[0, 1],
                     help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
     ap.add_argument("--dst", type=int, default=1, choices=[0, 1], help="FD sine transforms: 1 FFT, 0 dense")
-    ap.add_argument("--qr", type=int, default=1, choices=[0, 1],
-                    help="Alg. 1 step 1: 1 QR only below n/2 columns, 0 QR whenever k < n")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
     ap.add_argument("--serve", type=float, default=0.0,
                     help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
@@ -423,7 +421,6 @@ def run_gpu(args):
     lib.check(L.tpcg_set_option(lib.OPT_GEMM_CTAS_PER_SM, args.gemm_ctas_per_sm), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_EIG, args.eig), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_DST, args.dst), "tpcg_set_option")
-    lib.check(L.tpcg_set_option(lib.OPT_QR, args.qr), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     main = torch.cuda.current_stream()
 
@@ -489,7 +486,6 @@ def run_gpu(args):
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
                       "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig, "dst": args.dst,
-                      "qr": args.qr,
                       "refine_keep": args.refine_keep,
                       "seeds": f"{seeds[0]}..{seeds[-1]} on rank 0, disjoint ranges per rank (amp from seed)",
                       "tol": TOL, "rank_cap": rc,

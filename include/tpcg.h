@@ -304,10 +304,10 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   O(n1 log n1) per column, by Bluestein's chirp-z identity for any n1 <= 1024 (power-of-two FFTs of size
  *   >= 2 n1 - 1 in shared memory); 0 the dense n1 x n1 product with the stored sine matrix. */
 #define TPCG_OPT_DST 4
-/*   TPCG_OPT_QR: when Alg. 1 step 1 factors Y_t = Q_t R_t.  Any orthonormal Q_t whose span contains the columns of
- *   Y_t gives the same truncation, Q_t = I (R_t = Y_t) included; the QR only shrinks Z from n to k_t in mode t.
- *   1 (default): QR only when k_t < n / 2, else Q_t = I; 0: QR whenever k_t < n. */
-#define TPCG_OPT_QR 5
+/*   TPCG_OPT_TC: where the FP32 contractions (Alg. 1 Z formation, mode Grams, projections and factor updates, the
+ *   scalar products) run: 1 on the tensor cores (tcgen05, 3xTF32 products with FP32 accumulation in tensor
+ *   memory), 0 (default) on the FP32 SIMT units.  FP64 contractions always use the FP64 units. */
+#define TPCG_OPT_TC 5
 int tpcg_set_option(int key, long long value);
 
 /* Best exponential sum s_R(lambda) = sum_j omega_j exp(-alpha_j lambda) for 1/lambda on [1, M] in the maximum

@@ -17,7 +17,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpcg_gb300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["round.cu", "eig.cu", "ops.cu", "api.cu", "elast.cu", "prof.cu", "dst.cu"]
+CU_SOURCES = ["round.cu", "eig.cu", "ops.cu", "api.cu", "elast.cu", "prof.cu", "dst.cu", "gemm_tc.cu"]
 CXX_SOURCES = ["setup.cpp", "expsum.cpp"]
 
 

@@ -236,6 +236,7 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
     }
     // per-device launch attributes are settled here, outside any stream capture
     TPCG_TRY(eig_prepare());
+    TPCG_TRY(tc_prepare());
     (void)sm_count();
     tpcg_ctx c = new tpcg_ctx_s();
     c->lo = nullptr;

@@ -188,10 +188,21 @@ inline int sm_count() {
     return cache[dev];
 }
 
+// FP32 groups on the tensor cores (gemm_tc.cu): same arguments, 3xTF32 products with FP32 accumulation
+template <bool TA, bool TB>
+int launch_gemm_tc(const GemmArgs* args, const int* count_dev, int ngroups_max, int bmax, int Mmax, int Nmax,
+                   cudaStream_t st);
+int tc_kind();        // TPCG_OPT_TC: 1 FP32 contractions on the tensor cores, 0 on the FP32 SIMT units
+int tc_prepare();     // shared-memory opt-in of the tensor-core kernels on the current device
+int tc_take_error();  // nonzero once a tensor-core kernel abandoned a wait (the flag is cleared)
+
 template <typename T, bool TA, bool TB>
 inline int launch_gemm(const GemmArgs* args, const int* count_dev, int ngroups_max, int bmax, int Mmax, int Nmax,
                        cudaStream_t st) {
     if (ngroups_max <= 0 || bmax <= 0 || Mmax <= 0 || Nmax <= 0) return TPCG_OK;
+    if constexpr (sizeof(T) == 4) {
+        if (tc_kind() == 1) return launch_gemm_tc<TA, TB>(args, count_dev, ngroups_max, bmax, Mmax, Nmax, st);
+    }
     const long long zmax = (long long)ngroups_max * bmax;
     // the kernel strides over z, so the grid can be capped at a CTA budget per SM: argument lists sized for
     // the worst case (most groups empty at run time) then do not flood the CTA scheduler

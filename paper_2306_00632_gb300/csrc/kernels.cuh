@@ -58,7 +58,6 @@ template <typename T>
 int launch_chirp(tpcg_problem pb, int kind, const TuckerDesc* sd, int mult, int rp_guard, int vcap, int maxcols,
                  const T* const* X, T* const* Y, int ldx, int ldy, cudaStream_t st);
 int dst_kind();   // TPCG_OPT_DST: 1 FFT sine transforms, 0 dense sine matrix
-int qr_kind();    // TPCG_OPT_QR: 1 QR of a factor only below n/2 columns, 0 whenever it has fewer than n
 
 int set_plain(tucker_t* t, int r1, int r2, int r3, cudaStream_t st);
 int set_zero(tucker_t* t, cudaStream_t st);

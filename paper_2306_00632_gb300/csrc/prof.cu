@@ -122,8 +122,8 @@ static std::atomic<int> g_eig_kind{1};
 int eig_kind() { return g_eig_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_dst_kind{1};
 int dst_kind() { return g_dst_kind.load(std::memory_order_relaxed); }
-static std::atomic<int> g_qr_kind{1};
-int qr_kind() { return g_qr_kind.load(std::memory_order_relaxed); }
+static std::atomic<int> g_tc_kind{0};
+int tc_kind() { return g_tc_kind.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
@@ -143,8 +143,8 @@ extern "C" int tpcg_set_option(int key, long long value) {
         tpcg::g_dst_kind.store((int)value);
         return TPCG_OK;
     }
-    if (key == TPCG_OPT_QR && (value == 0 || value == 1)) {
-        tpcg::g_qr_kind.store((int)value);
+    if (key == TPCG_OPT_TC && (value == 0 || value == 1)) {
+        tpcg::g_tc_kind.store((int)value);
         return TPCG_OK;
     }
     tpcg::set_error("tpcg_set_option: unknown key or value out of range");

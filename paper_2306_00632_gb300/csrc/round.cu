@@ -31,7 +31,7 @@ template <typename T>
 __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* plan, GemmArgs* ga, int n,
                                   int cap, double eps_host, const double* eps_dev, void* Rq0, void* Rq1,
                                   void* Rq2, const void* U0, const void* U1, const void* U2, T* T1, T* Wm,
-                                  int* counts, long long t1cap, double* prof, int strict_mode, int qr_below) {
+                                  int* counts, long long t1cap, double* prof, int strict_mode) {
     if (threadIdx.x != 0) return;
     RoundPlan p;
     p.n = n;
@@ -40,10 +40,8 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
     const void* U[3] = {U0, U1, U2};
     for (int t = 0; t < 3; ++t) {
         p.k[t] = d->rank[t];
-        // any orthonormal Q_t spanning the columns of Y_t serves Alg. 1 exactly; Q_t = I (R_t = Y_t, Z of size n
-        // in mode t) avoids the QR, which only pays when it shrinks mode t well below n (k_t < qr_below)
-        p.useQ[t] = (p.k[t] < qr_below) ? 1 : 0;
-        p.kp[t] = p.useQ[t] ? p.k[t] : n;
+        p.useQ[t] = (p.k[t] < n) ? 1 : 0;
+        p.kp[t] = p.k[t] < n ? p.k[t] : n;
         p.Rp[t] = p.useQ[t] ? (const void*)Rq[t] : U[t];
         p.ldR[t] = n;
         p.s[t] = 0;
@@ -397,8 +395,7 @@ int round_stage12(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, in
     plan_round_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(y->desc), c->plan, ga, n, rc, eps, eps_dev,
                                            c->Rq[0], c->Rq[1], c->Rq[2], y->U[0], y->U[1], y->U[2],
                                            static_cast<T*>(c->T1), static_cast<T*>(c->Wm), counts,
-                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev(), strict_mode,
-                                           qr_kind() == 1 ? (n + 1) / 2 : n);
+                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev(), strict_mode);
     TPCG_CHECK_LAUNCH();
     set_c_kernel<<<1, 32, 0, st>>>(ga + 2 * TPCG_MAX_BLOCKS, Z0);
     TPCG_CHECK_LAUNCH();

@@ -1,5 +1,5 @@
-"""The FFT sine transforms of the preconditioner (Alg. 4 with App. B, chirp-z FFTs of any length) and the QR
-choice of Alg. 1 step 1, each against the oracle and against the library's other path.
+"""The FFT sine transforms of the preconditioner (Alg. 4 with App. B, chirp-z FFTs of any length) against the
+oracle and against the library's dense sine product.
 
 n1 (the sine-transform length) covers DST-I (odd p, length n1 = n - p + 1) and DST-II/III (even p, n1 =
 n - p + 2) with FFT sizes 32 to 1024, including lengths whose doubled DFT size has a large prime factor
@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle import rounding, tucker
+from oracle import tucker
 from tests.gpu_helpers import gpu_problem, oracle_problem, rel
 
 pytestmark = pytest.mark.gpu
@@ -25,7 +25,6 @@ def api():
     lib.load()
     yield a
     a.set_option(lib.OPT_DST, 1)
-    a.set_option(lib.OPT_QR, 1)
 
 
 def _fd(api, pb, ctx, s, cap, kind):
@@ -68,23 +67,3 @@ def test_fft_sine_transforms_fp32_and_n512(api):
         _, fac_d = _fd(api, pb, ctx, s, cap, 0)
         for t in range(3):
             assert rel(fac_f[t], fac_d[t]) < tol
-
-
-def test_round_without_qr_equals_round_with_qr(api):
-    # Alg. 1 with Q_t = I for a factor of n/2 <= k < n columns equals Alg. 1 with its QR (exact identity)
-    from paper_2306_00632_gb300 import lib
-    n = 40
-    Y = synth.random_tucker((n, n, n), (25, 30, 22), seed=31, decay=0.6)
-    out = []
-    for qr in (0, 1):
-        api.set_option(lib.OPT_QR, qr)
-        y = api.Tucker.from_numpy(Y[0], Y[1], cap=32, core_cap=32 ** 3)
-        ctx = api.Ctx(n, 64, 32)
-        api.tucker_round(ctx, y, 1e-6)
-        out.append(y.to_numpy())
-    api.set_option(lib.OPT_QR, 1)
-    assert out[0][0].shape == out[1][0].shape
-    assert rel(tucker.full(out[0]), tucker.full(out[1])) < 1e-12
-    G0, U0 = rounding.t_rel(Y, 1e-6)
-    assert out[1][0].shape == G0.shape
-    assert rel(tucker.full(out[1]), tucker.full((G0, U0))) < 1e-10
