@@ -62,10 +62,15 @@ def parse():
     ap.add_argument("--eig", type=int, default=1, choices=[0, 1],
                     help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
     ap.add_argument("--dst", type=int, default=1, choices=[0, 1], help="FD sine transforms: 1 FFT, 0 dense")
+    ap.add_argument("--tc", type=int, default=-1, choices=[-1, 0, 1],
+                    help="FP32 contractions: 1 tensor cores (tcgen05), 0 SIMT, -1 the library default")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
     ap.add_argument("--serve", type=float, default=0.0,
                     help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
     ap.add_argument("--requests", type=int, default=48, help="requests in the --serve stream")
+    ap.add_argument("--mix", type=int, default=0,
+                    help="instead of the batch benchmark: this many independent solves of uneven n, p, rank cap and "
+                         "geometry (n in {32..256}, p in {2,3,4}, caps 20-60), all submitted at once")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement beside the mixed one")
@@ -421,6 +426,8 @@ def run_gpu(args):
     lib.check(L.tpcg_set_option(lib.OPT_GEMM_CTAS_PER_SM, args.gemm_ctas_per_sm), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_EIG, args.eig), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_DST, args.dst), "tpcg_set_option")
+    if args.tc >= 0:
+        lib.check(L.tpcg_set_option(lib.OPT_TC, args.tc), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
     main = torch.cuda.current_stream()
 
@@ -485,7 +492,7 @@ def run_gpu(args):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
-                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig, "dst": args.dst,
+                      "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig, "dst": args.dst, "tc": args.tc,
                       "refine_keep": args.refine_keep,
                       "seeds": f"{seeds[0]}..{seeds[-1]} on rank 0, disjoint ranges per rank (amp from seed)",
                       "tol": TOL, "rank_cap": rc,
@@ -617,10 +624,50 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mix(args):
+    """Many independent solves of uneven size at once: the mixed form (FP32 inner solves, FP64 refinement)
+    on seeded twisted annuli with n in {32, 64, 96, 128, 192, 256}, p in {2, 3, 4}, amplitude in [0, 0.3] and
+    rank caps 20-60, all submitted at t = 0 to the continuous-batching server (at most 32 in flight, admitted by
+    device memory).  Operators are built before the clock starts.  Prints solves/s and the per-result status."""
+    import torch
+    from paper_2306_00632_gb300 import lib, serve
+    lib.load()
+    mix = synth.batch_mix(args.mix, seed0=SEED)
+    reqs = [serve.Request(lib.GEOM_TWIST, pr.amp, pr.degree, pr.n, cap, tol=TOL, dtype=lib.MIXED, arrival=0.0)
+            for pr, cap in mix]
+    free, _ = torch.cuda.mem_get_info()
+    srv = serve.Server(int(free * 0.7), max_slots=32)
+    t0 = time.perf_counter()
+    srv.prepare(reqs, workers=min(16, os.cpu_count() or 8))
+    setup_s = time.perf_counter() - t0
+    srv.run(reqs[:8])   # warm-up: kernels loaded, per-device attributes set
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    ok = [r for r in res if r.status == 0 and r.true_rel_res <= TOL]
+    by_n = {}
+    for r in res:
+        d = by_n.setdefault(str(r.request.n), {"solves": 0, "converged": 0, "iters": []})
+        d["solves"] += 1
+        d["converged"] += int(r.status == 0 and r.true_rel_res <= TOL)
+        d["iters"].append(r.iters)
+    line = {"metric": "independent mixed-precision TPCG solves/sec to rel-residual 1e-6 (uneven n, p, rank cap)",
+            "value": len(res) / wall, "unit": "solves/s", "solves": len(res), "converged": len(ok), "wall_s": wall,
+            "setup_s_untimed": setup_s, "max_in_flight": 32, "dtype": "mixed", "data": "synthetic",
+            "config": {"workload": "twisted quarter annuli, n in {32,64,96,128,192,256}, p in {2,3,4}, amp in "
+                                   "[0,0.3], rank caps 20-60", "seeds": f"{SEED}..{SEED + args.mix - 1}", "tol": TOL},
+            "latency_s": serve.percentiles(res), "max_true_rel_res": max(r.true_rel_res for r in res),
+            "by_n": by_n}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mix > 0:
+        run_mix(args)
     elif args.serve > 0:
         run_serve(args)
     else:

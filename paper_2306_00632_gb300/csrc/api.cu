@@ -851,9 +851,13 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     tucker_t* big = &c->tens[tbase + 5];
     tucker_t* big2 = &c->tens[tbase + 6];
     double* eta = sc + S_ETA;
+    // the FP64 rule's strict mode (reading R23) serves solves whose tolerance is below what the Gram resolves;
+    // at tol >= 1e-8 Alg. 2's tolerance still falls to eps_min (about tol ||f~|| / 10), where strict mode would
+    // keep Gram noise in x up to the rank cap, so those solves use the plain rule
+    const int strict = prm->tol < 1e-8 ? -1 : 0;
     auto round_to = [&](tucker_t*& dst, const double* eps_dev) -> int {
         // round `big` in place, then make it the new `dst` (swap buffers)
-        TPCG_TRY(round_cached<T>(c, big, eps_dev, rc, s));
+        TPCG_TRY(round_cached<T>(c, big, eps_dev, rc, s, strict));
         std::swap(dst, big);
         return TPCG_OK;
     };
@@ -922,7 +926,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         TPCG_TRY(axpby_impl<T>(1.0, nullptr, x, 0.0, sc + S_OMEGA, p, big, nullptr, s));
         for (int trial = 0;; ++trial) {
             TPCG_TRY(copy_tensor_impl<T>(big, big2, c->n, c->max_cols, s));
-            TPCG_TRY(round_cached<T>(c, big2, sc + S_EPS, rc, s));
+            TPCG_TRY(round_cached<T>(c, big2, sc + S_EPS, rc, s, strict));
             TPCG_TRY(dot_cached<T>(c, p, big2, sc + S_PXN, s));
             launch_scalar(OP_DT, sc, dprm, s);
             ++trials_total;

@@ -157,6 +157,7 @@ struct tpcg_ctx_s {
         const void* U0;
         const double* eps_dev;
         int rc;
+        int strict;
         cudaGraphExec_t exec;
         long long nkern;
     };

@@ -111,7 +111,7 @@ static int elast_solve_impl(tpcg_elast e, tpcg_ctx c, const tpcg_params* prm, tu
         for (int i = 0; i < 3; ++i) std::swap(a[i], b[i]);
     };
     auto bround = [&](tucker_t** y, const double* eps_dev) -> int {
-        for (int i = 0; i < 3; ++i) TPCG_TRY(round_cached<T>(c, y[i], eps_dev, rc, s));
+        for (int i = 0; i < 3; ++i) TPCG_TRY(round_cached<T>(c, y[i], eps_dev, rc, s, prm->tol < 1e-8 ? -1 : 0));
         return TPCG_OK;
     };
     auto bcopy = [&](tucker_t** a, tucker_t** b) -> int {

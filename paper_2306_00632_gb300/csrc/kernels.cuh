@@ -14,7 +14,7 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
 // FP64 Z formation, FP32 ST-HOSVD into out32; the discarded energy may also reach abs_tol^2 (absolute norm floor)
 // round_impl(c, y, 0, eps_dev, cap) replayed from a per-context CUDA graph (captured on first use)
 template <typename T>
-int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st);
+int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st, int strict_mode = -1);
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
                 double abs_tol, double* info_dev, cudaStream_t st);
 // ||y||^2 of any (block) tensor by the Z formation of Alg. 1

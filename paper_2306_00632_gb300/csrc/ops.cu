@@ -370,7 +370,7 @@ int dot_cached(tpcg_ctx c, const tucker_t* x, const tucker_t* y, double* out_dev
         set_error(std::string("dot_cached: graph instantiation failed: ") + cudaGetErrorString(ei));
         return TPCG_E_CUDA;
     }
-    c->rgraphs.push_back({x->desc, y->desc, out_dev, -1, exec, t_launches - k0});
+    c->rgraphs.push_back({x->desc, y->desc, out_dev, -1, 0, exec, t_launches - k0});
     TPCG_CUDA(cudaGraphLaunch(exec, st));
     return TPCG_OK;
 }

@@ -500,19 +500,19 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
 // launch sequence of a truncation does not depend on ranks (all sizes are read on the device), so the
 // replay is exact.  Falls back to direct launches while profiling or on the legacy default stream.
 template <typename T>
-int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st) {
+int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st, int strict_mode) {
     const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
     if (prof_on() || !eps_dev || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
-        return round_impl<T>(c, y, 0.0, eps_dev, cap, nullptr, st);
+        return round_impl<T>(c, y, 0.0, eps_dev, cap, nullptr, st, strict_mode);
     for (const auto& g : c->rgraphs)
-        if (g.desc == y->desc && g.U0 == y->U[0] && g.eps_dev == eps_dev && g.rc == rc) {
+        if (g.desc == y->desc && g.U0 == y->U[0] && g.eps_dev == eps_dev && g.rc == rc && g.strict == strict_mode) {
             TPCG_CUDA(cudaGraphLaunch(g.exec, st));
             g_launches.fetch_add(g.nkern, std::memory_order_relaxed);
             return TPCG_OK;
         }
     const long long k0 = t_launches;
     TPCG_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const int s = round_impl<T>(c, y, 0.0, eps_dev, rc, nullptr, st);
+    const int s = round_impl<T>(c, y, 0.0, eps_dev, rc, nullptr, st, strict_mode);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(st, &graph);
     if (s != TPCG_OK || e != cudaSuccess || !graph) {
@@ -530,12 +530,12 @@ int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaSt
         set_error(std::string("round_cached: graph instantiation failed: ") + cudaGetErrorString(ei));
         return TPCG_E_CUDA;
     }
-    c->rgraphs.push_back({y->desc, y->U[0], eps_dev, rc, exec, t_launches - k0});
+    c->rgraphs.push_back({y->desc, y->U[0], eps_dev, rc, strict_mode, exec, t_launches - k0});
     TPCG_CUDA(cudaGraphLaunch(exec, st));   // the kernels counted during capture run now
     return TPCG_OK;
 }
-template int round_cached<double>(tpcg_ctx, tucker_t*, const double*, int, cudaStream_t);
-template int round_cached<float>(tpcg_ctx, tucker_t*, const double*, int, cudaStream_t);
+template int round_cached<double>(tpcg_ctx, tucker_t*, const double*, int, cudaStream_t, int);
+template int round_cached<float>(tpcg_ctx, tucker_t*, const double*, int, cudaStream_t, int);
 
 // Mixed rounding: Alg. 1 steps 1-2 in FP64 (the Z formation carries the cancellation of a residual), then
 // steps 3-4 in FP32 on the rounded Z.  y64 is an FP64 (block) tensor, out32 receives an FP32 plain tensor.

@@ -73,16 +73,22 @@ class Server:
         self._running = 0
 
     # ------------------------------------------------------------------ per-request resources
+    @staticmethod
+    def _key(r: Request):
+        return (r.problem, r.kind, float(r.amp), r.degree, r.n, r.dtype, r.lame_lambda, r.lame_mu, tuple(r.force))
+
+    @staticmethod
+    def _build(r: Request):
+        if r.problem == "elasticity":
+            return api.tpcg_elast_setup(r.kind, r.amp, r.degree, r.n, r.lame_lambda, r.lame_mu, r.force, r.dtype)
+        return api.tpcg_setup(r.kind, r.amp, r.degree, r.n, r.dtype)
+
     def problem(self, r: Request):
-        key = (r.problem, r.kind, float(r.amp), r.degree, r.n, r.dtype, r.lame_lambda, r.lame_mu, tuple(r.force))
         with self._plock:
-            pb = self._problems.get(key)
+            pb = self._problems.get(self._key(r))
             if pb is None:
-                if r.problem == "elasticity":
-                    pb = api.tpcg_elast_setup(r.kind, r.amp, r.degree, r.n, r.lame_lambda, r.lame_mu, r.force, r.dtype)
-                else:
-                    pb = api.tpcg_setup(r.kind, r.amp, r.degree, r.n, r.dtype)
-                self._problems[key] = pb
+                pb = self._build(r)
+                self._problems[self._key(r)] = pb
             return pb
 
     @staticmethod
@@ -135,6 +141,21 @@ class Server:
                 self._used -= need
                 self._running -= 1
                 self._cv.notify_all()
+
+    def prepare(self, requests, workers: int = 8):
+        """Build the operators of `requests` on `workers` host threads (the host setup of App. A and B is
+        independent per problem); later calls of problem() find them in the cache."""
+        from concurrent.futures import ThreadPoolExecutor
+        todo = {}
+        with self._plock:
+            for r in requests:
+                if self._key(r) not in self._problems:
+                    todo.setdefault(self._key(r), r)
+        with ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
+            built = list(ex.map(self._build, todo.values()))
+        with self._plock:
+            for key, pb in zip(todo.keys(), built):
+                self._problems.setdefault(key, pb)
 
     def run(self, requests):
         """Serve `requests` (sorted by arrival time) and return their results in the same order."""
