@@ -56,16 +56,22 @@ def tucker_of_samples(T: np.ndarray, eps: float):
     return core, S
 
 
-def operator_terms(kind: str, amp: float, n: int, p: int, eps: float = 1e-8):
+def operator_terms(kind: str, amp: float, n: int, p: int, eps: float = 1e-8, trial: str = "dirichlet"):
     """Kronecker-sum operator: list of (w, [K1, K2, K3]) with dense n x n matrices.
 
     A~ = sum_j w_j K3^j (x) K2^j (x) K1^j acts on vec(X) with mode 1 fastest (Sec. 2.3).
+    With trial="full" the trial functions run over the whole B-spline basis (boundary functions included):
+    the matrices are n x (n + 2), the operator between the interior test functions and all trial functions
+    that the non-homogeneous Dirichlet problem of the Remark in Sec. 3 needs.
     """
     n_el = n - p + 2
     Q, _ = sample(kind, amp)
     xs, ws = bspline.quadrature(n_el, p)
     B0 = bspline.dirichlet_basis(n_el, p, xs, 0)
     B1 = bspline.dirichlet_basis(n_el, p, xs, 1)
+    knots = bspline.open_uniform_knots(n_el, p)
+    T0 = bspline.basis(knots, p, xs, 0) if trial == "full" else B0
+    T1 = bspline.basis(knots, p, xs, 1) if trial == "full" else B1
     norms = np.array([[np.linalg.norm(Q[..., k, l]) for l in range(3)] for k in range(3)])
     terms = []
     for k in range(3):
@@ -88,7 +94,7 @@ def operator_terms(kind: str, amp: float, n: int, p: int, eps: float = 1e-8):
                     mats = []
                     for t in range(3):
                         Bi = B1 if t == l else B0     # delta^{(l,t)} acts on the test function b_i
-                        Bj = B1 if t == k else B0     # delta^{(k,t)} acts on the trial function b_j
+                        Bj = T1 if t == k else T0     # delta^{(k,t)} acts on the trial function b_j
                         mats.append((Bi * (ws * funcs[t])) @ Bj.T)
                     terms.append((1.0, mats))
     return terms
