@@ -264,8 +264,8 @@ def _roofline(prof, dt_name, lib, step_ms_total):
     alu = {"f64": bf16 * 1.25 / 2250.0, "f32": bf16 * 75.0 / 2250.0}
     classes = ["zgemm", "zblk", "gram", "eig", "proj", "qr", "apply", "fd"]
     # DRAM bytes per launch of the FP32 eigensolver from one ncu capture of this workload (dram__bytes_read.sum +
-    # dram__bytes_write.sum, mean of 3 launches); other kernels: no capture, traffic null
-    ncu_traffic = {"eig": 105216.0} if dt_name == "mixed" else {}
+    # dram__bytes_write.sum, mean of 2 launches of hestenes_eig_kernel); other kernels: no capture, traffic null
+    ncu_traffic = {"eig": 118656.0} if dt_name == "mixed" else {}
     dom = max(classes, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     per_launch_ms = d["ms"] / max(d["launches"], 1)
