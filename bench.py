@@ -71,6 +71,10 @@ def parse():
     ap.add_argument("--mix", type=int, default=0,
                     help="instead of the batch benchmark: this many independent solves of uneven n, p, rank cap and "
                          "geometry (n in {32..256}, p in {2,3,4}, caps 20-60), all submitted at once")
+    ap.add_argument("--large", type=int, default=0, help="n of the large configuration (e.g. 512); 0: off")
+    ap.add_argument("--large-cap", type=int, default=80, help="large configuration: rank cap")
+    ap.add_argument("--large-concurrent", type=int, default=2, help="large configuration: solves at once")
+    ap.add_argument("--large-fp64", action="store_true", help="large configuration: also the FP64 form")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement beside the mixed one")
@@ -318,7 +322,7 @@ def _norms(core, U, w, bands, p, mass):
         Q.append(q)
         Z = np.moveaxis(np.tensordot(r, Z, axes=(1, t)), 0, t)
     l2c = float(np.linalg.norm(Z))
-    l2 = _quad(Z, [q.T @ mass @ q for q in Q])
+    l2 = _quad(Z, [q.T @ mass @ q for q in Q]) if mass is not None else 0.0
     en = 0.0
     for j in range(len(w)):
         en += w[j] * _quad(Z, [Q[t].T @ _band_matrix_product(bands, j, t, Q[t], p) for t in range(3)])
@@ -338,13 +342,20 @@ def solution_error(X, ex, info, ref):
     G = np.zeros(tuple(a + b for a, b in zip(r1, r2)))
     G[:r1[0], :r1[1], :r1[2]] = core_x
     G[r1[0]:, r1[1]:, r1[2]:] = -core_r
-    e = _norms(G, [np.hstack([Ux[t], Ur[t]]) for t in range(3)], w, bands, p, ref["mass"])
-    r = _norms(core_r, Ur, w, bands, p, ref["mass"])
-    return {"rel_l2_coeff": e[0] / r[0], "rel_l2_param": e[1] / r[1], "rel_energy": e[2] / r[2],
-            "reference": f"oracle FP64 Alg. 5 at tol {ref['tol_ref']:g} (stored), seed {SEED}"}
+    mass = ref.get("mass")
+    e = _norms(G, [np.hstack([Ux[t], Ur[t]]) for t in range(3)], w, bands, p, mass)
+    r = _norms(core_r, Ur, w, bands, p, mass)
+    out = {"rel_l2_coeff": e[0] / r[0], "rel_energy": e[2] / r[2],
+           "reference": ref.get("label", f"oracle FP64 Alg. 5 at tol {ref.get('tol_ref', 0):g} (stored), seed {SEED}")}
+    if mass is not None:
+        out["rel_l2_param"] = e[1] / r[1]
+    return out
 
 
 # ------------------------------------------------------------------------------------------- FP64 arm
+FP64_STOP = 0.9
+
+
 def fp64_arm(api, lib, pbs, rc, args, flush):
     """The plain FP64 form on the same problems: a single solve alone (the comparison arm), then
     args.fp64_concurrent solves at once; FP64 problems are re-created from the setup's exported tables."""
@@ -359,7 +370,10 @@ def fp64_arm(api, lib, pbs, rc, args, flush):
     pb64 = [api.problem_from_export(ex, info, dtype=lib.F64, pinned=False) for ex, info in exs]
     ctx64 = [_ctx_for(api, p.info, lib.F64, rc) for p in pb64]
     x64 = [api.Tucker(N_DOF, cap=rc, core_cap=rc ** 3, dtype=lib.F64) for _ in range(B)]
-    kw = dict(tol=TOL, rank_cap=rc)
+    # FP64 Alg. 5 stops on the truncated residual, which the true one may exceed by the last truncations
+    # (eta_k): the stop tolerance is set 10% below the target so that every solve reaches a true residual
+    # <= TOL, the metric's definition
+    kw = dict(tol=FP64_STOP * TOL, rank_cap=rc)
     api.tpcg_solve(pb64[0], ctx64[0], x64[0], **kw)     # warm-up (graphs captured)
     torch.cuda.synchronize()
     lat, sts = [], []
@@ -371,7 +385,7 @@ def fp64_arm(api, lib, pbs, rc, args, flush):
         b.record(main)
         torch.cuda.synchronize()
         lat.append(a.elapsed_time(b))
-    out = {"single_solve_ms": float(np.median(lat)), "single_solves_per_s": 1000.0 / float(np.median(lat)),
+    out = {"stop_tol": kw["tol"], "single_solve_ms": float(np.median(lat)), "single_solves_per_s": 1000.0 / float(np.median(lat)),
            "single_true_rel_res": float(sts[-1].true_rel_res), "single_iters": int(sts[-1].iters),
            "single_status": int(sts[-1].status)}
     x_single = x64[0].to_numpy()
@@ -662,10 +676,115 @@ def run_mix(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args):
+    """The large configuration: one twisted-annulus Poisson problem family at n = args.large dofs per direction
+    (p = 3, rank cap args.large_cap, mixed form: FP32 inner solves with their Grams above 128 reduced by the
+    Rayleigh-Ritz step, FP64 refinement), args.large_concurrent solves at once.  Reports solves/s, a single
+    solve's per-kernel-class times with the roofline fractions of the operator apply (HBM) and of the rounding's
+    contractions (FP32 SIMT, or TF32 tensor cores with --tc 1), and with --large-fp64 the FP64 form's single
+    solve on the same problem and the difference between the two solutions."""
+    import torch
+    from paper_2306_00632_gb300 import api, lib
+    L = lib.load()
+    n, rc, B = args.large, min(args.large_cap, args.large), max(args.large_concurrent, 1)
+    if args.tc >= 0:
+        lib.check(L.tpcg_set_option(lib.OPT_TC, args.tc), "tpcg_set_option")
+    seeds = [SEED + i for i in range(B)]
+    pbs = [api.tpcg_setup(lib.GEOM_TWIST, synth.amp_from_seed(sd), DEGREE, n, lib.MIXED) for sd in seeds]
+    ctxs = [api.Ctx(n, api.max_cols_for(p.info, rc, lib.MIXED), rc, lib.MIXED) for p in pbs]
+    xs = [api.Tucker(n, cap=rc, core_cap=rc ** 3, dtype=lib.MIXED) for _ in range(B)]
+    kw = dict(tol=TOL, rank_cap=rc, inner_tol=args.inner_tol, refine_keep=args.refine_keep)
+    main = torch.cuda.current_stream()
+    api.tpcg_solve(pbs[0], ctxs[0], xs[0], **kw)   # warm-up: graphs captured
+    torch.cuda.synchronize()
+    L.tpcg_profile_reset()
+    L.tpcg_profile_enable(1)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(main)
+    st0 = api.tpcg_solve(pbs[0], ctxs[0], xs[0], **kw)
+    b.record(main)
+    torch.cuda.synchronize()
+    L.tpcg_profile_enable(0)
+    single_ms = a.elapsed_time(b)
+    prof = _profile(L, lib)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    src = "of measured" if peaks else "of fallback"
+    tc_on = args.tc == 1
+    # FP32 contractions: SIMT peak (nominal 75 of 2250 bf16), or TF32 tensor peak (nominal 1125 of 2250) / 3
+    # for the three MMAs of the 3xTF32 split
+    f32_peak = bf16 * (1125.0 / 2250.0 / 3.0 if tc_on else 75.0 / 2250.0)
+    classes = {}
+    for k in ("apply", "fd", "zgemm", "zblk", "gram", "eig", "proj", "qr", "dot", "round"):
+        d = prof[k]
+        row = {"ms": round(d["ms"], 3), "launches": d["launches"]}
+        if d["ms"] > 0 and k in ("apply", "fd"):
+            ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+            row.update({"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm})
+        elif d["ms"] > 0 and k in ("zgemm", "zblk", "gram", "proj", "eig"):
+            ach = d["flops"] / (d["ms"] * 1e-3) / 1e12
+            row.update({"bound": "tensor" if tc_on else "alu", "achieved_tflops": ach, "frac": ach / f32_peak})
+        classes[k] = row
+    # throughput: steps of B concurrent solves
+    def batch():
+        return api.tpcg_solve_batch(pbs, ctxs, xs, [None] * B, **kw)
+    batch()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(main)
+    res = []
+    for _ in range(args.steps):
+        res.append(batch())
+    g1.record(main)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = g0.elapsed_time(g1)
+    codes, sts = res[-1]
+    out = {"metric": f"TPCG solves/sec to rel-residual 1e-6 at n={n}", "value": B * args.steps * 1000.0 / total_ms,
+           "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "ms_per_step": total_ms / args.steps,
+           "higher_is_better": True, "dtype": "mixed", "data": "synthetic",
+           "config": {"workload": f"twisted quarter annulus Poisson, p={DEGREE}, n={n}/direction", "rank_cap": rc,
+                      "solves_per_step": B, "seeds": f"{seeds[0]}..{seeds[-1]}", "tol": TOL, "tc": args.tc,
+                      "R": [p.info.R for p in pbs], "RP": pbs[0].info.RP, "inner_tol": args.inner_tol},
+           "status": [int(c) for c in codes], "true_rel_res": [float(s.true_rel_res) for s in sts],
+           "inner_iters": [int(s.iters) for s in sts], "outer_iters": [int(s.outer_iters) for s in sts],
+           "rank": [list(s.rank) for s in sts],
+           "single": {"ms": single_ms, "iters": int(st0.iters), "true_rel_res": float(st0.true_rel_res)},
+           "kernel_classes_single": classes,
+           "peaks": {"hbm_gbs": hbm, "f32_tflops": f32_peak, "source": src}, "clocks": clk}
+    if args.large_fp64:
+        ex = pbs[0].export()
+        ex["v2u2"] = ex["v2u2"][: pbs[0].info.n * pbs[0].info.n2]
+        pb64 = api.problem_from_export(ex, pbs[0].info, dtype=lib.F64, pinned=False)
+        ctx64 = api.Ctx(n, api.max_cols_for(pb64.info, rc, lib.F64), rc, lib.F64)
+        x64 = api.Tucker(n, cap=rc, core_cap=rc ** 3, dtype=lib.F64)
+        a.record(main)
+        s64 = api.tpcg_solve(pb64, ctx64, x64, tol=FP64_STOP * TOL, rank_cap=rc)
+        b.record(main)
+        torch.cuda.synchronize()
+        X64 = x64.to_numpy()
+        Xm = xs[0].to_numpy()   # problem 0's solution from the last timed step
+        err = solution_error(Xm, ex, pbs[0].info, {"core": X64[0], "U": list(X64[1]),
+                                                  "label": f"FP64 Alg. 5 on the GPU, stop tol {FP64_STOP * TOL:g}"})
+        out["fp64"] = {"single_ms": a.elapsed_time(b), "iters": int(s64.iters), "status": int(s64.status),
+                       "true_rel_res": float(s64.true_rel_res), "rank": list(s64.rank),
+                       "mixed_vs_fp64": err}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.large > 0:
+        run_large(args)
     elif args.mix > 0:
         run_mix(args)
     elif args.serve > 0:

@@ -175,8 +175,14 @@ int tucker_dot_static(const tucker_t* x, const tucker_t* y, double* out_dev, voi
 /* In-place relative truncation, Alg. 1: y <- T_rel(y, eps) with ST-HOSVD split eps^2/3 per mode, ranks
  * clipped to rank_cap (<= 0: the context's cap).  Factors come out orthonormal, so ||y|| = ||core||.
  * If info_dev is non-NULL it receives 6 doubles: ||y||^2 before, the discarded squared norm, the new
- * ranks (3, as doubles) and a flag that is nonzero when the new core did not fit the tensor's core_cap; TPCG_E_RANK_CAP
- * is not raised here (check info). */
+ * ranks (3, as doubles) and a flag: 0 ok, 1 the new core did not fit the tensor's core_cap, 2 the input's
+ * blocks need more Z-formation workspace than the context holds (sum over blocks of r1 min(n, k2) r3 above
+ * max_cols n rank_cap; y is then left with rank 0); TPCG_E_RANK_CAP is not raised here (check info).
+ * Grams of order above 128 are first reduced to the Rayleigh-Ritz matrix Q^T G Q of an orthonormal basis Q of
+ * at most 128 pivoted-Cholesky columns of G (stopped once the Schur complement holds 1% (FP32) or 1e-8 (FP64)
+ * of the mode's budget) in FP32 contexts with n > 128 and in FP64 contexts with n > 256 and rank_cap <= 112:
+ * the error bound of Alg. 1 holds exactly, and the ranks are the exact rule's up to that fraction unless 128
+ * columns do not reach it (such a Gram then keeps at most 128 directions). */
 int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int rank_cap, double* info_dev,
                  void* stream);
 /* v = P~^{-1} s, Alg. 4 steps 5-9: factors [U~ D_(t,1) U~^T S_t, ..., U~ D_(t,RP) U~^T S_t], core
@@ -308,6 +314,12 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   scalar products) run: 1 on the tensor cores (tcgen05, 3xTF32 products with FP32 accumulation in tensor
  *   memory), 0 (default) on the FP32 SIMT units.  FP64 contractions always use the FP64 units. */
 #define TPCG_OPT_TC 5
+/*   TPCG_OPT_RR: 1 (default) contexts created afterwards (FP32 with n > 128; FP64 with n > 256 and rank_cap <=
+ *   112) reduce mode Grams of order above 128 to a Rayleigh-Ritz matrix of at most 128 pivoted-Cholesky columns
+ *   before the eigensolver (see tucker_round); 0 they give every Gram to the one-CTA Jacobi eigensolvers, whose
+ *   FP32 variant above order 128 tracks the eigenvalues by rotation updates and can misjudge the discarded
+ *   energy by more than the FP32 Gram's resolution. */
+#define TPCG_OPT_RR 6
 int tpcg_set_option(int key, long long value);
 
 /* Best exponential sum s_R(lambda) = sum_j omega_j exp(-alpha_j lambda) for 1/lambda on [1, M] in the maximum

@@ -160,9 +160,11 @@ def tpcg_setup(kind: int, amp: float, degree: int, n: int, dtype: int = L.F64, e
     return Problem(h.value, dtype)
 
 
-def problem_from_export(ex, info, dtype=L.F64, pinned=True) -> Problem:
+def problem_from_export(ex, info, dtype=L.F64, pinned=True, rhs=None) -> Problem:
     """Re-create a problem from exported host arrays (bands and W in CSR as stored by the library).
-    With ``pinned`` the arrays are first placed in page-locked host memory."""
+    With ``pinned`` the arrays are first placed in page-locked host memory.  ``rhs`` = (core, [U1, U2, U3])
+    replaces the exported right-hand side (any Tucker tensor of the problem's n, e.g. the load vector of
+    another source term or a lifted right-hand side)."""
     keep = []
 
     def host(a, np_dt):
@@ -181,9 +183,16 @@ def problem_from_export(ex, info, dtype=L.F64, pinned=True) -> Problem:
     iptr = lambda arr: C.cast(host(arr, np.int32), C.POINTER(C.c_int))
     a.w = dptr(ex["w"])
     a.bands = dptr(ex["bands"])
-    a.rf = (C.c_int * 3)(*info.rf)
-    a.f_core = dptr(ex["f_core"])
-    a.f_U = (C.POINTER(C.c_double) * 3)(*[dptr(ex[f"f_U{t}"]) for t in range(3)])
+    if rhs is None:
+        a.rf = (C.c_int * 3)(*info.rf)
+        a.f_core = dptr(ex["f_core"])
+        a.f_U = (C.POINTER(C.c_double) * 3)(*[dptr(ex[f"f_U{t}"]) for t in range(3)])
+    else:
+        core, U = rhs
+        a.rf = (C.c_int * 3)(*[int(d) for d in np.shape(core)])
+        a.f_core = dptr(np.asarray(core, dtype=np.float64).reshape(-1, order="F"))
+        a.f_U = (C.POINTER(C.c_double) * 3)(*[dptr(np.asarray(U[t], dtype=np.float64).reshape(-1, order="F"))
+                                              for t in range(3)])
     a.n1, a.n2, a.RP, a.w_nnz = info.n1, info.n2, info.RP, info.w_nnz
     a.lam = dptr(ex["lam"])
     a.mu = dptr(ex["mu"])

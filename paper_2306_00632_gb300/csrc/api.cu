@@ -165,7 +165,7 @@ extern "C" void tpcg_params_default(tpcg_params* p) {
 }
 
 // ======================================================================================= contexts
-static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) {
+static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes, bool rr) {
     const size_t e = elt_of(dtype);
     const size_t nn = (size_t)n * n;
     size_t i = 0;
@@ -184,6 +184,8 @@ static size_t ctx_layout(int n, int max_cols, int rc, int dtype, size_t* sizes) 
     sizes[i++] = 3 * (size_t)rc * rc * e;                    // dotw
     sizes[i++] = 2 * (size_t)rc * rc * rc * e;               // dotT
     for (int t = 0; t < 12; ++t) sizes[i++] = (size_t)n * max_cols * e;   // fd scratch
+    const size_t rrb = rr ? (size_t)n * RR_L * e : 0;
+    for (int t = 0; t < 3; ++t) sizes[i++] = rrb;                         // rrY, rrQ, rrW
     size_t tot = eig_work_bytes(n);
     for (size_t j = 0; j < i; ++j) tot += (sizes[j] + 255) & ~(size_t)255;
     return tot;
@@ -198,10 +200,12 @@ static size_t tens_bytes(int n, int max_cols, int rc, int dtype, int count = 10)
 extern "C" size_t tpcg_ctx_bytes(int n, int max_cols, int rank_cap, int dtype) {
     size_t sizes[64];
     if (dtype == TPCG_MIXED)
-        return ctx_layout(n, max_cols, rank_cap, TPCG_F64, sizes) + ctx_layout(n, max_cols, rank_cap, TPCG_F32, sizes) +
+        return ctx_layout(n, max_cols, rank_cap, TPCG_F64, sizes, rr_context(n, rank_cap, TPCG_F64)) +
+               ctx_layout(n, max_cols, rank_cap, TPCG_F32, sizes, rr_context(n, rank_cap, TPCG_F32)) +
                tens_bytes(n, max_cols, rank_cap, TPCG_F64, 17) + tens_bytes(n, max_cols, rank_cap, TPCG_F32) +
                2 * eig_work_bytes(n);
-    return ctx_layout(n, max_cols, rank_cap, dtype, sizes) + tens_bytes(n, max_cols, rank_cap, dtype) +
+    return ctx_layout(n, max_cols, rank_cap, dtype, sizes, rr_context(n, rank_cap, dtype)) +
+           tens_bytes(n, max_cols, rank_cap, dtype) +
            eig_work_bytes(n);
 }
 
@@ -266,7 +270,8 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
     c->have_tens = 0;
     c->tens_cap = 0;
     size_t sizes[64];
-    ctx_layout(n, max_cols, rank_cap, dtype, sizes);
+    c->rr = rr_context(n, rank_cap, dtype) ? 1 : 0;
+    ctx_layout(n, max_cols, rank_cap, dtype, sizes, c->rr != 0);
     void** slots[64];
     int i = 0;
     slots[i++] = &c->Z0;
@@ -287,6 +292,9 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
     slots[i++] = &c->dotT;
     for (int t = 0; t < 3; ++t)
         for (int q = 0; q < 4; ++q) slots[i++] = &c->fd[t][q];
+    slots[i++] = &c->rrY;
+    slots[i++] = &c->rrQ;
+    slots[i++] = &c->rrW;
     for (int j = 0; j < i; ++j) {
         int s = dmalloc(slots[j], sizes[j], &c->owned);
         if (s != TPCG_OK) {

@@ -98,6 +98,9 @@ struct RoundPlan {
     int cap;
     int nsplit;        // groups of the current Gram
     int gm, gM;        // current Gram: mode and size
+    int eM;            // order of the eigensolver's input: gM, or RR_L when the Gram goes through rr
+    int rr;            // 1 while the current Gram is reduced by the Rayleigh-Ritz step (round.cu)
+    double gtrace;     // trace of the current Gram when rr (the eigensolver's input is then Q^T G Q)
     int zdim[3];       // current dims of the working tensor
     double eps, budget, norm2, discarded;
     double abs2;       // absolute floor of the discarded energy (0: relative rule only)
@@ -142,6 +145,11 @@ struct tpcg_ctx_s {
     void* dotT;          // rank_cap^3 * 2 temporaries for dot contractions
     void* fd[3][4];      // n * max_cols each: FD application scratch (gather, transform, scaled, back)
     tpcg::EigWork eigw;  // eigensolver work area
+    // Rayleigh-Ritz reduction of Grams above RR_L (contexts with n > RR_L and rank_cap <= RR_MAXCAP; round.cu)
+    int rr;              // 1 if this context uses it
+    void* rrY;           // n x RR_L: pivoted-Cholesky columns, then G Q, then Q U
+    void* rrQ;           // n x RR_L: orthonormal basis
+    void* rrW;           // n x RR_L: QR working copy
     // TPCG iterate tensors (allocated on first solve)
     std::vector<void*> owned;
     tucker_t tens[TPCG_CTX_TENSORS];

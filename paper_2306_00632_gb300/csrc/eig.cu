@@ -51,6 +51,19 @@ __host__ __device__ constexpr double jacobi_tau() { return sizeof(T) == 8 ? 1e-1
 // are then eigenvectors orthonormal to about HJ_TAU; the FP32 dot product itself resolves about 4e-7 at 128 rows.
 constexpr float HJ_TAU = 2e-6f;
 
+// Energy of the Gram outside the Rayleigh-Ritz subspace (trace(G) minus the Ritz values; 0 when the
+// eigensolver's input is the Gram itself).  The FP32 rule (trace minus kept) counts it implicitly.
+__device__ __forceinline__ double rr_remainder(const RoundPlan& p, const double* lam, int M, double trace) {
+    if (!p.rr) return 0.0;
+    double all = 0.0;
+    for (int i = 0; i < M; ++i) all += lam[i] > 0.0 ? lam[i] : 0.0;
+    return trace - all > 0.0 ? trace - all : 0.0;
+}
+
+// trace the truncation rule works with: the input's own, or the Gram's when the input is the Rayleigh-Ritz
+// matrix Q^T G Q
+__device__ __forceinline__ double rule_trace(const RoundPlan& p, double own) { return p.rr ? p.gtrace : own; }
+
 template <typename T>
 __device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double trace, int m) {
     int s = M;
@@ -61,7 +74,7 @@ __device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double tr
         // still fits the budget, so the truncation stays lossless instead of dropping directions whose energy
         // it cannot see; otherwise the clamped eigenvalues are used as they are.
         const double unc = p.strict ? 4.0 * 2.220446049250313e-16 * trace : 0.0;
-        double tail = 0.0;
+        double tail = rr_remainder(p, lam, M, trace);
         for (int i = M - 1; i >= 0; --i) {
             const double li = (lam[i] > 0.0 ? lam[i] : 0.0) + unc;
             if (tail + li <= p.budget) { tail += li; s = i; } else break;
@@ -78,6 +91,7 @@ __device__ int truncation_rule(RoundPlan& p, const double* lam, int M, double tr
     if (p.cap > 0 && s > p.cap) s = p.cap;
     double disc = 0.0;
     if (sizeof(T) == 8) {
+        disc = rr_remainder(p, lam, M, trace);
         for (int i = s; i < M; ++i) disc += lam[i] > 0.0 ? lam[i] : 0.0;
     } else {
         double cum = 0.0;
@@ -96,7 +110,7 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
                                                           T* __restrict__ Vg, T* __restrict__ S, double* evals, int m,
                                                           int a_smem, int v_smem, int max_sweeps, double* prof) {
     RoundPlan& p = *plan;
-    const int M = p.gM;
+    const int M = p.eM;
     const int n = p.n;
     const int tid = threadIdx.x, nt = blockDim.x;
     extern __shared__ unsigned char smem_raw[];
@@ -127,8 +141,8 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
         for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
         s_tr = t;
         if (m == 0) {
-            p.norm2 = t;
-            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+            p.norm2 = rule_trace(p, t);
+            p.budget = fmax(p.eps * p.eps * p.norm2, p.abs2) / 3.0;
         }
     }
     __syncthreads();
@@ -280,7 +294,7 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
     }
     __syncthreads();
     if (tid == 0) {
-        const int s = truncation_rule<T>(p, lam, M, s_tr, m);
+        const int s = truncation_rule<T>(p, lam, M, rule_trace(p, s_tr), m);
         s_keep = s;
         for (int i = 0; i < M; ++i) evals[i] = lam[i];
         if (prof) {   // algorithmic work: the dense symmetric eigen-decomposition count 9 M^3; Gram in, S out
@@ -329,15 +343,15 @@ __global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
     cgx::cluster_group cluster = cgx::this_cluster();
     const int crank = (int)cluster.block_rank();
     RoundPlan& p = *plan;
-    const int M = p.gM;
+    const int M = p.eM;
     const int n = p.n;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (M <= 1) {   // uniform across the cluster: nothing to rotate
         if (crank == 0 && tid == 0) {
             double t = M == 1 ? (double)G[0] : 0.0;
-            if (m == 0) { p.norm2 = t; p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0; }
+            if (m == 0) { p.norm2 = rule_trace(p, t); p.budget = fmax(p.eps * p.eps * p.norm2, p.abs2) / 3.0; }
             double lam1[1] = {t};
-            const int s = truncation_rule<T>(p, lam1, M, t, m);
+            const int s = truncation_rule<T>(p, lam1, M, rule_trace(p, t), m);
             if (M == 1) evals[0] = t;
             if (s > 0) S[0] = T(1);
         }
@@ -381,8 +395,8 @@ __global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
         for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
         s_tr = t;
         if (m == 0 && crank == 0) {
-            p.norm2 = t;
-            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+            p.norm2 = rule_trace(p, t);
+            p.budget = fmax(p.eps * p.eps * p.norm2, p.abs2) / 3.0;
         }
     }
     __syncthreads();
@@ -557,7 +571,7 @@ __global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
         }
         __syncthreads();
         if (tid == 0) {
-            const int s = truncation_rule<T>(p, lam, M, s_tr, m);
+            const int s = truncation_rule<T>(p, lam, M, rule_trace(p, s_tr), m);
             s_keep = s;
             for (int i = 0; i < M; ++i) evals[i] = lam[i];
             if (prof) {
@@ -633,7 +647,7 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
                                                                    float* __restrict__ S, double* evals, int m,
                                                                    int max_sweeps, double* prof) {
     RoundPlan& p = *plan;
-    const int M = p.gM;
+    const int M = p.eM;
     const int n = p.n;
     const int tid = threadIdx.x, nt = blockDim.x;
     extern __shared__ __align__(16) unsigned char jv_smem[];
@@ -667,8 +681,8 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
         for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
         s_tr = t;
         if (m == 0) {
-            p.norm2 = t;
-            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+            p.norm2 = rule_trace(p, t);
+            p.budget = fmax(p.eps * p.eps * p.norm2, p.abs2) / 3.0;
         }
     }
     __syncthreads();
@@ -821,7 +835,7 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
     }
     __syncthreads();
     if (tid == 0) {
-        const int s = truncation_rule<float>(p, lam, M, s_tr, m);
+        const int s = truncation_rule<float>(p, lam, M, rule_trace(p, s_tr), m);
         s_keep = s;
         for (int i = 0; i < M; ++i) evals[i] = lam[i];
         if (prof) {   // algorithmic work: the dense symmetric eigen-decomposition count 9 M^3; Gram in, S out
@@ -882,7 +896,7 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
                                                                   float* __restrict__ S, double* evals, int m,
                                                                   int max_sweeps, float tau, double* prof) {
     RoundPlan& p = *plan;
-    const int M = p.gM;
+    const int M = p.eM;
     const int n = p.n;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr unsigned FULL = 0xffffffffu;
@@ -924,8 +938,8 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
         for (int i = 0; i < M; ++i) t += (double)G[i + (long long)i * M];
         s_tr = t;
         if (m == 0) {
-            p.norm2 = t;
-            p.budget = fmax(p.eps * p.eps * t, p.abs2) / 3.0;
+            p.norm2 = rule_trace(p, t);
+            p.budget = fmax(p.eps * p.eps * p.norm2, p.abs2) / 3.0;
         }
     }
     __syncthreads();
@@ -1163,7 +1177,7 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
     }
     __syncthreads();
     if (tid == 0) {
-        int s = truncation_rule<float>(p, lsort, M, s_tr, m);
+        int s = truncation_rule<float>(p, lsort, M, rule_trace(p, s_tr), m);
         while (s > 0 && !(lsort[s - 1] > 0.0)) --s;   // a zero column is never kept (its energy is already
         p.s[m] = s;                                   // counted as discarded)
         s_keep = s;

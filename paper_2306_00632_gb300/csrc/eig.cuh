@@ -9,6 +9,10 @@ namespace tpcg {
 struct RoundPlan;
 
 constexpr int SMAX_EIG = 1024;   // largest Gram (= n) the one-CTA eigensolver accepts
+// Rayleigh-Ritz reduction of large Grams (round.cu): the largest basis (pivoted-Cholesky columns), and the
+// largest rank cap of the contexts that use it
+constexpr int RR_L = 128;
+constexpr int RR_MAXCAP = RR_L - 16;
 
 struct EigWork {
     void* Aw;        // n (n + 1) elements: the Gram when it does not fit shared memory

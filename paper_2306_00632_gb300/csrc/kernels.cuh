@@ -17,6 +17,14 @@ template <typename T>
 int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st, int strict_mode = -1);
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
                 double abs_tol, double* info_dev, cudaStream_t st);
+// whether a context of this size, rank cap and dtype reduces its large Grams by Rayleigh-Ritz
+int rr_kind();   // TPCG_OPT_RR
+// FP32: every context with n > RR_L (the one-CTA FP32 Jacobi for larger Grams keeps its diagonal by rotation
+// updates, whose drift spoils the trace-minus-kept rule); FP64: n > 256 (beyond the cluster eigensolver) with a
+// rank cap that leaves the basis room
+inline bool rr_context(int n, int rank_cap, int dtype) {
+    return rr_kind() == 1 && (dtype == TPCG_F32 ? n > RR_L : (n > 256 && rank_cap <= RR_MAXCAP));
+}
 // ||y||^2 of any (block) tensor by the Z formation of Alg. 1
 template <typename T>
 int tensor_norm2(tpcg_ctx c, tucker_t* y, double* out_dev, cudaStream_t st);

@@ -124,6 +124,8 @@ static std::atomic<int> g_dst_kind{1};
 int dst_kind() { return g_dst_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_tc_kind{0};
 int tc_kind() { return g_tc_kind.load(std::memory_order_relaxed); }
+static std::atomic<int> g_rr_kind{1};
+int rr_kind() { return g_rr_kind.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
@@ -145,6 +147,10 @@ extern "C" int tpcg_set_option(int key, long long value) {
     }
     if (key == TPCG_OPT_TC && (value == 0 || value == 1)) {
         tpcg::g_tc_kind.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_RR && (value == 0 || value == 1)) {
+        tpcg::g_rr_kind.store((int)value);
         return TPCG_OK;
     }
     tpcg::set_error("tpcg_set_option: unknown key or value out of range");

@@ -140,31 +140,24 @@ __device__ T block_sum(T v, T* red) {
     return r;
 }
 
+// Householder QR of Y (rows x k, column stride ld, k <= rows) by one CTA: A <- Y is the working copy; R (k x k,
+// upper triangle, ld ldr) when R is non-null; Q = H_0 ... H_{k-1} [I; 0] (rows x k, ld ld).  tau holds k scalars
+// and red 33 of shared memory.
 template <typename T>
-__global__ void __launch_bounds__(1024) qr_kernel(const RoundPlan* __restrict__ plan, const T* Y0, const T* Y1,
-                                                  const T* Y2, T* W0, T* W1, T* W2, T* R0, T* R1, T* R2, T* Q0,
-                                                  T* Q1, T* Q2) {
-    const int t = blockIdx.x;
-    const RoundPlan& p = *plan;
-    if (!p.useQ[t]) return;
-    const int n = p.n, k = p.k[t];
-    const T* Y = t == 0 ? Y0 : (t == 1 ? Y1 : Y2);
-    T* A = t == 0 ? W0 : (t == 1 ? W1 : W2);
-    T* R = t == 0 ? R0 : (t == 1 ? R1 : R2);
-    T* Q = t == 0 ? Q0 : (t == 1 ? Q1 : Q2);
-    extern __shared__ unsigned char smem_raw[];
-    T* tau = reinterpret_cast<T*>(smem_raw);      // k
-    T* red = tau + n;                              // 33
-    __shared__ T s_beta;
-    for (long long e = threadIdx.x; e < (long long)n * k; e += blockDim.x) A[e] = Y[e];
+__device__ void householder_qr(const T* Y, T* A, T* R, T* Q, int rows, int k, long long ld, long long ldr, T* tau,
+                               T* red, T* s_beta) {
+    for (long long e = threadIdx.x; e < (long long)rows * k; e += blockDim.x) {
+        const long long i = e % rows, c = e / rows;
+        A[i + c * ld] = Y[i + c * ld];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < k; ++j) {
-        // Householder vector of A[j:n, j] (LAPACK larfg convention: v[0] = 1, R[j,j] = beta)
+        // Householder vector of A[j:rows, j] (LAPACK larfg convention: v[0] = 1, R[j,j] = beta)
         T part = T(0);
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) part += A[i + (long long)j * n] * A[i + (long long)j * n];
+        for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) part += A[i + j * ld] * A[i + j * ld];
         T sig = block_sum(part, red);
-        const T alpha0 = A[j + (long long)j * n];
+        const T alpha0 = A[j + j * ld];
         T beta, tj, scal;
         if (sig == T(0)) {
             tj = T(0); beta = alpha0; scal = T(0);
@@ -174,51 +167,70 @@ __global__ void __launch_bounds__(1024) qr_kernel(const RoundPlan* __restrict__ 
             tj = (beta - alpha0) / beta;
             scal = T(1) / (alpha0 - beta);
         }
-        for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (long long)j * n] *= scal;
-        if (threadIdx.x == 0) { tau[j] = tj; s_beta = beta; }
+        for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) A[i + j * ld] *= scal;
+        if (threadIdx.x == 0) { tau[j] = tj; *s_beta = beta; }
         __syncthreads();
         // apply H_j to the trailing columns, one warp per column
         if (tj != T(0)) {
             for (int c = j + 1 + wid; c < k; c += nw) {
-                T* col = A + (long long)c * n;
-                const T* v = A + (long long)j * n;
+                T* col = A + c * ld;
+                const T* v = A + j * ld;
                 T w = T(0);
-                for (int i = j + lane; i < n; i += 32) w += (i == j ? T(1) : v[i]) * col[i];
+                for (int i = j + lane; i < rows; i += 32) w += (i == j ? T(1) : v[i]) * col[i];
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 w *= tj;
-                for (int i = j + lane; i < n; i += 32) col[i] -= w * (i == j ? T(1) : v[i]);
+                for (int i = j + lane; i < rows; i += 32) col[i] -= w * (i == j ? T(1) : v[i]);
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) A[j + (long long)j * n] = s_beta;
+        if (threadIdx.x == 0) A[j + j * ld] = *s_beta;
         __syncthreads();
     }
-    // R (k x k, ld n): upper triangle of A
-    for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
-        int i = (int)(e % k), c = (int)(e / k);
-        R[i + (long long)c * n] = (i <= c) ? A[i + (long long)c * n] : T(0);
+    if (R) {
+        for (long long e = threadIdx.x; e < (long long)k * k; e += blockDim.x) {
+            const int i = (int)(e % k), c = (int)(e / k);
+            R[i + c * ldr] = (i <= c) ? A[i + c * ld] : T(0);
+        }
     }
     // Q = H_0 H_1 ... H_{k-1} [I; 0], accumulated backwards
-    for (long long e = threadIdx.x; e < (long long)n * k; e += blockDim.x) {
-        int i = (int)(e % n), c = (int)(e / n);
-        Q[e] = (i == c) ? T(1) : T(0);
+    for (long long e = threadIdx.x; e < (long long)rows * k; e += blockDim.x) {
+        const int i = (int)(e % rows), c = (int)(e / rows);
+        Q[i + (long long)c * ld] = (i == c) ? T(1) : T(0);
     }
     __syncthreads();
     for (int j = k - 1; j >= 0; --j) {
         const T tj = tau[j];
         if (tj != T(0)) {
             for (int c = j + wid; c < k; c += nw) {
-                T* col = Q + (long long)c * n;
-                const T* v = A + (long long)j * n;
+                T* col = Q + c * ld;
+                const T* v = A + j * ld;
                 T w = T(0);
-                for (int i = j + lane; i < n; i += 32) w += (i == j ? T(1) : v[i]) * col[i];
+                for (int i = j + lane; i < rows; i += 32) w += (i == j ? T(1) : v[i]) * col[i];
                 for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
                 w *= tj;
-                for (int i = j + lane; i < n; i += 32) col[i] -= w * (i == j ? T(1) : v[i]);
+                for (int i = j + lane; i < rows; i += 32) col[i] -= w * (i == j ? T(1) : v[i]);
             }
         }
         __syncthreads();
     }
+}
+
+// Alg. 1 step 1: Y_t = Q_t R_t for the modes with k_t < n, one CTA per mode (n x k_t, ld n)
+template <typename T>
+__global__ void __launch_bounds__(1024) qr_kernel(const RoundPlan* __restrict__ plan, const T* Y0, const T* Y1,
+                                                  const T* Y2, T* W0, T* W1, T* W2, T* R0, T* R1, T* R2, T* Q0,
+                                                  T* Q1, T* Q2) {
+    const int t = blockIdx.x;
+    const RoundPlan& p = *plan;
+    if (!p.useQ[t]) return;
+    const int n = p.n, k = p.k[t];
+    extern __shared__ unsigned char smem_raw[];
+    T* tau = reinterpret_cast<T*>(smem_raw);      // k
+    T* red = tau + n;                              // 33
+    __shared__ T s_beta;
+    householder_qr<T>(t == 0 ? Y0 : (t == 1 ? Y1 : Y2), t == 0 ? W0 : (t == 1 ? W1 : W2),
+                      t == 0 ? R0 : (t == 1 ? R1 : R2), t == 0 ? Q0 : (t == 1 ? Q1 : Q2), n, k, n, n, tau, red,
+                      &s_beta);
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -271,6 +283,8 @@ __global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* 
     p.nsplit = used;
     p.gm = m;
     p.gM = M;
+    p.eM = M;
+    p.rr = 0;
     counts[0] = used;
     counts[1] = M;
     counts[2] = M;
@@ -312,6 +326,176 @@ __global__ void plan_proj_kernel(RoundPlan* plan, GemmArgs* ga, const T* S, cons
 
 __global__ void set_zdim_kernel(RoundPlan* plan, int m) {
     if (threadIdx.x == 0) plan->zdim[m] = plan->s[m];
+}
+
+// --------------------------------------------------------------------------------------------------
+// Rayleigh-Ritz reduction of a Gram G of order gM > RR_L (contexts with n > RR_L and a rank cap of at most
+// RR_MAXCAP) to at most RR_L columns before the eigensolver:
+//  1. pivoted Cholesky G = L L^T + S (diagonal pivoting, left-looking, one column per step) until the trace of
+//     the Schur complement S is at most 1% (FP32) or 1e-8 (FP64) of this mode's truncation budget, or RR_L
+//     columns;
+//  2. Q = qr(L) (gM x rc), B = Q^T G Q (rc x rc) replaces G as the eigensolver's input, and the kept Ritz
+//     vectors Q U are written back.
+// The truncation rule is charged against trace(G).  For orthonormal kept vectors the discarded energy
+// ||Z - S S^T Z||^2 = trace(G) - sum of the kept Ritz values exactly, so Alg. 1's bound holds.  The Ritz
+// values of range(L) miss at most trace(S) of G's energy in total (Q^T G Q >= Q^T L L^T Q, whose trace is
+// trace(G) - trace(S)), so the ranks are those of the exact rule up to that fraction of the budget.  When RR_L columns do
+// not reach the 1% (slowly decaying spectra) the remainder counts as discarded and the rule keeps at most RR_L
+// columns, more than the rank cap.  A Gram of order <= RR_L goes to the eigensolver unchanged.
+// --------------------------------------------------------------------------------------------------
+constexpr int RR_THREADS = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(RR_THREADS) rr_pchol_kernel(RoundPlan* plan, const T* __restrict__ G, T* Lf,
+                                                               double* prof) {
+    RoundPlan& p = *plan;
+    const int M = p.gM, n = p.n, m = p.gm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = RR_THREADS / 32;
+    extern __shared__ __align__(16) unsigned char rr_smem[];
+    T* dg = reinterpret_cast<T*>(rr_smem);            // remaining diagonal (M entries; -1 once pivoted)
+    T* prow = dg + n;                                   // row piv of L (RR_L entries)
+    __shared__ T wbest[NW], wsum[NW];
+    __shared__ int wbi[NW];
+    __shared__ double s_tr, wtr[NW];
+    if (M <= RR_L) {   // small Gram: the eigensolver takes it as it is
+        if (tid == 0) { p.rr = 0; p.eM = M; }
+        return;
+    }
+    double t = 0.0;
+    for (int i = tid; i < M; i += RR_THREADS) {
+        const T d = G[i + (long long)i * M];
+        dg[i] = d;
+        t += (double)d;
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) wtr[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+        double tr = 0.0;
+        for (int w = 0; w < NW; ++w) tr += wtr[w];   // fixed order: deterministic
+        s_tr = tr;
+        p.gtrace = tr;
+        if (m == 0) {   // the budget of every mode comes from ||Z||^2 = trace of the first Gram
+            p.norm2 = tr;
+            p.budget = fmax(p.eps * p.eps * tr, p.abs2) / 3.0;
+        }
+    }
+    __syncthreads();
+    const double tr = s_tr;
+    // FP32: 1% of the budget (the FP32 Gram resolves no finer); FP64: 1e-8 of it, which puts the Ritz vectors of
+    // the kept directions within about 1e-4 eps of the eigenvectors (a direction u_j of eigenvalue lambda_j has
+    // at most trace(S) / lambda_j of its square outside range(L))
+    const T thr = (T)((sizeof(T) == 8 ? 1e-15 : 1e-9) * tr);
+    const T stop_rem = (T)fmax((double)thr, (sizeof(T) == 8 ? 1e-8 : 1e-2) * p.budget);
+    int rc = 0;
+    for (int k = 0; k < RR_L; ++k) {
+        // the largest remaining diagonal entry (ties: the lowest index) and the remaining trace
+        T v = (T)-2, sm = (T)0;
+        int bi = 0x7fffffff;
+        for (int i = tid; i < M; i += RR_THREADS) {
+            const T d = dg[i];
+            if (d > v) { v = d; bi = i; }
+            sm += d > (T)0 ? d : (T)0;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const T v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int b2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            sm += __shfl_xor_sync(0xffffffffu, sm, o);
+            if (v2 > v || (v2 == v && b2 < bi)) { v = v2; bi = b2; }
+        }
+        if (lane == 0) { wbest[warp] = v; wbi[warp] = bi; wsum[warp] = sm; }
+        __syncthreads();
+        T dmax = (T)-2, rem = (T)0;
+        int piv = 0;
+        for (int w = 0; w < NW; ++w) {
+            rem += wsum[w];
+            if (wbest[w] > dmax || (wbest[w] == dmax && wbi[w] < piv)) { dmax = wbest[w]; piv = wbi[w]; }
+        }
+        // the same decision in every thread (a NaN stops the factorisation)
+        if (!(dmax > thr) || !(rem > stop_rem)) break;
+        for (int j = tid; j < k; j += RR_THREADS) prow[j] = Lf[piv + (long long)j * n];
+        __syncthreads();
+        const T r = sqrt(dmax);
+        const T inv = (T)1 / r;
+        for (int i = tid; i < M; i += RR_THREADS) {
+            T l;
+            if (i == piv) {
+                l = r;
+            } else if (dg[i] < (T)0) {   // pivoted earlier: its Schur complement row is zero
+                l = (T)0;
+            } else {
+                T acc = G[i + (long long)piv * M];
+                for (int j = 0; j < k; ++j) acc -= Lf[i + (long long)j * n] * prow[j];
+                l = acc * inv;
+            }
+            Lf[i + (long long)k * n] = l;
+            dg[i] = (i == piv) ? (T)-1 : (dg[i] < (T)0 ? dg[i] : dg[i] - l * l);
+        }
+        __syncthreads();
+        rc = k + 1;
+    }
+    if (tid == 0) {
+        p.rr = 1;
+        p.eM = rc;
+        if (prof) {   // Cholesky columns, QR of the basis, G Q, Q^T (G Q) and Q U (U counted as rc columns)
+            const double mm = M, l = rc;
+            prof[2 * PK_EIG] += mm * l * l + 4.0 * mm * l * l + 2.0 * mm * mm * l + 4.0 * mm * l * l;
+            prof[2 * PK_EIG + 1] += sizeof(T) * (2.0 * mm * mm + 8.0 * mm * l);
+        }
+    }
+}
+
+// orthonormal basis Q (gM x eM, ld n) of the Cholesky columns by Householder QR; nothing when the Gram is small
+template <typename T>
+__global__ void __launch_bounds__(1024) rr_qr_kernel(const RoundPlan* __restrict__ plan, const T* Y, T* W, T* Q) {
+    const RoundPlan& p = *plan;
+    if (!p.rr) return;
+    __shared__ T tau[RR_L];
+    __shared__ T red[33];
+    __shared__ T s_beta;
+    householder_qr<T>(Y, W, nullptr, Q, p.gM, p.eM, p.n, 0, tau, red, &s_beta);
+}
+
+// the next product of the reduction (k = eM basis columns): 0: Y = G Q;  1: B = Q^T Y into the Gram's buffer
+// (ld k); 2: Y = Q U (U = the eigensolver's kept vectors of B, in S, ld n)
+template <typename T>
+__global__ void rr_step_kernel(const RoundPlan* __restrict__ plan, GemmArgs* ga, T* G, const T* Q, T* Y, const T* S,
+                               int m, int which) {
+    if (threadIdx.x != 0) return;
+    const RoundPlan& p = *plan;
+    const int M = p.gM, k = p.eM;
+    const bool on = p.rr && k > 0;
+    GemmArgs a{};
+    a.alpha = 1.0; a.beta = 0.0; a.nbatch = 1; a.acc = 0;
+    if (which == 0) {
+        a.M = on ? M : 0; a.N = k; a.K = M;
+        a.A = G; a.lda = M > 0 ? M : 1; a.B = Q; a.ldb = p.n; a.C = Y; a.ldc = p.n;
+    } else if (which == 1) {
+        a.M = on ? k : 0; a.N = k; a.K = M;
+        a.A = Q; a.lda = p.n; a.B = Y; a.ldb = p.n; a.C = G; a.ldc = k > 0 ? k : 1;
+    } else {
+        a.M = on ? M : 0; a.N = p.s[m]; a.K = k;
+        a.A = Q; a.lda = p.n; a.B = S; a.ldb = p.n; a.C = Y; a.ldc = p.n;
+    }
+    ga[0] = a;
+}
+
+// S <- Y (the kept Ritz vectors, gM x s_m)
+template <typename T>
+__global__ void rr_copy_kernel(const RoundPlan* __restrict__ plan, const T* Y, T* S, int m) {
+    const RoundPlan& p = *plan;
+    if (!p.rr) return;
+    const int M = p.gM, s = p.s[m], n = p.n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)M * s;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e % M, c = e / M;
+        S[i + c * n] = Y[i + c * n];
+    }
+}
+
+__global__ void rr_end_kernel(RoundPlan* plan) {
+    if (threadIdx.x == 0) { plan->rr = 0; plan->eM = plan->gM; }
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -375,7 +559,7 @@ __global__ void final_copy_kernel(const RoundPlan* __restrict__ plan, const T* S
             info[2] = p.s[0];
             info[3] = p.s[1];
             info[4] = p.s[2];
-            info[5] = (cs <= core_cap) ? 0.0 : 1.0;
+            info[5] = p.status ? 2.0 : ((cs <= core_cap) ? 0.0 : 1.0);
         }
     }
 }
@@ -450,8 +634,33 @@ int round_stage34(tpcg_ctx c, tucker_t* y, double* info_dev, cudaStream_t st) {
         TPCG_CHECK_LAUNCH();
         prof_end(PK_GRAM, st);
         prof_begin(PK_EIG, st);
-        TPCG_TRY(launch_eig<T>(c->plan, static_cast<const T*>(c->Gm), c->eigw, static_cast<T*>(c->S[m]),
-                                       c->evals, m, n, st));
+        T* Gm = static_cast<T*>(c->Gm);
+        T* Sm = static_cast<T*>(c->S[m]);
+        T* rY = static_cast<T*>(c->rrY);
+        T* rQ = static_cast<T*>(c->rrQ);
+        if (c->rr) {   // Grams above RR_L: Rayleigh-Ritz matrix Q^T G Q of a pivoted-Cholesky basis in place of G
+            const size_t sm = ((size_t)n + RR_L) * sizeof(T);
+            rr_pchol_kernel<T><<<1, RR_THREADS, sm, st>>>(c->plan, Gm, rY, prof_dev());
+            TPCG_CHECK_LAUNCH();
+            rr_qr_kernel<T><<<1, 1024, 0, st>>>(c->plan, rY, static_cast<T*>(c->rrW), rQ);
+            TPCG_CHECK_LAUNCH();
+            rr_step_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Gm, rQ, rY, Sm, m, 0);
+            TPCG_CHECK_LAUNCH();
+            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n, RR_L, st)));
+            rr_step_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Gm, rQ, rY, Sm, m, 1);
+            TPCG_CHECK_LAUNCH();
+            TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, RR_L, RR_L, st)));
+        }
+        TPCG_TRY(launch_eig<T>(c->plan, Gm, c->eigw, Sm, c->evals, m, c->rr ? RR_L : n, st));
+        if (c->rr) {   // kept Ritz vectors Q U back into S
+            rr_step_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Gm, rQ, rY, Sm, m, 2);
+            TPCG_CHECK_LAUNCH();
+            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n, RR_L, st)));
+            rr_copy_kernel<T><<<64, 256, 0, st>>>(c->plan, rY, Sm, m);
+            TPCG_CHECK_LAUNCH();
+            rr_end_kernel<<<1, 32, 0, st>>>(c->plan);
+            TPCG_CHECK_LAUNCH();
+        }
         prof_end(PK_EIG, st);
         prof_begin(PK_PROJ, st);
         plan_proj_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, static_cast<const T*>(c->S[m]), Zc, Zn, m, counts);
