@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--rank-cap", type=int, default=96)
     ap.add_argument("--inner-tol", type=float, default=2e-2, help="mixed form: inner FP32 solve tolerance")
     ap.add_argument("--refine-keep", type=float, default=3e-2, help="mixed form: accuracy kept of each correction")
+    ap.add_argument("--max-outer", type=int, default=12, help="mixed form: cap on FP64 refinements")
     ap.add_argument("--gemm-ctas-per-sm", type=int, default=2, help="grouped-GEMM CTA budget per SM (0: uncapped)")
     ap.add_argument("--eig", type=int, default=1, choices=[0, 1],
                     help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
@@ -68,10 +69,13 @@ def parse():
     ap.add_argument("--serve", type=float, default=0.0,
                     help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
     ap.add_argument("--requests", type=int, default=48, help="requests in the --serve stream")
+    ap.add_argument("--mix-caps", default="20,60", help="--mix: range of the rank caps (lo,hi)")
     ap.add_argument("--mix", type=int, default=0,
                     help="instead of the batch benchmark: this many independent solves of uneven n, p, rank cap and "
                          "geometry (n in {32..256}, p in {2,3,4}, caps 20-60), all submitted at once")
     ap.add_argument("--large", type=int, default=0, help="n of the large configuration (e.g. 512); 0: off")
+    ap.add_argument("--kernels", type=int, default=0, help="time apply / FD / one truncation at this n; 0: off")
+    ap.add_argument("--kernels-dtype", default="both", choices=["f32", "f64", "both"])
     ap.add_argument("--large-cap", type=int, default=80, help="large configuration: rank cap")
     ap.add_argument("--large-concurrent", type=int, default=2, help="large configuration: solves at once")
     ap.add_argument("--large-fp64", action="store_true", help="large configuration: also the FP64 form")
@@ -641,14 +645,17 @@ def run_serve(args):
 def run_mix(args):
     """Many independent solves of uneven size at once: the mixed form (FP32 inner solves, FP64 refinement)
     on seeded twisted annuli with n in {32, 64, 96, 128, 192, 256}, p in {2, 3, 4}, amplitude in [0, 0.3] and
-    rank caps 20-60, all submitted at t = 0 to the continuous-batching server (at most 32 in flight, admitted by
-    device memory).  Operators are built before the clock starts.  Prints solves/s and the per-result status."""
+    rank caps in --mix-caps (default 20-60), all submitted at t = 0 to the continuous-batching server (at most 32
+    in flight, admitted by device memory).  Operators are built before the clock starts.  `value` counts the
+    solves that reached true relative residual 1e-6 (a cap below the solution's rank cannot); the per-n status
+    follows."""
     import torch
     from paper_2306_00632_gb300 import lib, serve
     lib.load()
-    mix = synth.batch_mix(args.mix, seed0=SEED)
-    reqs = [serve.Request(lib.GEOM_TWIST, pr.amp, pr.degree, pr.n, cap, tol=TOL, dtype=lib.MIXED, arrival=0.0)
-            for pr, cap in mix]
+    caps = tuple(int(v) for v in args.mix_caps.split(","))
+    mix = synth.batch_mix(args.mix, seed0=SEED, caps=caps)
+    reqs = [serve.Request(lib.GEOM_TWIST, pr.amp, pr.degree, pr.n, min(cap, pr.n), tol=TOL, dtype=lib.MIXED,
+                          arrival=0.0) for pr, cap in mix]
     free, _ = torch.cuda.mem_get_info()
     srv = serve.Server(int(free * 0.7), max_slots=32)
     t0 = time.perf_counter()
@@ -667,10 +674,12 @@ def run_mix(args):
         d["converged"] += int(r.status == 0 and r.true_rel_res <= TOL)
         d["iters"].append(r.iters)
     line = {"metric": "independent mixed-precision TPCG solves/sec to rel-residual 1e-6 (uneven n, p, rank cap)",
-            "value": len(res) / wall, "unit": "solves/s", "solves": len(res), "converged": len(ok), "wall_s": wall,
+            "value": len(ok) / wall, "unit": "solves/s", "all_solves_per_s": len(res) / wall, "solves": len(res),
+            "converged": len(ok), "wall_s": wall,
             "setup_s_untimed": setup_s, "max_in_flight": 32, "dtype": "mixed", "data": "synthetic",
             "config": {"workload": "twisted quarter annuli, n in {32,64,96,128,192,256}, p in {2,3,4}, amp in "
-                                   "[0,0.3], rank caps 20-60", "seeds": f"{SEED}..{SEED + args.mix - 1}", "tol": TOL},
+                                   f"[0,0.3], rank caps {caps[0]}-{caps[1]} (at most n)",
+                       "seeds": f"{SEED}..{SEED + args.mix - 1}", "tol": TOL},
             "latency_s": serve.percentiles(res), "max_true_rel_res": max(r.true_rel_res for r in res),
             "by_n": by_n}
     print(json.dumps(line), flush=True)
@@ -693,7 +702,7 @@ def run_large(args):
     pbs = [api.tpcg_setup(lib.GEOM_TWIST, synth.amp_from_seed(sd), DEGREE, n, lib.MIXED) for sd in seeds]
     ctxs = [api.Ctx(n, api.max_cols_for(p.info, rc, lib.MIXED), rc, lib.MIXED) for p in pbs]
     xs = [api.Tucker(n, cap=rc, core_cap=rc ** 3, dtype=lib.MIXED) for _ in range(B)]
-    kw = dict(tol=TOL, rank_cap=rc, inner_tol=args.inner_tol, refine_keep=args.refine_keep)
+    kw = dict(tol=TOL, rank_cap=rc, inner_tol=args.inner_tol, refine_keep=args.refine_keep, max_outer=args.max_outer)
     main = torch.cuda.current_stream()
     api.tpcg_solve(pbs[0], ctxs[0], xs[0], **kw)   # warm-up: graphs captured
     torch.cuda.synchronize()
@@ -752,7 +761,8 @@ def run_large(args):
            "higher_is_better": True, "dtype": "mixed", "data": "synthetic",
            "config": {"workload": f"twisted quarter annulus Poisson, p={DEGREE}, n={n}/direction", "rank_cap": rc,
                       "solves_per_step": B, "seeds": f"{seeds[0]}..{seeds[-1]}", "tol": TOL, "tc": args.tc,
-                      "R": [p.info.R for p in pbs], "RP": pbs[0].info.RP, "inner_tol": args.inner_tol},
+                      "R": [p.info.R for p in pbs], "RP": pbs[0].info.RP, "inner_tol": args.inner_tol,
+                      "refine_keep": args.refine_keep, "max_outer": args.max_outer},
            "status": [int(c) for c in codes], "true_rel_res": [float(s.true_rel_res) for s in sts],
            "inner_iters": [int(s.iters) for s in sts], "outer_iters": [int(s.outer_iters) for s in sts],
            "rank": [list(s.rank) for s in sts],
@@ -779,10 +789,113 @@ def run_large(args):
     print(json.dumps(out), flush=True)
 
 
+def run_kernels(args):
+    """The operator pieces at n = args.kernels (p = 3, twisted annulus, seed 7) on a solver-like input of rank
+    args.large_cap (random orthonormal factors, geometric core): the banded apply y = A x, the preconditioner
+    v = P^-1 x and one truncation of A x (Alg. 1 at eps 1e-3), in FP32 and FP64, each timed alone with CUDA
+    events on its stream (median of the repeats, L2 flushed before each).  Reports the algorithmic bytes or
+    flops per launch (the library's device-side accounting from the actual ranks) over the measured time,
+    against the measured HBM copy peak or the FP32/FP64 SIMT peaks."""
+    import torch
+    from paper_2306_00632_gb300 import api, lib
+    L = lib.load()
+    n, r = args.kernels, args.large_cap
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1900.0))
+    alu = {lib.F32: bf16 * 75.0 / 2250.0, lib.F64: bf16 * 1.25 / 2250.0}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    main = torch.cuda.current_stream()
+    g = np.random.default_rng(SEED)
+    core = np.einsum("i,j,k->ijk", *[0.7 ** np.arange(r)] * 3) * g.standard_normal((r, r, r))
+    U = [np.linalg.qr(g.standard_normal((n, r)))[0] for _ in range(3)]
+    out = {"metric": f"operator pieces at n={n}: fraction of roofline", "n": n, "rank": r, "kernels": {},
+           "peaks": {"hbm_gbs": hbm, "f32_tflops": alu[lib.F32], "f64_tflops": alu[lib.F64],
+                     "source": "of measured" if peaks else "of fallback"}, "l2": "256 MB buffer written before each launch"}
+
+    def timed(fn, reps):
+        # the 256 MB flush keeps the stream busy while the host enqueues the start event and the launches, so the
+        # events bracket the kernels and not the host's launch latency
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            fn()
+            b.record(main)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    kinds = {"f32": [(lib.F32, "f32")], "f64": [(lib.F64, "f64")], "both": [(lib.F32, "f32"), (lib.F64, "f64")]}
+    for dt, name in kinds[args.kernels_dtype]:
+        pb = api.tpcg_setup(lib.GEOM_TWIST, AMP, DEGREE, n, dt)
+        R, RP = pb.info.R, pb.info.RP
+        x = api.Tucker.from_numpy(core, U, cap=r, core_cap=r ** 3, dtype=dt)
+        y = api.Tucker(n, cap=R * r, core_cap=1, dtype=dt)
+        v = api.Tucker(n, cap=RP * r, core_cap=1, dtype=dt)
+        ctx = api.Ctx(n, max(R, RP) * r, r, dt)
+        api.tucker_apply(pb, x, y)
+        api.fd_precond_apply(pb, ctx, x, v)
+        torch.cuda.synchronize()
+        for kind, fn, reps in (("apply", lambda: api.tucker_apply(pb, x, y), 20),
+                               ("fd", lambda: api.fd_precond_apply(pb, ctx, x, v), 20)):
+            L.tpcg_profile_reset()
+            L.tpcg_profile_enable(1)
+            fn()
+            torch.cuda.synchronize()
+            L.tpcg_profile_enable(0)
+            work = _profile(L, lib)[kind]
+            ms = timed(fn, reps)
+            ach = work["bytes"] / (ms * 1e-3) / 1e9
+            out["kernels"][f"{kind}_{name}"] = {"ms": ms, "bytes": work["bytes"], "flops": work["flops"],
+                                                "achieved_gbs": ach, "bound": "hbm", "frac": ach / hbm}
+        # one truncation of A x (k = R r columns per mode), re-applied before every repeat
+        yr = api.Tucker(n, cap=R * r, core_cap=r ** 3, dtype=dt)
+        ctx2 = api.Ctx(n, R * r, r, dt)
+
+        def trunc():
+            api.tucker_round(ctx2, yr, 1e-3)
+
+        ts, work = [], None
+        for rep in range(4):
+            api.tucker_apply(pb, x, yr)
+            torch.cuda.synchronize()
+            flush.zero_()
+            L.tpcg_profile_reset()
+            L.tpcg_profile_enable(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(main)
+            trunc()
+            b.record(main)
+            torch.cuda.synchronize()
+            L.tpcg_profile_enable(0)
+            if rep > 0:
+                ts.append(a.elapsed_time(b))
+            work = _profile(L, lib)
+        ms = float(np.median(ts))
+        fl = sum(work[k]["flops"] for k in ("zgemm", "zblk", "gram", "proj"))
+        cls = {k: round(work[k]["ms"], 3) for k in ("qr", "zblk", "zgemm", "gram", "eig", "proj")}
+        ach = fl / (ms * 1e-3) / 1e12
+        out["kernels"][f"round_{name}"] = {"ms": ms, "contraction_flops": fl, "achieved_tflops": ach,
+                                           "bound": "alu", "frac": ach / alu[dt], "class_ms": cls,
+                                           "k": R * r}
+        del pb, x, y, v, ctx, yr, ctx2
+        torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.kernels > 0:
+        run_kernels(args)
     elif args.large > 0:
         run_large(args)
     elif args.mix > 0:

@@ -50,6 +50,9 @@ __host__ __device__ constexpr double jacobi_tau() { return sizeof(T) == 8 ? 1e-1
 // one-sided Jacobi (FP32): a pair is orthogonal once |a_p . a_q| <= HJ_TAU |a_p| |a_q|.  The normalised columns
 // are then eigenvectors orthonormal to about HJ_TAU; the FP32 dot product itself resolves about 4e-7 at 128 rows.
 constexpr float HJ_TAU = 2e-6f;
+// a sweep whose rotations all had |a_p . a_q| <= HJ_TAU_LAST |a_p| |a_q| is the last one: cyclic Jacobi converges
+// quadratically, so the sweep after it would only meet products near HJ_TAU_LAST^2 ~ HJ_TAU
+constexpr float HJ_TAU_LAST = 1.5e-3f;
 
 // Energy of the Gram outside the Rayleigh-Ritz subspace (trace(G) minus the Ritz values; 0 when the
 // eigensolver's input is the Gram itself).  The FP32 rule (trace minus kept) counts it implicitly.
@@ -867,7 +870,9 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_v_kernel(RoundPlan* pl
 //     eigenvalues; no rotation matrix is accumulated.  Pair (a_p, a_q) with alpha = |a_p|^2, beta = |a_q|^2,
 //     gamma = a_p . a_q rotates when gamma^2 > tau^2 alpha beta: zeta = (beta - alpha) / (2 gamma),
 //     t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), a_p <- c a_p - s a_q, a_q <- s a_p + c a_q, and the
-//     norms follow as alpha - t gamma, beta + t gamma (recomputed exactly at every sweep start).
+//     norms follow as alpha - t gamma, beta + t gamma (recomputed exactly at every sweep start).  Sweeps end
+//     when none rotates, or after a sweep whose rotations were all below HJ_TAU_LAST (quadratic convergence
+//     leaves the next sweep's products near HJ_TAU).
 //  3. The columns are the players of a round-robin tournament (circle method, one fixed player) on 8 NWA
 //     players, NWA in {2, 4, 8, 16} the fewest warps whose ring holds the rc columns of L: four pair slots per
 //     warp, every lane holding four rows of each of its warp's eight columns in registers.  A step computes
@@ -1027,6 +1032,7 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
     const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0;
     const float floor_g = 1e-12f * tr;      // products below this are rounding noise of the factor
     const float tau2 = tau * tau;
+    const float taul2 = HJ_TAU_LAST * HJ_TAU_LAST;
     int nsweeps = 0, buf = 0;
     for (int sweep = 0; sweep < max_sweeps && rc > 1; ++sweep) {
         ++nsweeps;
@@ -1038,7 +1044,7 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
             aT[j] = warp_sum(st);
             aB[j] = warp_sum(sb);
         }
-        int rot = 0;
+        int rot = 0, big = 0;
         for (int step = 0; step < P - 1; ++step) {
             if (active) {
                 float g[HJ_SLOTS];
@@ -1069,6 +1075,7 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
                     s = c * t;
                     tg = t * gm;
                     rot = 1;
+                    if (gm * gm > taul2 * al * be) big = 1;
                 }
 #pragma unroll
                 for (int j = 0; j < HJ_SLOTS; ++j) {
@@ -1142,6 +1149,7 @@ __global__ void __launch_bounds__(HJ_THREADS) hestenes_eig_kernel(RoundPlan* pla
             buf ^= 1;
         }
         if (!__syncthreads_or(rot)) break;
+        if (!__syncthreads_or(big)) break;   // only small rotations this sweep: converged to about HJ_TAU
     }
     // ---- 3. eigenvalues (exact squared norms), decreasing order, truncation rule, normalised kept columns
     __syncthreads();

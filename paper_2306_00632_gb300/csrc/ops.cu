@@ -37,49 +37,16 @@ int set_zero(tucker_t* t, cudaStream_t st) { return set_plain(t, 0, 0, 0, st); }
 // y = A x  /  y = f - A x  (eq. tt_product): Y_t[:, base_t + j k_t + c] = K_t^j X_t[:, c];
 // bands[((j*3 + t)*(2p+1) + d)*n + i] = K_t^j[i, i + d - p].  The extra "term" j = R copies F_t into the
 // first columns for the residual.
+// Grid: x = 128-row tiles, y = (term, chunk of APPLY_CB input columns), z = mode; a thread owns one row and
+// keeps its 2p+1 band entries in registers across its chunk's columns (rows of X are reused from L1 by the
+// neighbouring lanes).  Enough CTAs for the SMs at n = 512 (4 x 20 x 10 x 3 at k = 80, R = 19).
 // --------------------------------------------------------------------------------------------------
-template <typename T>
-__global__ void apply_kernel(const T* __restrict__ bands, int n, int p, int R, const TuckerDesc* __restrict__ xd,
-                             const T* X0, const T* X1, const T* X2, T* Y0, T* Y1, T* Y2, int cap,
-                             const TuckerDesc* __restrict__ fd, const T* F0, const T* F1, const T* F2) {
-    const int t = blockIdx.z, j = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const T* X = t == 0 ? X0 : (t == 1 ? X1 : X2);
-    T* Y = t == 0 ? Y0 : (t == 1 ? Y1 : Y2);
-    const int kx = xd->rank[t];
-    const int base = fd ? fd->rank[t] : 0;
-    if (j == R) {   // copy the rhs factor
-        if (base > cap) return;
-        const T* F = t == 0 ? F0 : (t == 1 ? F1 : F2);
-        for (int c = 0; c < base; ++c) Y[i + (long long)c * n] = F[i + (long long)c * n];
-        return;
-    }
-    if (base + (long long)R * kx > cap) return;   // capacity violated: flagged by the descriptor kernel
-    const int bw = 2 * p + 1;
-    T band[11];
-    const T* bj = bands + ((long long)(j * 3 + t) * bw) * n;
-#pragma unroll
-    for (int d = 0; d < 11; ++d) band[d] = (d < bw) ? bj[(long long)d * n + i] : T(0);
-    const int col0 = base + j * kx;
-    for (int c = 0; c < kx; ++c) {
-        const T* xc = X + (long long)c * n;
-        T acc = T(0);
-#pragma unroll
-        for (int d = 0; d < 11; ++d) {
-            if (d >= bw) break;
-            const int ii = i + d - p;
-            if (ii >= 0 && ii < n) acc = fma(band[d], xc[ii], acc);
-        }
-        Y[i + (long long)(col0 + c) * n] = acc;
-    }
-}
+constexpr int APPLY_CB = 8;
 
 // output descriptor of the apply: blocks (f) + (j, b) for every term j and input block b
-__global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const double* __restrict__ w, int R,
-                                  double sign, const TuckerDesc* fdsc, TuckerDesc* yd, int cap,
-                                  int* err, double* prof, int n, int p, int elt) {
-    if (threadIdx.x != 0) return;
+__device__ void apply_desc(const TuckerDesc* __restrict__ xd, const double* __restrict__ w, int R, double sign,
+                           const TuckerDesc* fdsc, TuckerDesc* yd, int cap, int* err, double* prof, int n, int p,
+                           int elt) {
     if (prof) {   // algorithmic work of the banded products: bands read once, X read, Y written
         double cols = (double)xd->rank[0] + xd->rank[1] + xd->rank[2];
         prof[2 * PK_APPLY] += 2.0 * (2 * p + 1) * (double)n * R * cols;
@@ -114,29 +81,123 @@ __global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const doubl
     for (int t = 0; t < 3; ++t) yd->rank[t] = base[t] + R * kx[t];
 }
 
+// yd: when non-null, block (0, 0, 0) also writes the output descriptor (only when yd is not read by this kernel,
+// i.e. not for appends).  P (the degree) is a template parameter: the 2P+1 taps are unrolled, and row tiles
+// that touch neither end of the band (all but the first and last) run without bounds checks.
+template <typename T, int P>
+__global__ void __launch_bounds__(128) apply_kernel(const T* __restrict__ bands, int n, int R, int nchunk,
+                                                    const TuckerDesc* __restrict__ xd, const T* X0, const T* X1,
+                                                    const T* X2, T* Y0, T* Y1, T* Y2, int cap,
+                                                    const TuckerDesc* __restrict__ fd, const T* F0, const T* F1,
+                                                    const T* F2, TuckerDesc* yd, const double* __restrict__ w,
+                                                    double sign, int* err, double* prof) {
+    constexpr int BW = 2 * P + 1;
+    if (yd && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+        apply_desc(xd, w, R, sign, fd, yd, cap, err, prof, n, P, (int)sizeof(T));
+    const int t = blockIdx.z, j = blockIdx.y / nchunk, chunk = blockIdx.y % nchunk;
+    const int i0 = blockIdx.x * blockDim.x;
+    const int i = i0 + threadIdx.x;
+    const T* X = t == 0 ? X0 : (t == 1 ? X1 : X2);
+    T* Y = t == 0 ? Y0 : (t == 1 ? Y1 : Y2);
+    const int kx = xd->rank[t];
+    const int base = fd ? fd->rank[t] : 0;
+    const int c0 = chunk * APPLY_CB;
+    if (j == R) {   // copy the rhs factor
+        if (base > cap || i >= n) return;
+        const T* F = t == 0 ? F0 : (t == 1 ? F1 : F2);
+        for (int c = c0; c < base; c += nchunk * APPLY_CB)
+            for (int q = c; q < c + APPLY_CB && q < base; ++q) Y[i + (long long)q * n] = F[i + (long long)q * n];
+        return;
+    }
+    if (base + (long long)R * kx > cap) return;   // capacity violated: flagged by the descriptor
+    if (c0 >= kx || i >= n) return;
+    T band[BW];
+    const T* bj = bands + ((long long)(j * 3 + t) * BW) * n;
+#pragma unroll
+    for (int d = 0; d < BW; ++d) band[d] = __ldg(bj + (long long)d * n + i);
+    const bool interior = i0 >= P && i0 + (int)blockDim.x + P <= n;   // uniform over the block
+    const long long col0 = base + (long long)j * kx;
+    // columns c0, c0 + nchunk CB, ... (chunks stride over the columns when kx exceeds nchunk CB)
+    for (int cb = c0; cb < kx; cb += nchunk * APPLY_CB) {
+        const T* xr = X + (long long)cb * n + i - P;   // tap d of column cb + q at xr[d + q n]
+        T* yr = Y + (col0 + cb) * n + i;
+        if (interior && cb + APPLY_CB <= kx) {      // full chunk, no bounds: all loads in flight together
+            T acc[APPLY_CB];
+#pragma unroll
+            for (int q = 0; q < APPLY_CB; ++q) {
+                acc[q] = T(0);
+#pragma unroll
+                for (int d = 0; d < BW; ++d) acc[q] = fma(band[d], __ldg(xr + d + (long long)q * n), acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < APPLY_CB; ++q) yr[(long long)q * n] = acc[q];
+        } else {
+            for (int q = 0; q < APPLY_CB && cb + q < kx; ++q) {
+                T acc = T(0);
+#pragma unroll
+                for (int d = 0; d < BW; ++d) {
+                    const int ii = i + d - P;
+                    if (ii >= 0 && ii < n) acc = fma(band[d], xr[d + (long long)q * n], acc);
+                }
+                yr[(long long)q * n] = acc;
+            }
+        }
+    }
+}
+
+template <typename T>
+static int launch_apply(int p, dim3 grid, cudaStream_t st, const T* bands, int n, int R, int nchunk,
+                        const TuckerDesc* xd, const T* X0, const T* X1, const T* X2, T* Y0, T* Y1, T* Y2, int cap,
+                        const TuckerDesc* fd, const T* F0, const T* F1, const T* F2, TuckerDesc* yd, const double* w,
+                        double sign, int* err, double* prof) {
+#define TPCG_APPLY_P(PP)                                                                                           \
+    apply_kernel<T, PP><<<grid, 128, 0, st>>>(bands, n, R, nchunk, xd, X0, X1, X2, Y0, Y1, Y2, cap, fd, F0, F1, F2, \
+                                              yd, w, sign, err, prof)
+    switch (p) {
+        case 1: TPCG_APPLY_P(1); break;
+        case 2: TPCG_APPLY_P(2); break;
+        case 3: TPCG_APPLY_P(3); break;
+        case 4: TPCG_APPLY_P(4); break;
+        case 5: TPCG_APPLY_P(5); break;
+        default:
+            set_error("apply: degree out of range (1..5)");
+            return TPCG_E_INVALID;
+    }
+#undef TPCG_APPLY_P
+    TPCG_CHECK_LAUNCH();
+    return TPCG_OK;
+}
+
+__global__ void apply_desc_kernel(const TuckerDesc* __restrict__ xd, const double* __restrict__ w, int R,
+                                  double sign, const TuckerDesc* fdsc, TuckerDesc* yd, int cap,
+                                  int* err, double* prof, int n, int p, int elt) {
+    if (threadIdx.x != 0) return;
+    apply_desc(xd, w, R, sign, fdsc, yd, cap, err, prof, n, p, elt);
+}
+
+// column chunks per term: enough to cover the largest input rank a y of this capacity can take (cap / R)
+static inline int apply_chunks(int cap, int R) {
+    const int kmax = std::max(1, cap / std::max(R, 1));
+    return std::min(64, (kmax + APPLY_CB - 1) / APPLY_CB);
+}
+
 template <typename T>
 int apply_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, bool residual, cudaStream_t st, const tucker_t* rhs,
                int* err) {
     const int n = pb->n;
     if (!err) err = reinterpret_cast<int*>(pb->d_scal + 60);
-    dim3 grid((n + 127) / 128, pb->R + (residual ? 1 : 0), 3);
+    const int nchunk = apply_chunks(y->cap, pb->R);
+    dim3 grid((n + 127) / 128, (pb->R + (residual ? 1 : 0)) * nchunk, 3);
     const tucker_t* f = rhs ? rhs : &pb->f;
     prof_begin(PK_APPLY, st);
-    apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
-                                          static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
-                                          static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
-                                          static_cast<T*>(y->U[0]), static_cast<T*>(y->U[1]),
-                                          static_cast<T*>(y->U[2]), y->cap,
-                                          residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
-                                          static_cast<const T*>(f->U[0]), static_cast<const T*>(f->U[1]),
-                                          static_cast<const T*>(f->U[2]));
-    TPCG_CHECK_LAUNCH();
-    apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R,
-                                        residual ? -1.0 : 1.0,
-                                        residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
-                                        static_cast<TuckerDesc*>(y->desc), y->cap, err, prof_dev(), n, pb->p,
-                                        (int)sizeof(T));
-    TPCG_CHECK_LAUNCH();
+    TPCG_TRY(launch_apply<T>(pb->p, grid, st, static_cast<const T*>(pb->d_bands), n, pb->R, nchunk,
+                             static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                             static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]), static_cast<T*>(y->U[0]),
+                             static_cast<T*>(y->U[1]), static_cast<T*>(y->U[2]), y->cap,
+                             residual ? static_cast<const TuckerDesc*>(f->desc) : nullptr,
+                             static_cast<const T*>(f->U[0]), static_cast<const T*>(f->U[1]),
+                             static_cast<const T*>(f->U[2]), static_cast<TuckerDesc*>(y->desc), pb->d_w,
+                             residual ? -1.0 : 1.0, err, prof_dev()));
     prof_end(PK_APPLY, st);
     return TPCG_OK;
 }
@@ -146,15 +207,16 @@ template <typename T>
 int apply_append_impl(tpcg_problem pb, const tucker_t* x, tucker_t* y, double sign, cudaStream_t st, int* err) {
     const int n = pb->n;
     if (!err) err = reinterpret_cast<int*>(pb->d_scal + 60);
-    dim3 grid((n + 127) / 128, pb->R, 3);
+    const int nchunk = apply_chunks(y->cap, pb->R);
+    dim3 grid((n + 127) / 128, pb->R * nchunk, 3);
     prof_begin(PK_APPLY, st);
-    apply_kernel<T><<<grid, 128, 0, st>>>(static_cast<const T*>(pb->d_bands), n, pb->p, pb->R,
-                                          static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
-                                          static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]),
-                                          static_cast<T*>(y->U[0]), static_cast<T*>(y->U[1]),
-                                          static_cast<T*>(y->U[2]), y->cap, static_cast<const TuckerDesc*>(y->desc),
-                                          nullptr, nullptr, nullptr);
-    TPCG_CHECK_LAUNCH();
+    // y's descriptor is read by every block (its old ranks are the column base): it is updated afterwards
+    TPCG_TRY(launch_apply<T>(pb->p, grid, st, static_cast<const T*>(pb->d_bands), n, pb->R, nchunk,
+                             static_cast<const TuckerDesc*>(x->desc), static_cast<const T*>(x->U[0]),
+                             static_cast<const T*>(x->U[1]), static_cast<const T*>(x->U[2]), static_cast<T*>(y->U[0]),
+                             static_cast<T*>(y->U[1]), static_cast<T*>(y->U[2]), y->cap,
+                             static_cast<const TuckerDesc*>(y->desc), nullptr, nullptr, nullptr, nullptr, nullptr,
+                             0.0, nullptr, nullptr));
     apply_desc_kernel<<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(x->desc), pb->d_w, pb->R, sign,
                                         static_cast<const TuckerDesc*>(y->desc), static_cast<TuckerDesc*>(y->desc),
                                         y->cap, err, prof_dev(), n, pb->p, (int)sizeof(T));
@@ -521,31 +583,34 @@ __global__ void plan_fd_kernel(const TuckerDesc* __restrict__ sd, const T* S0, c
     counts[0] = 3;
 }
 
+// E_(t,j) = D_(t,j) Z_t: grid x = row tiles, y = term j, z = mode; a thread computes its row's factor
+// exp(-alpha_j c_t lambda_l / lambda_min) / mu_l^2 once (in the compute precision) and scales that row of all r
+// input columns (coalesced along the rows)
 template <typename T>
 __global__ void fd_scale_kernel(const TuckerDesc* __restrict__ sd, const T* U0, const T* U1, const T* U2,
                                 const T* __restrict__ lam, const T* __restrict__ mu, const double* __restrict__ alpha,
                                 double lmin, double c0, double c1, double c2, int n1, int n2, int RP, T* E0, T* E1,
                                 T* E2, int vcap) {
-    const int t = blockIdx.z;
+    const int t = blockIdx.z, j = blockIdx.y;
     const int r = sd->rank[t];
     const int n = n1 + n2;
-    const int col = blockIdx.y;          // j * r + c
-    if (col >= RP * r || RP * r > vcap) return;
-    const int j = col / r, c = col % r;
+    if (j >= RP || RP * r > vcap) return;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
     const T* U = t == 0 ? U0 : (t == 1 ? U1 : U2);
     T* E = t == 0 ? E0 : (t == 1 ? E1 : E2);
     const long long cols = (long long)RP * r;
     // direction weight c_t (1 for the Poisson operator; mu + (lambda + mu) delta_ti for elasticity block i)
-    const double aj = alpha[j] * (t == 0 ? c0 : (t == 1 ? c1 : c2)) / lmin;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
-        const T dl = (T)exp(-aj * (double)lam[l]);
-        if (l < n1) {
-            const T m = mu[l];
-            E[l + (long long)col * n1] = dl * U[l + (long long)c * n1] / (m * m);
-        } else {
-            const int q = l - n1;
-            E[(long long)n1 * cols + q + (long long)col * n2] = dl * U[(long long)n1 * r + q + (long long)c * n2];
-        }
+    const T aj = (T)(alpha[j] * (t == 0 ? c0 : (t == 1 ? c1 : c2)) / lmin);
+    const T dl = exp(-aj * lam[l]);
+    if (l < n1) {
+        const T m = mu[l];
+        const T f = dl / (m * m);
+        for (int c = 0; c < r; ++c) E[l + (long long)(j * r + c) * n1] = f * U[l + (long long)c * n1];
+    } else {
+        const int q = l - n1;
+        for (int c = 0; c < r; ++c)
+            E[(long long)n1 * cols + q + (long long)(j * r + c) * n2] = dl * U[(long long)n1 * r + q + (long long)c * n2];
     }
 }
 
@@ -566,8 +631,15 @@ __global__ void fd_scatter_kernel(const TuckerDesc* __restrict__ sd, const T* A0
 }
 
 __global__ void fd_desc_kernel(const TuckerDesc* __restrict__ sd, const double* __restrict__ omega, double lmin,
-                               int RP, TuckerDesc* vd, int vcap, int* err) {
+                               int RP, TuckerDesc* vd, int vcap, int* err, double* prof, int n, int n1, int n2, int p,
+                               int elt) {
     if (threadIdx.x != 0) return;
+    if (prof) {   // algorithmic work of Alg. 4 per input column: W^T gather, sine transforms, R_P scalings, W scatter
+        const double cols = (double)sd->rank[0] + sd->rank[1] + sd->rank[2];
+        const double lg = n1 > 1 ? log2((double)n1) : 1.0;
+        prof[2 * PK_FD] += (1.0 + RP) * cols * (5.0 * n1 * lg + 4.0 * (p + 1) * n + 2.0 * (double)n * n2);
+        prof[2 * PK_FD + 1] += (double)elt * (double)n * cols * (2.0 + 2.0 * RP);
+    }
     bool ok = RP * sd->nblk <= TPCG_MAX_BLOCKS;
     for (int t = 0; t < 3; ++t) ok = ok && (RP * sd->rank[t] <= vcap);
     if (!ok) {
@@ -625,7 +697,7 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
     else
         TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, n1, rc, st)));
     if (n2 > 0) TPCG_TRY((launch_gemm<T, true, false>(ga + 3, counts, 3, 1, n2, rc, st)));
-    dim3 g2(2, RP * rc, 3);
+    dim3 g2((n + 255) / 256, RP, 3);
     fd_scale_kernel<T><<<g2, 256, 0, st>>>(sd, buf[0][1], buf[1][1], buf[2][1], static_cast<const T*>(pb->d_lam),
                                            static_cast<const T*>(pb->d_mu), pb->d_alpha, lmin, cw[0], cw[1], cw[2], n1, n2, RP,
                                            buf[0][2], buf[1][2], buf[2][2], v->cap);
@@ -643,7 +715,7 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
     TPCG_CHECK_LAUNCH();
     if (n2 > 0) TPCG_TRY((launch_gemm<T, false, false>(ga + 9, counts, 3, 1, n, RP * rc, st)));
     fd_desc_kernel<<<1, 32, 0, st>>>(sd, pb->d_omega, lmin, RP, static_cast<TuckerDesc*>(v->desc), v->cap,
-                                     err);
+                                     err, prof_dev(), n, n1, n2, pb->p, (int)sizeof(T));
     TPCG_CHECK_LAUNCH();
     prof_end(PK_FD, st);
     return TPCG_OK;

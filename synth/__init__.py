@@ -56,15 +56,15 @@ TWIST_128 = Problem(kind="twist", degree=3, n=128, amp=amp_from_seed(7), seed=7)
 TWIST_512 = Problem(kind="twist", degree=3, n=512, amp=amp_from_seed(7), seed=7)      # twisted annulus p=3 n=512
 
 
-def batch_mix(count: int, seed0: int = 0):
+def batch_mix(count: int, seed0: int = 0, caps=(20, 60)):
     """Mixed batch of independent Poisson problems: n in {32..256}, p in {2,3,4},
-    amplitude in [0, 0.3], rank caps in [20, 60] (one record per solve)."""
+    amplitude in [0, 0.3], rank caps uniform in [caps[0], caps[1]] (one record per solve)."""
     ns = (32, 64, 96, 128, 192, 256)
     out = []
     for s in range(seed0, seed0 + count):
         n = ns[int(unit_from_seed(s, 2) * len(ns))]
         p = 2 + int(unit_from_seed(s, 3) * 3)
-        cap = 20 + int(unit_from_seed(s, 4) * 41)
+        cap = caps[0] + int(unit_from_seed(s, 4) * (caps[1] - caps[0] + 1))
         out.append((Problem(kind="twist", degree=p, n=n, amp=amp_from_seed(s), seed=s), cap))
     return out
 
