@@ -525,6 +525,8 @@ def run_gpu(args):
            "single": {"iters": [int(s.iters) for s in single], "true_rel_res": [float(s.true_rel_res) for s in single]},
            "gpu_launches": int(launches), "roofline": roof,
            "kernel_ms_single": {k: round(v["ms"], 3) for k, v in prof.items() if k != "sweeps"},
+           "kernel_tflops_single": {k: round(v["flops"] / (v["ms"] * 1e9), 3) for k, v in prof.items()
+                                    if k in ("zgemm", "zblk", "gram", "proj", "eig", "apply", "fd") and v["ms"] > 0},
            "eig_sweeps_per_gram": prof["sweeps"]["flops"] / max(prof["sweeps"]["bytes"], 1.0),
            "clocks": clk}
 

@@ -583,35 +583,64 @@ __global__ void plan_fd_kernel(const TuckerDesc* __restrict__ sd, const T* S0, c
     counts[0] = 3;
 }
 
-// E_(t,j) = D_(t,j) Z_t: grid x = row tiles, y = term j, z = mode; a thread computes its row's factor
-// exp(-alpha_j c_t lambda_l / lambda_min) / mu_l^2 once (in the compute precision) and scales that row of all r
-// input columns (coalesced along the rows)
+// E_(t,j) = D_(t,j) Z_t: grid x = 128-row tiles, y = (term j, group of FD_CG input columns), z = mode; a thread
+// computes its row's factor exp(-alpha_j c_t lambda_l / lambda_min) / mu_l^2 once (in the compute precision) and
+// scales that row of its group's columns (coalesced along the rows, the group's loads in flight together)
+constexpr int FD_CG = 16;
+
 template <typename T>
-__global__ void fd_scale_kernel(const TuckerDesc* __restrict__ sd, const T* U0, const T* U1, const T* U2,
-                                const T* __restrict__ lam, const T* __restrict__ mu, const double* __restrict__ alpha,
-                                double lmin, double c0, double c1, double c2, int n1, int n2, int RP, T* E0, T* E1,
-                                T* E2, int vcap) {
-    const int t = blockIdx.z, j = blockIdx.y;
+__global__ void __launch_bounds__(128) fd_scale_kernel(const TuckerDesc* __restrict__ sd, const T* __restrict__ U0,
+                                                       const T* __restrict__ U1, const T* __restrict__ U2,
+                                                       const T* __restrict__ lam, const T* __restrict__ mu,
+                                                       const double* __restrict__ alpha, double lmin, double c0,
+                                                       double c1, double c2, int n1, int n2, int RP, int ncg,
+                                                       T* __restrict__ E0, T* __restrict__ E1, T* __restrict__ E2,
+                                                       int vcap) {
+    const int t = blockIdx.z, j = blockIdx.y / ncg, cg = blockIdx.y % ncg;
     const int r = sd->rank[t];
     const int n = n1 + n2;
     if (j >= RP || RP * r > vcap) return;
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
-    const T* U = t == 0 ? U0 : (t == 1 ? U1 : U2);
-    T* E = t == 0 ? E0 : (t == 1 ? E1 : E2);
+    const T* __restrict__ U = t == 0 ? U0 : (t == 1 ? U1 : U2);
+    T* __restrict__ E = t == 0 ? E0 : (t == 1 ? E1 : E2);
     const long long cols = (long long)RP * r;
     // direction weight c_t (1 for the Poisson operator; mu + (lambda + mu) delta_ti for elasticity block i)
     const T aj = (T)(alpha[j] * (t == 0 ? c0 : (t == 1 ? c1 : c2)) / lmin);
     const T dl = exp(-aj * lam[l]);
-    if (l < n1) {
-        const T m = mu[l];
-        const T f = dl / (m * m);
-        for (int c = 0; c < r; ++c) E[l + (long long)(j * r + c) * n1] = f * U[l + (long long)c * n1];
-    } else {
-        const int q = l - n1;
-        for (int c = 0; c < r; ++c)
-            E[(long long)n1 * cols + q + (long long)(j * r + c) * n2] = dl * U[(long long)n1 * r + q + (long long)c * n2];
+    for (int cb = cg * FD_CG; cb < r; cb += ncg * FD_CG) {
+        const int ce = cb + FD_CG < r ? cb + FD_CG : r;
+        if (l < n1) {
+            const T m = mu[l];
+            const T f = dl / (m * m);
+#pragma unroll 4
+            for (int c = cb; c < ce; ++c) E[l + (long long)(j * r + c) * n1] = f * U[l + (long long)c * n1];
+        } else {
+            const int q = l - n1;
+#pragma unroll 4
+            for (int c = cb; c < ce; ++c)
+                E[(long long)n1 * cols + q + (long long)(j * r + c) * n2] = dl * U[(long long)n1 * r + q + (long long)c * n2];
+        }
     }
+}
+
+// z2_t (n2 x r) = v2u2^T S_t (n2 <= 3 rows, K = n): one warp per output entry, fixed-order shuffle reduction
+template <typename T>
+__global__ void fd_v2_kernel(const TuckerDesc* __restrict__ sd, const T* __restrict__ v2u2, const T* S0,
+                             const T* S1, const T* S2, T* Ub0, T* Ub1, T* Ub2, int n, int n1, int n2, int RP,
+                             int vcap) {
+    const int t = blockIdx.z;
+    const int r = sd->rank[t];
+    if (RP * r > vcap) return;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= n2 * r) return;
+    const int q = w % n2, c = w / n2;
+    const T* S = t == 0 ? S0 : (t == 1 ? S1 : S2);
+    T* Ub = t == 0 ? Ub0 : (t == 1 ? Ub1 : Ub2);
+    T acc = T(0);
+    for (int i = lane; i < n; i += 32) acc = fma(v2u2[i + (long long)q * n], S[i + (long long)c * n], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) Ub[(long long)n1 * r + q + (long long)c * n2] = acc;
 }
 
 template <typename T>
@@ -696,11 +725,17 @@ int fd_impl(tpcg_problem pb, tpcg_ctx c, const tucker_t* s, tucker_t* v, cudaStr
         TPCG_TRY(launch_chirp<T>(pb, 0, sd, 1, RP, v->cap, rc, fx, fy, n1, n1, st));
     else
         TPCG_TRY((launch_gemm<T, true, false>(ga, counts, 3, 1, n1, rc, st)));
-    if (n2 > 0) TPCG_TRY((launch_gemm<T, true, false>(ga + 3, counts, 3, 1, n2, rc, st)));
-    dim3 g2((n + 255) / 256, RP, 3);
-    fd_scale_kernel<T><<<g2, 256, 0, st>>>(sd, buf[0][1], buf[1][1], buf[2][1], static_cast<const T*>(pb->d_lam),
+    if (n2 > 0) {
+        fd_v2_kernel<T><<<dim3((n2 * rc + 7) / 8, 1, 3), 256, 0, st>>>(
+            sd, static_cast<const T*>(pb->d_v2u2), static_cast<const T*>(s->U[0]), static_cast<const T*>(s->U[1]),
+            static_cast<const T*>(s->U[2]), buf[0][1], buf[1][1], buf[2][1], n, n1, n2, RP, v->cap);
+        TPCG_CHECK_LAUNCH();
+    }
+    const int ncg = (rc + FD_CG - 1) / FD_CG;
+    dim3 g2((n + 127) / 128, RP * ncg, 3);
+    fd_scale_kernel<T><<<g2, 128, 0, st>>>(sd, buf[0][1], buf[1][1], buf[2][1], static_cast<const T*>(pb->d_lam),
                                            static_cast<const T*>(pb->d_mu), pb->d_alpha, lmin, cw[0], cw[1], cw[2], n1, n2, RP,
-                                           buf[0][2], buf[1][2], buf[2][2], v->cap);
+                                           ncg, buf[0][2], buf[1][2], buf[2][2], v->cap);
     TPCG_CHECK_LAUNCH();
     const T* ex[3] = {buf[0][2], buf[1][2], buf[2][2]};
     T* ey[3] = {buf[0][3], buf[1][3], buf[2][3]};
