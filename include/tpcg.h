@@ -320,6 +320,11 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   FP32 variant above order 128 tracks the eigenvalues by rotation updates and can misjudge the discarded
  *   energy by more than the FP32 Gram's resolution. */
 #define TPCG_OPT_RR 6
+/*   TPCG_OPT_GRAM_MIN_K: the mode Grams of ST-HOSVD (Alg. 1 step 3) are split-K reductions into at most 64 partial
+ *   Grams summed in a fixed order; a value k > 0 gives every partial at least k of the reduction (fewer, longer
+ *   partials: less partial traffic and block start-up, which pays when many solves share the device), 0 (default)
+ *   always uses the most partials.  Read when a truncation is launched or captured. */
+#define TPCG_OPT_GRAM_MIN_K 7
 int tpcg_set_option(int key, long long value);
 
 /* Best exponential sum s_R(lambda) = sum_j omega_j exp(-alpha_j lambda) for 1/lambda on [1, M] in the maximum

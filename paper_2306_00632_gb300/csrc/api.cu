@@ -39,22 +39,62 @@ static int dmalloc(void** p, size_t bytes, std::vector<void*>* owned) {
     return TPCG_OK;
 }
 
+namespace {
+// one private non-blocking stream per host thread for the blocking copies below (created on first use)
+struct PrivStream {
+    cudaStream_t s = nullptr;
+    ~PrivStream() {
+        if (s) cudaStreamDestroy(s);
+    }
+};
+thread_local PrivStream t_priv;
+
+int priv_stream(cudaStream_t* out) {
+    if (!t_priv.s && cudaStreamCreateWithFlags(&t_priv.s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        t_priv.s = nullptr;
+        set_error("cudaStreamCreateWithFlags failed");
+        return TPCG_E_CUDA;
+    }
+    *out = t_priv.s;
+    return TPCG_OK;
+}
+}  // namespace
+
+int sync_to_device(void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return TPCG_OK;
+    cudaStream_t s = nullptr;
+    TPCG_TRY(priv_stream(&s));
+    TPCG_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    TPCG_CUDA(cudaStreamSynchronize(s));
+    return TPCG_OK;
+}
+
+int sync_zero(void* dst, size_t bytes) {
+    if (bytes == 0) return TPCG_OK;
+    cudaStream_t s = nullptr;
+    TPCG_TRY(priv_stream(&s));
+    TPCG_CUDA(cudaMemsetAsync(dst, 0, bytes, s));
+    TPCG_CUDA(cudaStreamSynchronize(s));
+    return TPCG_OK;
+}
+
 // upload host doubles converted to the compute dtype
 static int upload(void** dst, const double* src, size_t count, int dtype, std::vector<void*>* owned) {
     TPCG_TRY(dmalloc(dst, std::max<size_t>(count, 1) * elt_of(dtype), owned));
     if (count == 0) return TPCG_OK;
     if (dtype == TPCG_F64) {
-        TPCG_CUDA(cudaMemcpy(*dst, src, count * sizeof(double), cudaMemcpyHostToDevice));
+        TPCG_TRY(sync_to_device(*dst, src, count * sizeof(double)));
     } else {
         std::vector<float> tmp(src, src + count);
-        TPCG_CUDA(cudaMemcpy(*dst, tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice));
+        TPCG_TRY(sync_to_device(*dst, tmp.data(), count * sizeof(float)));
     }
     return TPCG_OK;
 }
 
 static int upload_int(int** dst, const int* src, size_t count, std::vector<void*>* owned) {
     TPCG_TRY(dmalloc(reinterpret_cast<void**>(dst), std::max<size_t>(count, 1) * sizeof(int), owned));
-    if (count) TPCG_CUDA(cudaMemcpy(*dst, src, count * sizeof(int), cudaMemcpyHostToDevice));
+    if (count) TPCG_TRY(sync_to_device(*dst, src, count * sizeof(int)));
     return TPCG_OK;
 }
 
@@ -309,10 +349,12 @@ extern "C" int tpcg_ctx_create(int n, int max_cols, int rank_cap, int dtype, tpc
             return s;
         }
     }
-    if (cudaMemset(c->scal, 0, 256 * sizeof(double)) != cudaSuccess) {
-        set_error("cudaMemset failed");
-        tpcg_ctx_destroy(c);
-        return TPCG_E_CUDA;
+    {
+        const int s = sync_zero(c->scal, 256 * sizeof(double));
+        if (s != TPCG_OK) {
+            tpcg_ctx_destroy(c);
+            return s;
+        }
     }
     *out = c;
     return TPCG_OK;
@@ -520,8 +562,7 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
     const int dt = a->dtype;
     if ((s = upload(&pb->d_bands, pb->bands.data(), pb->bands.size(), dt, nullptr))) return fail(s);
     if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_w), a->R * sizeof(double), nullptr))) return fail(s);
-    if (cudaMemcpy(pb->d_w, pb->w.data(), a->R * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(TPCG_E_CUDA);
+    if ((s = sync_to_device(pb->d_w, pb->w.data(), a->R * sizeof(double)))) return fail(s);
     if ((s = upload(&pb->d_lam, pb->lam.data(), n, dt, nullptr))) return fail(s);
     if ((s = upload(&pb->d_mu, pb->mu.data(), n1, dt, nullptr))) return fail(s);
     if ((s = upload_int(&pb->d_wrow, pb->w_rowptr.data(), n + 1, nullptr))) return fail(s);
@@ -539,11 +580,10 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
     }
     if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_omega), a->RP * sizeof(double), nullptr))) return fail(s);
     if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_alpha), a->RP * sizeof(double), nullptr))) return fail(s);
-    if (cudaMemcpy(pb->d_omega, pb->omega.data(), a->RP * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(pb->d_alpha, pb->alpha.data(), a->RP * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-        return fail(TPCG_E_CUDA);
+    if ((s = sync_to_device(pb->d_omega, pb->omega.data(), a->RP * sizeof(double)))) return fail(s);
+    if ((s = sync_to_device(pb->d_alpha, pb->alpha.data(), a->RP * sizeof(double)))) return fail(s);
     if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_scal), 64 * sizeof(double), nullptr))) return fail(s);
-    cudaMemset(pb->d_scal, 0, 64 * sizeof(double));
+    if ((s = sync_zero(pb->d_scal, 64 * sizeof(double)))) return fail(s);
     // rhs tensor
     tucker_t& f = pb->f;
     f.dtype = dt;
@@ -776,7 +816,7 @@ int tpcg::ensure_tensors(tpcg_ctx c, int count) {
         for (int q = 0; q < 3; ++q) TPCG_TRY(dmalloc(&t.U[q], (size_t)n * cap * c->elt, &c->owned));
         TPCG_TRY(dmalloc(&t.core, (size_t)t.core_cap * c->elt, &c->owned));
         TPCG_TRY(dmalloc(&t.desc, TPCG_DESC_BYTES, &c->owned));
-        TPCG_CUDA(cudaMemset(t.desc, 0, TPCG_DESC_BYTES));
+        TPCG_TRY(sync_zero(t.desc, TPCG_DESC_BYTES));
         c->have_tens = i + 1;
     }
     return TPCG_OK;

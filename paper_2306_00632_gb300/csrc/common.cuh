@@ -15,6 +15,12 @@ namespace tpcg {
 
 // ------------------------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
+// Host-to-device copies and zero fills that complete before the call returns, on a private non-blocking stream.
+// cudaMemcpy / cudaMemset use the legacy default stream, which is not ordered with the non-blocking streams the
+// solvers run on, and may return before the device write is done (pageable uploads, device memsets): a solve
+// started right after them on another stream could read stale data or be overwritten by the late write.
+int sync_to_device(void* dst, const void* src, size_t bytes);
+int sync_zero(void* dst, size_t bytes);
 
 // ------------------------------------------------------------------------------------ profiling
 extern std::atomic<long long> g_launches;

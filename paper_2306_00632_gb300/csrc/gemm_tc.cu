@@ -305,12 +305,14 @@ template int launch_gemm_tc<true, false>(const GemmArgs*, const int*, int, int, 
 template int launch_gemm_tc<true, true>(const GemmArgs*, const int*, int, int, int, int, cudaStream_t);
 
 int tc_take_error() {
-    int h = 0, zero = 0;
+    int h = 0;
     if (cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (h) cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int));
+    void* addr = nullptr;
+    if (h && cudaGetSymbolAddress(&addr, g_tc_error) == cudaSuccess && addr) sync_zero(addr, sizeof(int));
+    cudaGetLastError();
     return h;
 }
 

@@ -18,7 +18,8 @@ int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaSt
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
                 double abs_tol, double* info_dev, cudaStream_t st);
 // whether a context of this size, rank cap and dtype reduces its large Grams by Rayleigh-Ritz
-int rr_kind();   // TPCG_OPT_RR
+int rr_kind();      // TPCG_OPT_RR
+int gram_min_k();   // TPCG_OPT_GRAM_MIN_K
 // FP32: every context with n > RR_L (the one-CTA FP32 Jacobi for larger Grams keeps its diagonal by rotation
 // updates, whose drift spoils the trace-minus-kept rule); FP64: n > 256 (beyond the cluster eigensolver) with a
 // rank cap that leaves the basis room

@@ -72,7 +72,7 @@ extern "C" int tpcg_profile_enable(int on) {
             set_error("tpcg_profile_enable: cudaMalloc failed");
             return TPCG_E_NOMEM;
         }
-        cudaMemset(g_dev, 0, PK_COUNT * 2 * sizeof(double));
+        if (sync_zero(g_dev, PK_COUNT * 2 * sizeof(double)) != TPCG_OK) return TPCG_E_CUDA;
     }
     g_on = on != 0;
     return TPCG_OK;
@@ -90,7 +90,7 @@ extern "C" int tpcg_profile_reset(void) {
         g_open[k] = -1;
         g_count[k] = 0;
     }
-    if (g_dev) cudaMemset(g_dev, 0, PK_COUNT * 2 * sizeof(double));
+    if (g_dev && sync_zero(g_dev, PK_COUNT * 2 * sizeof(double)) != TPCG_OK) return TPCG_E_CUDA;
     return TPCG_OK;
 }
 
@@ -126,6 +126,8 @@ static std::atomic<int> g_tc_kind{0};
 int tc_kind() { return g_tc_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_rr_kind{1};
 int rr_kind() { return g_rr_kind.load(std::memory_order_relaxed); }
+static std::atomic<int> g_gram_min_k{0};
+int gram_min_k() { return g_gram_min_k.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
@@ -151,6 +153,10 @@ extern "C" int tpcg_set_option(int key, long long value) {
     }
     if (key == TPCG_OPT_RR && (value == 0 || value == 1)) {
         tpcg::g_rr_kind.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_GRAM_MIN_K && value >= 0 && value <= (1 << 24)) {
+        tpcg::g_gram_min_k.store((int)value);
         return TPCG_OK;
     }
     tpcg::set_error("tpcg_set_option: unknown key or value out of range");

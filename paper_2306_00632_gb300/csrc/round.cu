@@ -31,7 +31,7 @@ template <typename T>
 __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* plan, GemmArgs* ga, int n,
                                   int cap, double eps_host, const double* eps_dev, void* Rq0, void* Rq1,
                                   void* Rq2, const void* U0, const void* U1, const void* U2, T* T1, T* Wm,
-                                  int* counts, long long t1cap, double* prof, int strict_mode) {
+                                  int* counts, long long t1cap, double* prof, int strict_mode, void* Zout) {
     if (threadIdx.x != 0) return;
     RoundPlan p;
     p.n = n;
@@ -89,7 +89,7 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
     z.M = kp1 * kp2; z.N = p.kp[2]; z.K = p.k[2]; z.nbatch = 1; z.acc = 0;
     z.A = Wm; z.lda = (long long)kp1 * kp2; z.sA = 0;
     z.B = p.Rp[2]; z.ldb = p.ldR[2]; z.sB = 0;
-    z.C = nullptr;  // set by the host launcher through counts[] slot (Z buffer is fixed)
+    z.C = Zout;
     z.ldc = (long long)kp1 * kp2; z.sC = 0;
     z.alpha = 1.0; z.beta = 0.0;
     ga[2 * TPCG_MAX_BLOCKS] = z;
@@ -113,10 +113,6 @@ __global__ void plan_round_kernel(const TuckerDesc* __restrict__ d, RoundPlan* p
         for (int t = 0; t < 3; ++t) p.zdim[t] = 0;
     }
     *plan = p;
-}
-
-__global__ void set_c_kernel(GemmArgs* ga, void* C) {
-    if (threadIdx.x == 0) ga->C = C;
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -241,10 +237,8 @@ __global__ void __launch_bounds__(1024) qr_kernel(const RoundPlan* __restrict__ 
 //   m = 2: G = Zmat^T Zmat          (TN, K = d1 d2 split)
 // --------------------------------------------------------------------------------------------------
 template <typename T>
-__global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* Part, int m, int nsplit_max,
-                                 int* counts, double* prof) {
-    if (threadIdx.x != 0) return;
-    RoundPlan& p = *plan;
+__device__ void plan_gram(RoundPlan& p, GemmArgs* ga, const T* Zc, T* Part, int m, int nsplit_max, int min_k,
+                          int* counts, double* prof) {
     const int d1 = p.zdim[0], d2 = p.zdim[1], d3 = p.zdim[2];
     const int M = p.zdim[m];
     int total = (m == 0) ? d2 * d3 : (m == 1 ? d3 : d1 * d2);
@@ -253,6 +247,11 @@ __global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* 
         prof[2 * PK_GRAM + 1] += sizeof(T) * ((double)d1 * d2 * d3 + (double)M * M);
     }
     int ns = total < nsplit_max ? total : nsplit_max;
+    if (min_k > 0) {   // at least min_k of the reduction per group: fewer, longer groups (less partial traffic)
+        const long long ktot = (long long)total * (m == 1 ? d1 : 1);
+        const long long cap_k = ktot / min_k;
+        if (cap_k < ns) ns = (int)cap_k;
+    }
     if (ns < 1) ns = 1;
     if (M == 0 || total == 0) ns = 0;
     const int chunk = ns ? (total + ns - 1) / ns : 0;
@@ -290,6 +289,12 @@ __global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* 
     counts[2] = M;
 }
 
+template <typename T>
+__global__ void plan_gram_kernel(RoundPlan* plan, GemmArgs* ga, const T* Zc, T* Part, int m, int nsplit_max,
+                                 int min_k, int* counts, double* prof) {
+    if (threadIdx.x == 0) plan_gram<T>(*plan, ga, Zc, Part, m, nsplit_max, min_k, counts, prof);
+}
+
 // --------------------------------------------------------------------------------------------------
 // Projection Z x_m S_m^T onto the s_m kept eigenvectors of mode m (the truncation rule itself runs in the
 // eigensolver, eig.cu).
@@ -315,17 +320,17 @@ __device__ void plan_projection(RoundPlan& p, GemmArgs* ga, const void* S, long 
     ga[0] = a;
 }
 
-// plan of the projection onto the kept eigenvectors (after the eigensolver set plan.s[m])
+// plan of the projection onto the kept eigenvectors (after the eigensolver set plan.s[m]) into gp; the working
+// tensor's mode m shrinks to s_m, and for m < 2 the Gram of mode m + 1 of the projected tensor is planned into
+// gg (a separate argument range: the projection's product runs first)
 template <typename T>
-__global__ void plan_proj_kernel(RoundPlan* plan, GemmArgs* ga, const T* S, const T* Zc, T* Znext, int m, int* counts) {
+__global__ void plan_proj_kernel(RoundPlan* plan, GemmArgs* gp, const T* S, const T* Zc, T* Znext, int m,
+                                 GemmArgs* gg, T* Part, int nsplit_max, int min_k, int* counts, double* prof) {
     if (threadIdx.x != 0) return;
     RoundPlan& p = *plan;
-    plan_projection(p, ga, S, p.n, Zc, Znext, m, p.s[m]);
-    counts[0] = 1;
-}
-
-__global__ void set_zdim_kernel(RoundPlan* plan, int m) {
-    if (threadIdx.x == 0) plan->zdim[m] = plan->s[m];
+    plan_projection(p, gp, S, p.n, Zc, Znext, m, p.s[m]);
+    p.zdim[m] = p.s[m];
+    if (m < 2) plan_gram<T>(p, gg, Znext, Part, m + 1, nsplit_max, min_k, counts, prof);
 }
 
 // --------------------------------------------------------------------------------------------------
@@ -579,9 +584,7 @@ int round_stage12(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, in
     plan_round_kernel<T><<<1, 32, 0, st>>>(static_cast<const TuckerDesc*>(y->desc), c->plan, ga, n, rc, eps, eps_dev,
                                            c->Rq[0], c->Rq[1], c->Rq[2], y->U[0], y->U[1], y->U[2],
                                            static_cast<T*>(c->T1), static_cast<T*>(c->Wm), counts,
-                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev(), strict_mode);
-    TPCG_CHECK_LAUNCH();
-    set_c_kernel<<<1, 32, 0, st>>>(ga + 2 * TPCG_MAX_BLOCKS, Z0);
+                                           (long long)c->max_cols * c->n * c->rank_cap, prof_dev(), strict_mode, Z0);
     TPCG_CHECK_LAUNCH();
     // step 1: QR where k_t < n
     prof_begin(PK_QR, st);
@@ -620,11 +623,13 @@ int round_stage34(tpcg_ctx c, tucker_t* y, double* info_dev, cudaStream_t st) {
     // step 3: ST-HOSVD
     T* Zc = Z0;
     T* Zn = Z1;
+    const int min_k = gram_min_k();
+    GemmArgs* gproj = ga + MAX_SPLIT;   // projection arguments, apart from the next Gram's
+    plan_gram_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Zc, static_cast<T*>(c->Part), 0, MAX_SPLIT, min_k, counts,
+                                          prof_dev());
+    TPCG_CHECK_LAUNCH();
     for (int m = 0; m < 3; ++m) {
         prof_begin(PK_GRAM, st);
-        plan_gram_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, Zc, static_cast<T*>(c->Part), m, MAX_SPLIT, counts,
-                                              prof_dev());
-        TPCG_CHECK_LAUNCH();
         if (m == 0)
             TPCG_TRY((launch_gemm<T, false, true>(ga, counts, MAX_SPLIT, 1, n, n, st)));
         else
@@ -663,16 +668,15 @@ int round_stage34(tpcg_ctx c, tucker_t* y, double* info_dev, cudaStream_t st) {
         }
         prof_end(PK_EIG, st);
         prof_begin(PK_PROJ, st);
-        plan_proj_kernel<T><<<1, 32, 0, st>>>(c->plan, ga, static_cast<const T*>(c->S[m]), Zc, Zn, m, counts);
+        plan_proj_kernel<T><<<1, 32, 0, st>>>(c->plan, gproj, static_cast<const T*>(c->S[m]), Zc, Zn, m, ga,
+                                              static_cast<T*>(c->Part), MAX_SPLIT, min_k, counts, prof_dev());
         TPCG_CHECK_LAUNCH();
         if (m == 0)
-            TPCG_TRY((launch_gemm<T, true, false>(ga, nullptr, 1, 1, n, n * n, st)));
+            TPCG_TRY((launch_gemm<T, true, false>(gproj, nullptr, 1, 1, n, n * n, st)));
         else if (m == 1)
-            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, n, n, n, st)));
+            TPCG_TRY((launch_gemm<T, false, false>(gproj, nullptr, 1, n, n, n, st)));
         else
-            TPCG_TRY((launch_gemm<T, false, false>(ga, nullptr, 1, 1, n * n, n, st)));
-        set_zdim_kernel<<<1, 32, 0, st>>>(c->plan, m);
-        TPCG_CHECK_LAUNCH();
+            TPCG_TRY((launch_gemm<T, false, false>(gproj, nullptr, 1, 1, n * n, n, st)));
         prof_end(PK_PROJ, st);
         T* tmp = Zc; Zc = Zn; Zn = tmp;
     }
