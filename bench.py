@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--large-cap", type=int, default=80, help="large configuration: rank cap")
     ap.add_argument("--large-concurrent", type=int, default=2, help="large configuration: solves at once")
     ap.add_argument("--large-fp64", action="store_true", help="large configuration: also the FP64 form")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="per-class CUDA-event times of one extra, untimed step of concurrent solves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form measurement beside the mixed one")
@@ -486,6 +488,8 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = L.tpcg_launch_count()
+    import resource
+    ru0 = resource.getrusage(resource.RUSAGE_SELF)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     results = []
     torch.cuda.synchronize()
@@ -500,11 +504,23 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.barrier()
     launches = L.tpcg_launch_count() - launches0
+    ru1 = resource.getrusage(resource.RUSAGE_SELF)
+    host_cpu_s = (ru1.ru_utime - ru0.ru_utime) + (ru1.ru_stime - ru0.ru_stime)
     clk = clocks.stop()
     total_ms = g0.elapsed_time(g1)
     if ws > 1:
         total_ms = max_over_ranks(total_ms, "cuda")
 
+    prof_batch = None
+    if args.profile_batch:   # one more (untimed) step with per-class CUDA events on every solve's stream
+        L.tpcg_profile_reset()
+        L.tpcg_profile_enable(1)
+        batch()
+        torch.cuda.synchronize()
+        L.tpcg_profile_enable(0)
+        pb_ = _profile(L, lib)
+        prof_batch = {k: {"ms_per_solve": round(v["ms"] / B, 3), "launches_per_solve": round(v["launches"] / B, 1)}
+                      for k, v in pb_.items() if k != "sweeps"}
     roof = _roofline(prof, args.dtype, lib, sum(lat_ms))
     value = job_throughput(ws, B, args.steps, total_ms)
     last = results[-1][1]
@@ -527,10 +543,12 @@ def run_gpu(args):
                      "rank": [list(s.rank) for s in last]},
            "single": {"iters": [int(s.iters) for s in single], "true_rel_res": [float(s.true_rel_res) for s in single]},
            "gpu_launches": int(launches), "roofline": roof,
+           "host_cpu_s_per_step": host_cpu_s / args.steps, "host_cores": os.cpu_count(),
            "kernel_ms_single": {k: round(v["ms"], 3) for k, v in prof.items() if k != "sweeps"},
            "kernel_tflops_single": {k: round(v["flops"] / (v["ms"] * 1e9), 3) for k, v in prof.items()
                                     if k in ("zgemm", "zblk", "gram", "proj", "eig", "apply", "fd") and v["ms"] > 0},
            "eig_sweeps_per_gram": prof["sweeps"]["flops"] / max(prof["sweeps"]["bytes"], 1.0),
+           **({"kernel_classes_in_batch": prof_batch} if prof_batch else {}),
            "clocks": clk}
 
     # the solution of seed SEED (problem 0) from the last timed step, against the oracle's stored solution

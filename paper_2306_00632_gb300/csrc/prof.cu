@@ -21,7 +21,16 @@ bool g_on = false;
 double* g_dev = nullptr;                // PK_COUNT * 2 doubles: flops, bytes
 std::vector<EvPair> g_pairs;            // recorded (start, stop) pairs
 std::vector<cudaEvent_t> g_free;        // recycled events
-std::vector<int> g_open(PK_COUNT, -1);  // index of the open pair per kind
+// index of the open pair per kind, per host thread (concurrent solves open and close pairs independently)
+thread_local std::vector<int> g_open(PK_COUNT, -1);
+long long g_gen = 0;                    // bumped by every reset: a thread's open pairs of an older generation are void
+thread_local long long t_gen = 0;
+void sync_gen() {
+    if (t_gen != g_gen) {
+        for (int k = 0; k < PK_COUNT; ++k) g_open[k] = -1;
+        t_gen = g_gen;
+    }
+}
 long long g_count[PK_COUNT] = {0};
 
 cudaEvent_t get_event() {
@@ -42,6 +51,7 @@ double* prof_dev() { return g_on ? g_dev : nullptr; }
 void prof_begin(int kind, cudaStream_t st) {
     if (!g_on) return;
     std::lock_guard<std::mutex> lk(g_mu);
+    sync_gen();
     EvPair p{get_event(), get_event(), kind};
     cudaEventRecord(p.a, st);
     g_open[kind] = (int)g_pairs.size();
@@ -51,8 +61,9 @@ void prof_begin(int kind, cudaStream_t st) {
 void prof_end(int kind, cudaStream_t st) {
     if (!g_on) return;
     std::lock_guard<std::mutex> lk(g_mu);
+    sync_gen();
     int i = g_open[kind];
-    if (i < 0) return;
+    if (i < 0 || i >= (int)g_pairs.size()) return;
     cudaEventRecord(g_pairs[i].b, st);
     g_open[kind] = -1;
     g_count[kind]++;
@@ -86,6 +97,7 @@ extern "C" int tpcg_profile_reset(void) {
         g_free.push_back(p.b);
     }
     g_pairs.clear();
+    ++g_gen;
     for (int k = 0; k < PK_COUNT; ++k) {
         g_open[k] = -1;
         g_count[k] = 0;
