@@ -64,6 +64,7 @@ def parse():
                     help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
     ap.add_argument("--dst", type=int, default=1, choices=[0, 1], help="FD sine transforms: 1 FFT, 0 dense")
     ap.add_argument("--gram-min-k", type=int, default=0, help="least reduction length per partial Gram (0: most partials)")
+    ap.add_argument("--gemm-kind", type=int, default=1, choices=[0, 1], help="FP32 SIMT GEMM: 1 8x4 per thread, 0 4x4")
     ap.add_argument("--tc", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP32 contractions: 1 tensor cores (tcgen05), 0 SIMT, -1 the library default")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")
@@ -448,6 +449,7 @@ def run_gpu(args):
     lib.check(L.tpcg_set_option(lib.OPT_EIG, args.eig), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_DST, args.dst), "tpcg_set_option")
     lib.check(L.tpcg_set_option(lib.OPT_GRAM_MIN_K, args.gram_min_k), "tpcg_set_option")
+    lib.check(L.tpcg_set_option(lib.OPT_GEMM_KIND, args.gemm_kind), "tpcg_set_option")
     if args.tc >= 0:
         lib.check(L.tpcg_set_option(lib.OPT_TC, args.tc), "tpcg_set_option")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -529,7 +531,7 @@ def run_gpu(args):
            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
            "config": {"workload": WORKLOAD, "solves_per_step": B, "inner_tol": args.inner_tol,
                       "gemm_ctas_per_sm": args.gemm_ctas_per_sm, "eig": args.eig, "dst": args.dst, "tc": args.tc,
-                      "gram_min_k": args.gram_min_k,
+                      "gram_min_k": args.gram_min_k, "gemm_kind": args.gemm_kind,
                       "refine_keep": args.refine_keep,
                       "seeds": f"{seeds[0]}..{seeds[-1]} on rank 0, disjoint ranges per rank (amp from seed)",
                       "tol": TOL, "rank_cap": rc,

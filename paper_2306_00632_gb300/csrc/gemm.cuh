@@ -151,6 +151,145 @@ __global__ void __launch_bounds__(GTHREADS) gemm_grouped_kernel(const GemmArgs* 
     }
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// FP32 variant with an 8 x 4 output block per thread: 128 threads per 64 x 64 tile, K-step 16.  Per K-step a thread
+// reads its 8 rows of A and 4 columns of B as three 16-byte shared loads and issues 32 FMAs (the 4 x 4 kernel
+// issues 8 scalar shared loads per 16 FMAs).  The tiles are staged through registers and two shared stages as in
+// gemm_grouped_kernel; row stride 68 floats keeps the 16-byte reads aligned and spreads the strided stores.
+// Same arguments, grid and results contract as gemm_grouped_kernel.
+// ------------------------------------------------------------------------------------------------------------
+constexpr int G8_THREADS = 128, G8_LD = GBM + 4, G8_LOAD = (GBM * GBK) / G8_THREADS;   // 8 elements per operand
+
+template <bool TA>
+__device__ __forceinline__ void g8_fetch_a(float (&r)[G8_LOAD], const float* A, long long lda, int M, int K, int m0,
+                                           int k0, int tid) {
+#pragma unroll
+    for (int q = 0; q < G8_LOAD; ++q) {
+        const int e = tid + q * G8_THREADS;
+        int mm, kk;
+        if (!TA) { mm = e % GBM; kk = e / GBM; }
+        else     { kk = e % GBK; mm = e / GBK; }
+        const int m = m0 + mm, k = k0 + kk;
+        r[q] = (m < M && k < K) ? (TA ? A[k + (long long)m * lda] : A[m + (long long)k * lda]) : 0.f;
+    }
+}
+
+template <bool TA>
+__device__ __forceinline__ void g8_store_a(float* As, const float (&r)[G8_LOAD], int tid) {
+#pragma unroll
+    for (int q = 0; q < G8_LOAD; ++q) {
+        const int e = tid + q * G8_THREADS;
+        if (!TA) As[(e / GBM) * G8_LD + e % GBM] = r[q];
+        else     As[(e % GBK) * G8_LD + e / GBK] = r[q];
+    }
+}
+
+template <bool TB>
+__device__ __forceinline__ void g8_fetch_b(float (&r)[G8_LOAD], const float* B, long long ldb, int N, int K, int n0,
+                                           int k0, int tid) {
+#pragma unroll
+    for (int q = 0; q < G8_LOAD; ++q) {
+        const int e = tid + q * G8_THREADS;
+        int nn, kk;
+        if (!TB) { kk = e % GBK; nn = e / GBK; }
+        else     { nn = e % GBN; kk = e / GBN; }
+        const int nI = n0 + nn, k = k0 + kk;
+        r[q] = (nI < N && k < K) ? (TB ? B[nI + (long long)k * ldb] : B[k + (long long)nI * ldb]) : 0.f;
+    }
+}
+
+template <bool TB>
+__device__ __forceinline__ void g8_store_b(float* Bs, const float (&r)[G8_LOAD], int tid) {
+#pragma unroll
+    for (int q = 0; q < G8_LOAD; ++q) {
+        const int e = tid + q * G8_THREADS;
+        if (!TB) Bs[(e % GBK) * G8_LD + e / GBK] = r[q];
+        else     Bs[(e / GBN) * G8_LD + e % GBN] = r[q];
+    }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(G8_THREADS) gemm88_kernel(const GemmArgs* __restrict__ args,
+                                                            const int* __restrict__ count_dev, int bmax, int zmax) {
+    __shared__ __align__(16) float As[2][GBK * G8_LD];
+    __shared__ __align__(16) float Bs[2][GBK * G8_LD];
+    const int gcount = count_dev != nullptr ? *count_dev : (zmax / bmax);
+    const int tid = threadIdx.x;
+    const int tx = tid % 8, ty = tid / 8;   // rows 8 tx .. 8 tx + 7, columns 4 ty .. 4 ty + 3 of the tile
+    for (int z = blockIdx.z; z < zmax; z += gridDim.z) {
+        const int g = z / bmax;
+        const int ib = z % bmax;
+        if (g >= gcount) break;
+        const GemmArgs a = args[g];
+        if (a.acc ? (ib != 0) : (ib >= a.nbatch)) continue;
+        const int M = a.M, N = a.N, K = a.K;
+        const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+        if (m0 >= M || n0 >= N) continue;
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        const int nb = a.acc ? a.nbatch : 1;
+        for (int b = 0; b < nb; ++b) {
+            const int bi = a.acc ? b : ib;
+            const float* A = static_cast<const float*>(a.A) + (long long)bi * a.sA;
+            const float* B = static_cast<const float*>(a.B) + (long long)bi * a.sB;
+            float ra[G8_LOAD], rb[G8_LOAD];
+            g8_fetch_a<TA>(ra, A, a.lda, M, K, m0, 0, tid);
+            g8_fetch_b<TB>(rb, B, a.ldb, N, K, n0, 0, tid);
+            g8_store_a<TA>(As[0], ra, tid);
+            g8_store_b<TB>(Bs[0], rb, tid);
+            __syncthreads();
+            int cur = 0;
+            for (int k0 = 0; k0 < K; k0 += GBK) {
+                const bool more = k0 + GBK < K;
+                if (more) {
+                    g8_fetch_a<TA>(ra, A, a.lda, M, K, m0, k0 + GBK, tid);
+                    g8_fetch_b<TB>(rb, B, a.ldb, N, K, n0, k0 + GBK, tid);
+                }
+                const float* Ac = As[cur];
+                const float* Bc = Bs[cur];
+#pragma unroll
+                for (int kk = 0; kk < GBK; ++kk) {
+                    const float4 a0 = *reinterpret_cast<const float4*>(Ac + kk * G8_LD + 8 * tx);
+                    const float4 a1 = *reinterpret_cast<const float4*>(Ac + kk * G8_LD + 8 * tx + 4);
+                    const float4 b0 = *reinterpret_cast<const float4*>(Bc + kk * G8_LD + 4 * ty);
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float bv[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                }
+                if (more) {
+                    g8_store_a<TA>(As[cur ^ 1], ra, tid);
+                    g8_store_b<TB>(Bs[cur ^ 1], rb, tid);
+                }
+                __syncthreads();
+                cur ^= 1;
+            }
+        }
+        float* C = static_cast<float*>(a.C) + (a.acc ? 0LL : (long long)ib * a.sC);
+        const float alpha = (float)a.alpha, beta = (float)a.beta;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nI = n0 + 4 * ty + j;
+            if (nI >= N) continue;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int m = m0 + 8 * tx + i;
+                if (m >= M) continue;
+                float* c = C + m + (long long)nI * a.ldc;
+                float v = alpha * acc[i][j];
+                if (a.beta != 0.0) v += beta * (*c);
+                *c = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // C = alpha * sum_{g < count} P_g + beta * C over an M x N column-major block (partials contiguous,
 // stride M*N); M, N, count read from device.
 template <typename T>
@@ -193,6 +332,7 @@ template <bool TA, bool TB>
 int launch_gemm_tc(const GemmArgs* args, const int* count_dev, int ngroups_max, int bmax, int Mmax, int Nmax,
                    cudaStream_t st);
 int tc_kind();        // TPCG_OPT_TC: 1 FP32 contractions on the tensor cores, 0 on the FP32 SIMT units
+int gemm_kind();      // TPCG_OPT_GEMM_KIND: 1 the 8 x 4-per-thread FP32 kernel, 0 the 4 x 4 one
 int tc_prepare();     // shared-memory opt-in of the tensor-core kernels on the current device
 int tc_take_error();  // nonzero once a tensor-core kernel abandoned a wait (the flag is cleared)
 
@@ -215,6 +355,17 @@ inline int launch_gemm(const GemmArgs* args, const int* count_dev, int ngroups_m
     if (grid.y > 65535u || zmax > (1LL << 30)) {
         set_error("gemm grid too large");
         return TPCG_E_INVALID;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (gemm_kind() == 1) {   // 8 x 4 outputs per thread: half the threads per tile, same thread budget
+            const long long zcap8 = per_sm > 0 ? std::max(1LL, ((long long)2 * per_sm * sm_count()) /
+                                                                   std::max(1LL, gx * gy))
+                                               : zmax;
+            dim3 grid8((unsigned)gx, (unsigned)gy, (unsigned)std::min(std::min(zmax, zcap8), 65535LL));
+            gemm88_kernel<TA, TB><<<grid8, G8_THREADS, 0, st>>>(args, count_dev, bmax, (int)zmax);
+            TPCG_CHECK_LAUNCH();
+            return TPCG_OK;
+        }
     }
     gemm_grouped_kernel<T, TA, TB><<<grid, GTHREADS, 0, st>>>(args, count_dev, bmax, (int)zmax);
     TPCG_CHECK_LAUNCH();
