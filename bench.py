@@ -64,7 +64,8 @@ def parse():
                     help="FP32 Gram eigensolver: 1 pivoted Cholesky + one-sided Jacobi, 0 two-sided Jacobi")
     ap.add_argument("--dst", type=int, default=1, choices=[0, 1], help="FD sine transforms: 1 FFT, 0 dense")
     ap.add_argument("--gram-min-k", type=int, default=0, help="least reduction length per partial Gram (0: most partials)")
-    ap.add_argument("--gemm-kind", type=int, default=1, choices=[0, 1], help="FP32 SIMT GEMM: 1 8x4 per thread, 0 4x4")
+    ap.add_argument("--gemm-kind", type=int, default=2, choices=[0, 1, 2],
+                    help="FP32 SIMT GEMM: 1 8x4 per thread, 2 the same with cp.async stages, 0 4x4")
     ap.add_argument("--tc", type=int, default=-1, choices=[-1, 0, 1],
                     help="FP32 contractions: 1 tensor cores (tcgen05), 0 SIMT, -1 the library default")
     ap.add_argument("--torch-streams", action="store_true", help="give each solve a torch stream (<= 32)")

@@ -325,8 +325,9 @@ void tpcg_elast_destroy(tpcg_elast e);
  *   partials: less partial traffic and block start-up, which pays when many solves share the device), 0 (default)
  *   always uses the most partials.  Read when a truncation is launched or captured. */
 #define TPCG_OPT_GRAM_MIN_K 7
-/*   TPCG_OPT_GEMM_KIND: the FP32 SIMT contractions: 1 (default) 128 threads per 64 x 64 output tile, 8 x 4 outputs
- *   per thread (16-byte shared loads, 32 FMAs per 3 loads); 0 256 threads, 4 x 4 outputs per thread. */
+/*   TPCG_OPT_GEMM_KIND: the FP32 SIMT contractions: 2 (default) 128 threads per 64 x 64 output tile, 8 x 4 outputs
+ *   per thread (16-byte shared loads, 32 FMAs per 3 loads), operands copied by cp.async through three shared
+ *   stages; 1 the same tile staged through registers and two stages; 0 256 threads, 4 x 4 outputs per thread. */
 #define TPCG_OPT_GEMM_KIND 8
 int tpcg_set_option(int key, long long value);
 

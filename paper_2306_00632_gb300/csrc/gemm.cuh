@@ -290,6 +290,128 @@ __global__ void __launch_bounds__(G8_THREADS) gemm88_kernel(const GemmArgs* __re
     }
 }
 
+// ------------------------------------------------------------------------------------------------------------
+// The same 8 x 4-per-thread FP32 tile with the operands copied global -> shared by cp.async (no staging
+// registers) through GCP_STAGES shared stages: while a K-step is multiplied, the copies of the next
+// GCP_STAGES - 1 are in flight.  Out-of-range elements are zero-filled by the copy itself (source size 0).
+// ------------------------------------------------------------------------------------------------------------
+constexpr int GCP_STAGES = 3;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool pred) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    const int n = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void gcp_issue(float* As, float* Bs, const float* A, const float* B, long long lda,
+                                          long long ldb, int M, int N, int K, int m0, int n0, int k0, int tid) {
+#pragma unroll 2
+    for (int q = 0; q < G8_LOAD; ++q) {
+        const int e = tid + q * G8_THREADS;
+        int mm, kk;
+        if (!TA) { mm = e % GBM; kk = e / GBM; }
+        else     { kk = e % GBK; mm = e / GBK; }
+        const int m = m0 + mm, k = k0 + kk;
+        const bool ok = m < M && k < K;
+        const float* src = ok ? (TA ? A + k + (long long)m * lda : A + m + (long long)k * lda) : A;
+        cp_async4(As + kk * G8_LD + mm, src, ok);
+    }
+#pragma unroll 2
+    for (int q = 0; q < G8_LOAD; ++q) {
+        const int e = tid + q * G8_THREADS;
+        int nn, kk;
+        if (!TB) { kk = e % GBK; nn = e / GBK; }
+        else     { nn = e % GBN; kk = e / GBN; }
+        const int nI = n0 + nn, k = k0 + kk;
+        const bool ok = nI < N && k < K;
+        const float* src = ok ? (TB ? B + nI + (long long)k * ldb : B + k + (long long)nI * ldb) : B;
+        cp_async4(Bs + kk * G8_LD + nn, src, ok);
+    }
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(G8_THREADS) gemm_cpa_kernel(const GemmArgs* __restrict__ args,
+                                                              const int* __restrict__ count_dev, int bmax, int zmax) {
+    __shared__ __align__(16) float As[GCP_STAGES][GBK * G8_LD];
+    __shared__ __align__(16) float Bs[GCP_STAGES][GBK * G8_LD];
+    const int gcount = count_dev != nullptr ? *count_dev : (zmax / bmax);
+    const int tid = threadIdx.x;
+    const int tx = tid % 8, ty = tid / 8;   // rows 8 tx .. 8 tx + 7, columns 4 ty .. 4 ty + 3 of the tile
+    for (int z = blockIdx.z; z < zmax; z += gridDim.z) {
+        const int g = z / bmax;
+        const int ib = z % bmax;
+        if (g >= gcount) break;
+        const GemmArgs a = args[g];
+        if (a.acc ? (ib != 0) : (ib >= a.nbatch)) continue;
+        const int M = a.M, N = a.N, K = a.K;
+        const int m0 = blockIdx.x * GBM, n0 = blockIdx.y * GBN;
+        if (m0 >= M || n0 >= N) continue;
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        const int nb = a.acc ? a.nbatch : 1;
+        const int nk = (K + GBK - 1) / GBK;
+        for (int b = 0; b < nb; ++b) {
+            const int bi = a.acc ? b : ib;
+            const float* A = static_cast<const float*>(a.A) + (long long)bi * a.sA;
+            const float* B = static_cast<const float*>(a.B) + (long long)bi * a.sB;
+#pragma unroll
+            for (int st = 0; st < GCP_STAGES - 1; ++st) {   // prologue: the first stages (empty groups past K)
+                if (st < nk) gcp_issue<TA, TB>(As[st], Bs[st], A, B, a.lda, a.ldb, M, N, K, m0, n0, st * GBK, tid);
+                cp_async_commit();
+            }
+            for (int kt = 0; kt < nk; ++kt) {
+                cp_async_wait<GCP_STAGES - 2>();   // this thread's copies of K-step kt have landed
+                __syncthreads();                   // everyone's have, and everyone is done with K-step kt - 1
+                const int nx = kt + GCP_STAGES - 1;
+                if (nx < nk) {
+                    const int sn = nx % GCP_STAGES;
+                    gcp_issue<TA, TB>(As[sn], Bs[sn], A, B, a.lda, a.ldb, M, N, K, m0, n0, nx * GBK, tid);
+                }
+                cp_async_commit();
+                const float* Ac = As[kt % GCP_STAGES];
+                const float* Bc = Bs[kt % GCP_STAGES];
+#pragma unroll
+                for (int kk = 0; kk < GBK; ++kk) {
+                    const float4 a0 = *reinterpret_cast<const float4*>(Ac + kk * G8_LD + 8 * tx);
+                    const float4 a1 = *reinterpret_cast<const float4*>(Ac + kk * G8_LD + 8 * tx + 4);
+                    const float4 b0 = *reinterpret_cast<const float4*>(Bc + kk * G8_LD + 4 * ty);
+                    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float bv[4] = {b0.x, b0.y, b0.z, b0.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                }
+            }
+            cp_async_wait<0>();
+            __syncthreads();   // the stages are refilled by the next batch or tile
+        }
+        float* C = static_cast<float*>(a.C) + (a.acc ? 0LL : (long long)ib * a.sC);
+        const float alpha = (float)a.alpha, beta = (float)a.beta;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nI = n0 + 4 * ty + j;
+            if (nI >= N) continue;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int m = m0 + 8 * tx + i;
+                if (m >= M) continue;
+                float* c = C + m + (long long)nI * a.ldc;
+                float v = alpha * acc[i][j];
+                if (a.beta != 0.0) v += beta * (*c);
+                *c = v;
+            }
+        }
+    }
+}
+
 // C = alpha * sum_{g < count} P_g + beta * C over an M x N column-major block (partials contiguous,
 // stride M*N); M, N, count read from device.
 template <typename T>
@@ -332,7 +454,7 @@ template <bool TA, bool TB>
 int launch_gemm_tc(const GemmArgs* args, const int* count_dev, int ngroups_max, int bmax, int Mmax, int Nmax,
                    cudaStream_t st);
 int tc_kind();        // TPCG_OPT_TC: 1 FP32 contractions on the tensor cores, 0 on the FP32 SIMT units
-int gemm_kind();      // TPCG_OPT_GEMM_KIND: 1 the 8 x 4-per-thread FP32 kernel, 0 the 4 x 4 one
+int gemm_kind();      // TPCG_OPT_GEMM_KIND: 1 the 8 x 4-per-thread FP32 kernel, 2 the same with cp.async stages, 0 the 4 x 4 one
 int tc_prepare();     // shared-memory opt-in of the tensor-core kernels on the current device
 int tc_take_error();  // nonzero once a tensor-core kernel abandoned a wait (the flag is cleared)
 
@@ -357,12 +479,15 @@ inline int launch_gemm(const GemmArgs* args, const int* count_dev, int ngroups_m
         return TPCG_E_INVALID;
     }
     if constexpr (sizeof(T) == 4) {
-        if (gemm_kind() == 1) {   // 8 x 4 outputs per thread: half the threads per tile, same thread budget
+        if (gemm_kind() >= 1) {   // 8 x 4 outputs per thread: half the threads per tile, same thread budget
             const long long zcap8 = per_sm > 0 ? std::max(1LL, ((long long)2 * per_sm * sm_count()) /
                                                                    std::max(1LL, gx * gy))
                                                : zmax;
             dim3 grid8((unsigned)gx, (unsigned)gy, (unsigned)std::min(std::min(zmax, zcap8), 65535LL));
-            gemm88_kernel<TA, TB><<<grid8, G8_THREADS, 0, st>>>(args, count_dev, bmax, (int)zmax);
+            if (gemm_kind() == 2)
+                gemm_cpa_kernel<TA, TB><<<grid8, G8_THREADS, 0, st>>>(args, count_dev, bmax, (int)zmax);
+            else
+                gemm88_kernel<TA, TB><<<grid8, G8_THREADS, 0, st>>>(args, count_dev, bmax, (int)zmax);
             TPCG_CHECK_LAUNCH();
             return TPCG_OK;
         }

@@ -138,7 +138,7 @@ static std::atomic<int> g_tc_kind{0};
 int tc_kind() { return g_tc_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_rr_kind{1};
 int rr_kind() { return g_rr_kind.load(std::memory_order_relaxed); }
-static std::atomic<int> g_gemm_kind{1};
+static std::atomic<int> g_gemm_kind{2};
 int gemm_kind() { return g_gemm_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_gram_min_k{0};
 int gram_min_k() { return g_gram_min_k.load(std::memory_order_relaxed); }
@@ -169,7 +169,7 @@ extern "C" int tpcg_set_option(int key, long long value) {
         tpcg::g_rr_kind.store((int)value);
         return TPCG_OK;
     }
-    if (key == TPCG_OPT_GEMM_KIND && (value == 0 || value == 1)) {
+    if (key == TPCG_OPT_GEMM_KIND && value >= 0 && value <= 2) {
         tpcg::g_gemm_kind.store((int)value);
         return TPCG_OK;
     }
