@@ -72,18 +72,32 @@ def dirichlet_basis(n_el: int, p: int, x: np.ndarray, der: int = 0) -> np.ndarra
     return B[1:-1]
 
 
-def weighted_matrix(n_el: int, p: int, di: int, dj: int, g=None) -> np.ndarray:
-    """C[i,j] = int_0^1 b_i^(di) b_j^(dj) g dx over the Dirichlet basis (App. A, matrices C)."""
+def bc_basis(n_el: int, p: int, x: np.ndarray, der: int = 0, bc=(0, 0)) -> np.ndarray:
+    """The B-splines of the space with the boundary conditions bc = (k0, k1) at 0 and 1 (App. B's flags:
+    1 = Neumann, 0 = Dirichlet).  A Dirichlet end drops the one function that does not vanish there (Sec.
+    2.2); a Neumann end keeps it (natural condition).  n = n_el + p - 2 + k0 + k1 functions."""
+    k0, k1 = bc
+    B = basis(open_uniform_knots(n_el, p), p, x, der)
+    return B[(0 if k0 else 1):(B.shape[0] if k1 else B.shape[0] - 1)]
+
+
+def n_el_of(n: int, p: int, bc=(0, 0)) -> int:
+    """Knot spans of the space with n functions, degree p and boundary conditions bc."""
+    return n - p + 2 - bc[0] - bc[1]
+
+
+def weighted_matrix(n_el: int, p: int, di: int, dj: int, g=None, bc=(0, 0)) -> np.ndarray:
+    """C[i,j] = int_0^1 b_i^(di) b_j^(dj) g dx over the basis of bc (App. A, matrices C)."""
     xs, ws = quadrature(n_el, p)
-    Bi = dirichlet_basis(n_el, p, xs, di)
-    Bj = dirichlet_basis(n_el, p, xs, dj)
+    Bi = bc_basis(n_el, p, xs, di, bc)
+    Bj = bc_basis(n_el, p, xs, dj, bc)
     gw = ws if g is None else ws * g(xs)
     return (Bi * gw) @ Bj.T
 
 
-def mass(n_el: int, p: int) -> np.ndarray:
-    return weighted_matrix(n_el, p, 0, 0)
+def mass(n_el: int, p: int, bc=(0, 0)) -> np.ndarray:
+    return weighted_matrix(n_el, p, 0, 0, bc=bc)
 
 
-def stiffness(n_el: int, p: int) -> np.ndarray:
-    return weighted_matrix(n_el, p, 1, 1)
+def stiffness(n_el: int, p: int, bc=(0, 0)) -> np.ndarray:
+    return weighted_matrix(n_el, p, 1, 1, bc=bc)

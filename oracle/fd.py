@@ -8,6 +8,11 @@ Readings:
     the L2-normalised sines sqrt(2) sin(j pi x) at the points x_i (one factor sqrt(2)).
   * App. B, V2: V2 = M^{-1} N with N a basis of null(V1^T), which makes span(V2) the
     M-orthogonal complement of V_h,1; U2, Lambda2 solve the projected pencil with U2^T (V2^T M V2) U2 = I.
+  * App. B, Neumann ends (flags bc = (k0, k1), 1 = Neumann): V_h keeps the end function; V_h,1 asks the odd
+    derivatives <= p - 1 to vanish there (even ones, from order 2, at a Dirichlet end); the end blocks of
+    Phi0 / Phi1 hold twice as many functions as their end has conditions (the paper's n2 when both ends
+    agree); the sinusoids sin(omega_j x + k0 pi/2), omega_j = (j - k0/2 - k1/2) pi, carry the same single
+    L2-normalising factor as the Dirichlet sines.
   * lambda_min / lambda_max (eq. estimate_prec_rel) are sums over the three directions of the
     extreme entries of Lambda~_i, outliers of Lambda2 included.
   * Exponential sums: the paper takes (omega_j, alpha_j) from Hackbusch's tables, which are not
@@ -30,18 +35,18 @@ from . import bspline, tucker
 # ---------------------------------------------------------------------------------------------
 # Exact FD (Alg. 3)
 # ---------------------------------------------------------------------------------------------
-def exact_eig(n: int, p: int):
+def exact_eig(n: int, p: int, bc=(0, 0)):
     """Generalized eigendecomposition K U = M U Lambda, U^T M U = I (eq. factorizations)."""
-    n_el = n - p + 2
-    K = bspline.stiffness(n_el, p)
-    M = bspline.mass(n_el, p)
+    n_el = bspline.n_el_of(n, p, bc)
+    K = bspline.stiffness(n_el, p, bc)
+    M = bspline.mass(n_el, p, bc)
     lam, U = scipy.linalg.eigh(K, M)
     return lam, U
 
 
-def exact_fd_apply_full(n: int, p: int, s: np.ndarray) -> np.ndarray:
+def exact_fd_apply_full(n: int, p: int, s: np.ndarray, bc=(0, 0)) -> np.ndarray:
     """v = P^{-1} s for the exact FD preconditioner (eq. factorized_FD), full vectors, tiny n."""
-    lam, U = exact_eig(n, p)
+    lam, U = exact_eig(n, p, bc)
     S = tucker.unvec(s, (n, n, n))
     T = S
     for m in range(3):
@@ -56,18 +61,41 @@ def exact_fd_apply_full(n: int, p: int, s: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------------------------
 # Approximate eigenpairs (App. B)
 # ---------------------------------------------------------------------------------------------
-def split_dims(n_el: int, p: int):
-    """(n1, n2) of the splitting V_h = V_h,1 (+) V_h,2 (App. B)."""
-    if p % 2 == 1:
-        return n_el - 1, p - 1
-    return n_el, p - 2
+def end_orders(p: int, k: int):
+    """Derivative orders that vanish at one end for functions of V_h,1 (App. B): the even orders 2, 4, ..
+    <= p - 1 at a Dirichlet end (k = 0; order 0 is the space's own condition), the odd orders 1, 3, ..
+    <= p - 1 at a Neumann end (k = 1)."""
+    first = 2 if k == 0 else 1
+    return list(range(first, p, 2))
 
 
-def interpolation_points(n_el: int, p: int) -> np.ndarray:
-    """Breakpoints except 0 and 1 (odd p) or span midpoints (even p) (App. B)."""
+def split_dims(n_el: int, p: int, bc=(0, 0)):
+    """(n1, n2) of the splitting V_h = V_h,1 (+) V_h,2 (App. B): every vanishing derivative at an end removes
+    one dimension from V_h (n = n_el + p - 2 + k0 + k1)."""
+    n = n_el + p - 2 + bc[0] + bc[1]
+    c = len(end_orders(p, bc[0])) + len(end_orders(p, bc[1]))
+    return n - c, c
+
+
+def interpolation_points(n_el: int, p: int, bc=(0, 0)) -> np.ndarray:
+    """Breakpoints, without the ends that carry a Dirichlet condition (odd p), or span midpoints (even p)."""
     if p % 2 == 1:
-        return np.arange(1, n_el) / n_el
+        return np.arange(1 - bc[0], n_el + bc[1]) / n_el
     return (np.arange(1, n_el + 1) - 0.5) / n_el
+
+
+def sine_frequencies(n1: int, bc=(0, 0)) -> np.ndarray:
+    """omega_j = (j - k0/2 - k1/2) pi, j = 1..n1: the sinusoids of App. B (the plain sines j pi when no end
+    carries a Neumann condition)."""
+    return (np.arange(1, n1 + 1) - 0.5 * (bc[0] + bc[1])) * np.pi
+
+
+def sine_matrix(x: np.ndarray, n1: int, bc=(0, 0)) -> np.ndarray:
+    """U_dft[l, j] = c_j sin(omega_j x_l + k0 pi/2) with c_j the L2 normalisation on [0, 1] (sqrt2, or 1 for
+    the constant of two Neumann ends)."""
+    w = sine_frequencies(n1, bc)
+    c = np.where(w == 0.0, 1.0, np.sqrt(2.0))
+    return c * np.sin(np.outer(x, w) + 0.5 * np.pi * bc[0])
 
 
 def _nullspace(A: np.ndarray) -> np.ndarray:
@@ -76,45 +104,46 @@ def _nullspace(A: np.ndarray) -> np.ndarray:
     return scipy.linalg.null_space(A)
 
 
-def v1_basis(n_el: int, p: int) -> np.ndarray:
-    """V1 (n x n1): columns Phi0 | Phi | Phi1 spanning V_h,1 (eq. Phi0, eq. Phi1)."""
-    n = n_el + p - 2
-    n1, n2 = split_dims(n_el, p)
-    nc = n2 // 2                              # constraints per end: even derivatives 2k <= p-1
+def v1_basis(n_el: int, p: int, bc=(0, 0)) -> np.ndarray:
+    """V1 (n x n1): columns Phi0 | Phi | Phi1 spanning V_h,1 (eq. Phi0, eq. Phi1).  Phi0 (Phi1) is the part
+    of the span of the first (last) 2 c functions that meets the c conditions of its end; the functions in
+    between are taken one by one.  With equal ends 2 c = n2, the paper's blocks."""
+    n = n_el + p - 2 + bc[0] + bc[1]
+    n1, _ = split_dims(n_el, p, bc)
+    o0, o1 = end_orders(p, bc[0]), end_orders(p, bc[1])
+    a, b = 2 * len(o0), 2 * len(o1)
     V1 = np.zeros((n, n1))
     col = 0
-    if n2 > 0:
-        ders = [2 * k for k in range(1, nc + 1)]
-        D0 = np.array([bspline.dirichlet_basis(n_el, p, np.array([0.0]), d)[:n2, 0] for d in ders])
-        D1 = np.array([bspline.dirichlet_basis(n_el, p, np.array([1.0]), d)[n1:, 0] for d in ders])
-        Z0 = _nullspace(D0)                   # n2 x nc
-        Z1 = _nullspace(D1)
-        V1[:n2, :Z0.shape[1]] = Z0
+    if o0:
+        D0 = np.array([bspline.bc_basis(n_el, p, np.array([0.0]), d, bc)[:a, 0] for d in o0])
+        Z0 = _nullspace(D0)
+        V1[:a, :Z0.shape[1]] = Z0
         col = Z0.shape[1]
-    for i in range(n2, n1):
+    for i in range(a, n - b):
         V1[i, col] = 1.0
         col += 1
-    if n2 > 0:
-        V1[n1:, col:col + Z1.shape[1]] = Z1
+    if o1:
+        D1 = np.array([bspline.bc_basis(n_el, p, np.array([1.0]), d, bc)[n - b:, 0] for d in o1])
+        Z1 = _nullspace(D1)
+        V1[n - b:, col:col + Z1.shape[1]] = Z1
         col += Z1.shape[1]
     assert col == n1
     return V1
 
 
-def approx_eig(n: int, p: int):
+def approx_eig(n: int, p: int, bc=(0, 0)):
     """U~ (n x n) and Lambda~ (n) of App. B, built from their definitions with dense matrices."""
-    n_el = n - p + 2
-    n1, n2 = split_dims(n_el, p)
-    M = bspline.mass(n_el, p)
-    K = bspline.stiffness(n_el, p)
-    V1 = v1_basis(n_el, p)
-    x = interpolation_points(n_el, p)
-    E = bspline.dirichlet_basis(n_el, p, x, 0).T          # E[l, a] = b_a(x_l)
+    n_el = bspline.n_el_of(n, p, bc)
+    n1, n2 = split_dims(n_el, p, bc)
+    M = bspline.mass(n_el, p, bc)
+    K = bspline.stiffness(n_el, p, bc)
+    V1 = v1_basis(n_el, p, bc)
+    x = interpolation_points(n_el, p, bc)
+    E = bspline.bc_basis(n_el, p, x, 0, bc).T             # E[l, a] = b_a(x_l)
     Cint = E @ V1                                          # Cint[l, i] = v_i(x_l)
-    j = np.arange(1, n1 + 1)
-    Udft = np.sqrt(2.0) * np.sin(np.pi * np.outer(x, j))   # Udft[l, j] = sqrt(2) sin(j pi x_l)
+    Udft = sine_matrix(x, n1, bc)
     U1 = np.linalg.solve(Cint, Udft)                       # interpolation: Cint c = f(x)
-    lam1 = (j * np.pi) ** 2
+    lam1 = sine_frequencies(n1, bc) ** 2
     parts = [V1 @ U1]
     lams = [lam1]
     if n2 > 0:
@@ -126,52 +155,49 @@ def approx_eig(n: int, p: int):
     return np.concatenate(parts, axis=1), np.concatenate(lams)
 
 
-def sine_symbol(n_el: int, p: int) -> np.ndarray:
-    """mu_j = sum over the interpolation lattice of B(x_l - c) cos(j pi (x_l - c)) for a B-spline b with
+def sine_symbol(n_el: int, p: int, bc=(0, 0)) -> np.ndarray:
+    """mu_j = sum over the interpolation lattice of B(x_l - c) cos(omega_j (x_l - c)) for a B-spline b with
     centre c whose local knots are uniform: the factor by which collocating the uniform spline with
-    coefficients sin(j pi c_i) multiplies the samples sin(j pi x_l)."""
-    n = n_el + p - 2
-    n1, _ = split_dims(n_el, p)
-    x = interpolation_points(n_el, p)
-    kn = open_knots = bspline.open_uniform_knots(n_el, p)
-    i0 = (p - 1 + n_el - 2) // 2                  # reduced index of a function with distinct local knots
-    c0 = 0.5 * (kn[i0 + 1] + kn[i0 + p + 2])
-    vals = bspline.dirichlet_basis(n_el, p, x)[i0]
-    j = np.arange(1, n1 + 1)
-    return np.cos(np.pi * np.outer(j, x - c0)) @ vals
+    coefficients sin(omega_j c_i + phi) multiplies the samples sin(omega_j x_l + phi) (B is symmetric)."""
+    n1, _ = split_dims(n_el, p, bc)
+    x = interpolation_points(n_el, p, bc)
+    kn = bspline.open_uniform_knots(n_el, p)
+    f0 = (p + n_el - 1) // 2                     # full index of a function with distinct local knots
+    c0 = 0.5 * (kn[f0] + kn[f0 + p + 1])
+    vals = bspline.basis(kn, p, x)[f0]
+    return np.cos(np.outer(sine_frequencies(n1, bc), x - c0)) @ vals
 
 
-def sine_factorization(n: int, p: int):
+def sine_factorization(n: int, p: int, bc=(0, 0)):
     """(W, mu) with V1 U1 = W U_dft diag(1/mu): the App. B eigenvector block written as a sparse
     boundary correction W (n x n1) of the scaled sine transform.  Dense construction:
     W = (V1 U1) diag(mu) U_dft^{-1}; entries below 1e-11 max|W| are dropped."""
-    n_el = n - p + 2
-    n1, _ = split_dims(n_el, p)
-    U, _ = approx_eig(n, p)
-    x = interpolation_points(n_el, p)
-    j = np.arange(1, n1 + 1)
-    Udft = np.sqrt(2.0) * np.sin(np.pi * np.outer(x, j))
-    mu = sine_symbol(n_el, p)
+    n_el = bspline.n_el_of(n, p, bc)
+    n1, _ = split_dims(n_el, p, bc)
+    U, _ = approx_eig(n, p, bc)
+    x = interpolation_points(n_el, p, bc)
+    Udft = sine_matrix(x, n1, bc)
+    mu = sine_symbol(n_el, p, bc)
     W = np.linalg.solve(Udft.T, (U[:, :n1] * mu).T).T
     W[np.abs(W) < 1e-11 * np.abs(W).max()] = 0.0
     return W, mu, Udft
 
 
-def mp_value(n: int, p: int) -> float:
+def mp_value(n: int, p: int, bc=(0, 0)) -> float:
     """M_P = lambda_max / lambda_min (eq. estimate_prec_rel) for the same n, p in all directions."""
-    _, lam = approx_eig(n, p)
+    _, lam = approx_eig(n, p, bc)
     return (3.0 * lam.max()) / (3.0 * lam.min())
 
 
-def mp_value_fast(n_el: int, p: int) -> float:
-    """M_P from Lambda1 = (j pi)^2 and the small pencil on V_h,2 only (no dense U1)."""
-    n = n_el + p - 2
-    n1, n2 = split_dims(n_el, p)
-    lam = [np.pi ** 2, (n1 * np.pi) ** 2]
+def mp_value_fast(n_el: int, p: int, bc=(0, 0)) -> float:
+    """M_P from Lambda1 = omega_j^2 and the small pencil on V_h,2 only (no dense U1)."""
+    n1, n2 = split_dims(n_el, p, bc)
+    w = sine_frequencies(n1, bc)
+    lam = [w[0] ** 2, w[-1] ** 2]
     if n2 > 0:
-        M = bspline.mass(n_el, p)
-        K = bspline.stiffness(n_el, p)
-        V1 = v1_basis(n_el, p)
+        M = bspline.mass(n_el, p, bc)
+        K = bspline.stiffness(n_el, p, bc)
+        V1 = v1_basis(n_el, p, bc)
         N = _nullspace(V1.T)
         V2 = np.linalg.solve(M, N)
         lam2 = scipy.linalg.eigh(V2.T @ K @ V2, V2.T @ M @ V2, eigvals_only=True)
@@ -218,11 +244,14 @@ def expsum_for(M: float, eps_prec: float, rmax: int = 80):
 # Low-rank FD application (Alg. 4)
 # ---------------------------------------------------------------------------------------------
 class ApproxFD:
-    """Setup of Alg. 4 for n dofs and degree p in every direction."""
+    """Setup of Alg. 4 for n dofs, degree p and boundary conditions bc in every direction.  bc = (1, 1) (Neumann
+    at both ends of every direction) is rejected: its Kronecker sum has the constant in its kernel."""
 
-    def __init__(self, n: int, p: int, eps_prec: float = 0.1, expsum=None):
-        self.n, self.p = n, p
-        self.U, self.lam = approx_eig(n, p)
+    def __init__(self, n: int, p: int, eps_prec: float = 0.1, expsum=None, bc=(0, 0)):
+        if tuple(bc) == (1, 1):
+            raise ValueError("Neumann at both ends of every direction: singular operator")
+        self.n, self.p, self.bc = n, p, tuple(bc)
+        self.U, self.lam = approx_eig(n, p, bc)
         self.lmin = 3.0 * self.lam.min()
         self.lmax = 3.0 * self.lam.max()
         self.MP = self.lmax / self.lmin

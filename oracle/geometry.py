@@ -6,7 +6,9 @@ For a map F: [0,1]^3 -> Omega the stiffness matrix and load vector become integr
 parametric cube with Q(eta) = det(J) J^-1 J^-T and omega(eta) = det(J) f(F(eta)).
 
 Geometries (synthetic stand-ins for the paper's domains):
-  cube   -- identity map, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+  cube   -- identity map, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z); with Neumann flags bc = (k0, k1) on the
+            faces eta_t = 0 / 1 of every direction, f = 3 w^2 s(x) s(y) s(z) with s(t) = sin(w t + k0 pi/2),
+            w = (1 - k0/2 - k1/2) pi, so that u = s(x) s(y) s(z) solves the problem with those conditions
   twist  -- quarter annulus (rho = 1 + eta1 in [1,2], theta = pi/2 eta2) extruded along z = eta3,
             with the cross-section rotated about its centroid c by tau(eta3) = amp sin(pi eta3); f = 1.
 """
@@ -50,13 +52,21 @@ def twist_jacobian(e1, e2, e3, amp):
     return J
 
 
-def coefficients(kind: str, amp: float, e1, e2, e3):
+def cube_solution_1d(t, bc=(0, 0)):
+    """s(t) = sin(w t + k0 pi/2), w = (1 - k0/2 - k1/2) pi: zero at the Dirichlet ends, zero slope at the
+    Neumann ends; -s'' = w^2 s."""
+    w = (1.0 - 0.5 * (bc[0] + bc[1])) * np.pi
+    return np.sin(w * np.asarray(t, float) + 0.5 * np.pi * bc[0]), w
+
+
+def coefficients(kind: str, amp: float, e1, e2, e3, bc=(0, 0)):
     """Q (shape (..., 3, 3)) and omega (shape (...)) at the parametric points (App. A)."""
     e1, e2, e3 = np.broadcast_arrays(np.asarray(e1, float), np.asarray(e2, float), np.asarray(e3, float))
     if kind == "cube":
         Q = np.zeros(e1.shape + (3, 3))
         Q[..., 0, 0] = Q[..., 1, 1] = Q[..., 2, 2] = 1.0
-        om = 3.0 * np.pi ** 2 * np.sin(np.pi * e1) * np.sin(np.pi * e2) * np.sin(np.pi * e3)
+        s1, w = cube_solution_1d(e1, bc)
+        om = 3.0 * w ** 2 * s1 * cube_solution_1d(e2, bc)[0] * cube_solution_1d(e3, bc)[0]
         return Q, om
     if kind == "twist":
         J = twist_jacobian(e1, e2, e3, amp)

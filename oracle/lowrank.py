@@ -42,11 +42,11 @@ def cheb_eval(values: np.ndarray, x: np.ndarray) -> np.ndarray:
         np.polynomial.chebyshev.chebval(2.0 * x - 1.0, coef)
 
 
-def sample(kind: str, amp: float, N: int = N_CHEB):
+def sample(kind: str, amp: float, N: int = N_CHEB, bc=(0, 0)):
     """Q[k,l] and omega sampled on the N^3 Chebyshev grid; arrays indexed [i1, i2, i3]."""
     xc = cheb_points(N)
     e1, e2, e3 = np.meshgrid(xc, xc, xc, indexing="ij")
-    Q, om = geometry.coefficients(kind, amp, e1, e2, e3)
+    Q, om = geometry.coefficients(kind, amp, e1, e2, e3, bc)
     return Q, om
 
 
@@ -56,19 +56,20 @@ def tucker_of_samples(T: np.ndarray, eps: float):
     return core, S
 
 
-def operator_terms(kind: str, amp: float, n: int, p: int, eps: float = 1e-8, trial: str = "dirichlet"):
+def operator_terms(kind: str, amp: float, n: int, p: int, eps: float = 1e-8, trial: str = "dirichlet", bc=(0, 0)):
     """Kronecker-sum operator: list of (w, [K1, K2, K3]) with dense n x n matrices.
 
     A~ = sum_j w_j K3^j (x) K2^j (x) K1^j acts on vec(X) with mode 1 fastest (Sec. 2.3).
     With trial="full" the trial functions run over the whole B-spline basis (boundary functions included):
     the matrices are n x (n + 2), the operator between the interior test functions and all trial functions
-    that the non-homogeneous Dirichlet problem of the Remark in Sec. 3 needs.
+    that the non-homogeneous Dirichlet problem of the Remark in Sec. 3 needs.  bc = (k0, k1) marks Neumann ends
+    (the same in every direction): their end functions stay in the test and trial spaces.
     """
-    n_el = n - p + 2
+    n_el = bspline.n_el_of(n, p, bc)
     Q, _ = sample(kind, amp)
     xs, ws = bspline.quadrature(n_el, p)
-    B0 = bspline.dirichlet_basis(n_el, p, xs, 0)
-    B1 = bspline.dirichlet_basis(n_el, p, xs, 1)
+    B0 = bspline.bc_basis(n_el, p, xs, 0, bc)
+    B1 = bspline.bc_basis(n_el, p, xs, 1, bc)
     knots = bspline.open_uniform_knots(n_el, p)
     T0 = bspline.basis(knots, p, xs, 0) if trial == "full" else B0
     T1 = bspline.basis(knots, p, xs, 1) if trial == "full" else B1
@@ -100,20 +101,20 @@ def operator_terms(kind: str, amp: float, n: int, p: int, eps: float = 1e-8, tri
     return terms
 
 
-def rhs_tucker(kind: str, amp: float, n: int, p: int, eps: float = 1e-8):
+def rhs_tucker(kind: str, amp: float, n: int, p: int, eps: float = 1e-8, bc=(0, 0)):
     """Tucker rhs f~: core W and factors [F_t]_{ij} = int b_i u_{t,j} (App. A)."""
-    n_el = n - p + 2
-    _, om = sample(kind, amp)
+    n_el = bspline.n_el_of(n, p, bc)
+    _, om = sample(kind, amp, bc=bc)
     core, U = tucker_of_samples(om, eps)
     xs, ws = bspline.quadrature(n_el, p)
-    B0 = bspline.dirichlet_basis(n_el, p, xs, 0)
+    B0 = bspline.bc_basis(n_el, p, xs, 0, bc)
     F = [(B0 * ws) @ cheb_eval(U[t], xs) for t in range(3)]
     return core, F
 
 
-def cube_terms(n: int, p: int):
+def cube_terms(n: int, p: int, bc=(0, 0)):
     """The exact unit-cube operator K(x)M(x)M + M(x)K(x)M + M(x)M(x)K (eq. FD_prec with Q = I)."""
-    n_el = n - p + 2
-    M = bspline.mass(n_el, p)
-    K = bspline.stiffness(n_el, p)
+    n_el = bspline.n_el_of(n, p, bc)
+    M = bspline.mass(n_el, p, bc)
+    K = bspline.stiffness(n_el, p, bc)
     return [(1.0, [K, M, M]), (1.0, [M, K, M]), (1.0, [M, M, K])]
