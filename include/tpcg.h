@@ -66,7 +66,8 @@ typedef struct tpcg_ctx_s* tpcg_ctx;          /* workspace for one solve stream 
 typedef struct tpcg_problem_s* tpcg_problem;  /* operator A~, rhs f~, preconditioner P~ on the device */
 
 /* ------------------------------------------------------------------------------------ problem setup */
-#define TPCG_GEOM_CUBE 0    /* identity map, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)                 */
+#define TPCG_GEOM_CUBE 0    /* identity map, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z); with Neumann faces
+                               f = 3 w^2 s(x) s(y) s(z), s(t) = sin(w t + k0 pi/2), w = (1 - k0/2 - k1/2) pi */
 #define TPCG_GEOM_TWIST 1   /* quarter annulus rho in [1,2], theta in [0,pi/2], extruded along z, with the
                                cross-section rotated about its centroid by amp sin(pi z); f = 1       */
 
@@ -75,13 +76,17 @@ typedef struct {
     double amp;         /* twist amplitude (radians), TPCG_GEOM_TWIST only                            */
     double eps_geo;     /* relative tolerance of the low-rank coefficient approximation (App. A); 0 = 1e-8 */
     double eps_prec;    /* relative tolerance of the preconditioner, eq. prec_bound; 0 = 0.1         */
+    int k0, k1;         /* boundary conditions on the faces eta_t = 0 (k0) and eta_t = 1 (k1) of every
+                           direction t: 0 homogeneous Dirichlet, 1 homogeneous Neumann (App. B's flags).
+                           (0,0), (0,1) or (1,0); (1,1) would leave the constant in the kernel           */
 } tpcg_geometry;
 
 /* Host FP64 setup (App. A, App. B, Prop. 1) followed by upload: B-spline matrices, low-rank Chebyshev
  * approximation of Q(eta) and omega(eta) folded into a Kronecker sum A~ = sum_j w_j K3^j (x) K2^j (x) K1^j,
  * the Tucker rhs f~ (rounded losslessly), and the low-rank FD tables with the exponential sums chosen by
  * TPCG_OPT_EXPSUM_BEST (by default the best sums, R_P of eq. estimate_prec_rel as in Table 1).  n dofs per
- * direction, degree p, n_el = n - p + 2 > p.  dtype selects the precision of the device copies.  *out is
+ * direction, degree p, n_el = n - p + 2 - k0 - k1 > p: a Neumann end keeps its end function (the natural
+ * condition), and the preconditioner takes App. B's Neumann variant.  dtype selects the precision of the device copies.  *out is
  * owned by the caller and released with tpcg_problem_destroy. */
 int tpcg_setup(const tpcg_geometry* geo, int degree, int n, int dtype, tpcg_problem* out);
 
@@ -89,13 +94,15 @@ int tpcg_setup(const tpcg_geometry* geo, int degree, int n, int dtype, tpcg_prob
  *   R terms: weights w[R]; bands[((j*3 + t)*(2p+1) + d)*n + i] = K_t^j[i, i + d - p] (zero outside);
  *   rhs: core f_core (rf1 x rf2 x rf3), factors f_U[t] (n x rf_t);
  *   preconditioner (Alg. 4 with the eigenvector factorisation of App. B):
- *     lam[n]      : Lambda~ (first n1 entries (j pi)^2, then Lambda2),
+ *     lam[n]      : Lambda~ (first n1 entries omega_j^2, omega_j = (j - k0/2 - k1/2) pi, then Lambda2),
  *     mu[n1]      : sine-basis scaling, U~[:, :n1] = W U_dft diag(1/mu),
  *     W (n x n1)  : sparse, given in CSR: w_rowptr[n+1], w_col[nnz], w_val[nnz],
  *     v2u2 (n x n2): V2 U2 dense,
- *     RP exponential-sum pairs omega[RP], alpha[RP], lambda_min.
- *   The sine transform is DST-I (U_dft[l,j] = sqrt2 sin(j pi l/(n1+1))) for odd p and DST-II
- *   (U_dft[l,j] = sqrt2 sin(j pi (l-1/2)/n1)) for even p, l, j = 1..n1. */
+ *     RP exponential-sum pairs omega[RP], alpha[RP], lambda_min,
+ *     k0, k1      : Neumann flags of the two ends (the same in every direction; (1,1) is refused).
+ *   The sine transform is U_dft[l,j] = sqrt2 sin(omega_j x_l + k0 pi/2), l, j = 1..n1, on the interpolation
+ *   points x_l of App. B: the breakpoints i/n_el without the Dirichlet ends for odd p (n_el = n1 + 1 - k0 -
+ *   k1), the span midpoints (l - 1/2)/n1 for even p.  With k0 = k1 = 0 it is DST-I (odd p) or DST-II (even p). */
 typedef struct {
     int n, p, R, dtype;
     const double* w;
@@ -113,6 +120,7 @@ typedef struct {
     const double* omega;
     const double* alpha;
     double lambda_min;
+    int k0, k1;
 } tpcg_problem_arrays;
 
 /* Returns TPCG_E_INVALID, before any device work, for inconsistent sizes or a NaN/Inf in any table. */
@@ -122,6 +130,7 @@ typedef struct {
     int n, p, R, RP, n1, n2, rf[3], dtype;
     double lambda_min, lambda_max, MP, norm_f;
     int w_nnz;          /* non-zeros of W */
+    int k0, k1;         /* Neumann flags of the ends */
 } tpcg_problem_info;
 
 int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* out);
@@ -268,7 +277,8 @@ int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, c
  * Forms: TPCG_F64 and TPCG_F32. */
 typedef struct tpcg_elast_s* tpcg_elast;
 
-/* Host FP64 setup of all nine blocks (force: 3 host doubles, the constant body force), then upload. */
+/* Host FP64 setup of all nine blocks (force: 3 host doubles, the constant body force), then upload.
+ * Homogeneous Dirichlet conditions on every face: geo->k0 and geo->k1 must be 0 (else TPCG_E_INVALID). */
 int tpcg_elast_setup(const tpcg_geometry* geo, int degree, int n, double lame_lambda, double lame_mu,
                      const double* force, int dtype, tpcg_elast* out);
 /* The same from caller tables: blocks[3 i + j] describes A_ij (its rhs fields give f_i; the preconditioner

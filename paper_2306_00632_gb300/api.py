@@ -153,8 +153,11 @@ class Problem:
         return out
 
 
-def tpcg_setup(kind: int, amp: float, degree: int, n: int, dtype: int = L.F64, eps_geo=0.0, eps_prec=0.0) -> Problem:
-    g = L.Geometry(kind, amp, eps_geo, eps_prec)
+def tpcg_setup(kind: int, amp: float, degree: int, n: int, dtype: int = L.F64, eps_geo=0.0, eps_prec=0.0,
+               bc=(0, 0)) -> Problem:
+    """bc = (k0, k1): 1 marks a homogeneous Neumann condition on the faces eta_t = 0 (k0) / eta_t = 1 (k1) of
+    every direction, 0 a homogeneous Dirichlet one."""
+    g = L.Geometry(kind, amp, eps_geo, eps_prec, int(bc[0]), int(bc[1]))
     h = C.c_void_p()
     check(L.load().tpcg_setup(C.byref(g), degree, n, dtype, C.byref(h)), "tpcg_setup")
     return Problem(h.value, dtype)
@@ -203,6 +206,7 @@ def problem_from_export(ex, info, dtype=L.F64, pinned=True, rhs=None) -> Problem
     a.omega = dptr(ex["omega"])
     a.alpha = dptr(ex["alpha"])
     a.lambda_min = info.lambda_min
+    a.k0, a.k1 = info.k0, info.k1
     h = C.c_void_p()
     check(L.load().tpcg_problem_create(C.byref(a), C.byref(h)), "tpcg_problem_create")
     return Problem(h.value, dtype)
@@ -255,12 +259,14 @@ def _problem_arrays(n, p, terms, f_core, f_U, fd, dtype, keep):
     a.omega = dp(fd["omega"])
     a.alpha = dp(fd["alpha"])
     a.lambda_min = float(fd["lambda_min"])
+    a.k0, a.k1 = (int(v) for v in fd.get("bc", (0, 0)))
     return a
 
 
 def tpcg_problem_create(n, p, terms, f_core, f_U, fd, dtype=L.F64) -> Problem:
     """Problem from host arrays.  terms: list of (w, [K1, K2, K3]) dense banded n x n matrices;
-    fd: dict with lam, mu, W (dense n x n1), v2u2 (n x n2), omega, alpha, lambda_min."""
+    fd: dict with lam, mu, W (dense n x n1), v2u2 (n x n2), omega, alpha, lambda_min and optionally bc = (k0, k1),
+    the Neumann flags of the ends (default (0, 0))."""
     keep = []
     a = _problem_arrays(n, p, terms, f_core, f_U, fd, dtype, keep)
     h = C.c_void_p()

@@ -453,7 +453,7 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
     if (n < 2 || p < 1 || p > 5 || a->R < 1 || a->R > TPCG_MAX_BLOCKS - 1 || a->n1 < 1 || a->n2 < 0 ||
         a->n1 + a->n2 != n || a->RP < 1 || a->RP > TPCG_MAX_BLOCKS || (a->dtype != TPCG_F64 && a->dtype != TPCG_F32) ||
         !a->w || !a->bands || !a->f_core || !a->lam || !a->mu || !a->w_rowptr || !a->omega || !a->alpha ||
-        a->lambda_min <= 0) {
+        a->lambda_min <= 0 || a->k0 < 0 || a->k0 > 1 || a->k1 < 0 || a->k1 > 1 || (a->k0 && a->k1)) {
         set_error("tpcg_problem_create: invalid arguments");
         return TPCG_E_INVALID;
     }
@@ -490,6 +490,7 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
     pb->d_wrow = pb->d_wcol = pb->d_wtrow = pb->d_wtcol = nullptr;
     pb->d_omega = pb->d_alpha = pb->d_scal = nullptr;
     pb->n = n; pb->p = p; pb->R = a->R; pb->RP = a->RP; pb->n1 = a->n1; pb->n2 = a->n2; pb->dtype = a->dtype;
+    pb->k0 = a->k0; pb->k1 = a->k1;
     for (int t = 0; t < 3; ++t) pb->rf[t] = a->rf[t];
     pb->lambda_min = a->lambda_min;
     const int bw = 2 * p + 1;
@@ -535,23 +536,14 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
                 fill[l]++;
             }
     }
-    // sine matrix U_dft[l, j] = sqrt2 sin(j pi x_l): DST-I points l/(n1+1) for odd p, DST-II (l - 1/2)/n1 for even p
+    // sine matrix U_dft[l, j] = sqrt2 sin(omega_j x_l + k0 pi/2) with the phase reduced exactly on its integer grid
     const int n1 = a->n1;
+    const SineGrid sg = sine_grid(n1, p, a->k0, a->k1);
     std::vector<double> dst((size_t)n1 * n1);
-    for (int j = 1; j <= n1; ++j)
-        for (int l = 1; l <= n1; ++l) {
-            double xl = (p % 2 == 1) ? (double)l / (n1 + 1) : (l - 0.5) / n1;
-            // sin(j pi x) evaluated with the argument reduced exactly on the rational grid
-            double arg;
-            if (p % 2 == 1) {
-                long long m = ((long long)j * l) % (2LL * (n1 + 1));
-                arg = M_PI * (double)m / (n1 + 1);
-            } else {
-                long long m = ((long long)j * (2 * l - 1)) % (4LL * n1);
-                arg = M_PI * (double)m / (2.0 * n1);
-            }
-            (void)xl;
-            dst[(l - 1) + (size_t)(j - 1) * n1] = sqrt(2.0) * sin(arg);
+    for (long long j = 0; j < n1; ++j)
+        for (long long l = 0; l < n1; ++l) {
+            const long long m = ((2 * j + sg.e) * (2 * l + sg.c) + sg.g) % (8 * sg.D);
+            dst[l + j * n1] = sqrt(2.0) * sin(M_PI * (double)m / (4.0 * (double)sg.D));
         }
     std::vector<void*> owned;   // not used: problem buffers are tracked in the struct
     int s = TPCG_OK;
@@ -575,7 +567,7 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
     if ((s = upload(&pb->d_dst, dst.data(), dst.size(), dt, nullptr))) return fail(s);
     if (n1 <= 1024) {   // FFT sine transforms (complex pairs in the compute dtype)
         std::vector<double> ct;
-        if ((s = chirp_tables(n1, p, &pb->chirp, &ct))) return fail(s);
+        if ((s = chirp_tables(n1, p, a->k0, a->k1, &pb->chirp, &ct))) return fail(s);
         if ((s = upload(&pb->d_chirp, ct.data(), ct.size(), dt, nullptr))) return fail(s);
     }
     if ((s = dmalloc(reinterpret_cast<void**>(&pb->d_omega), a->RP * sizeof(double), nullptr))) return fail(s);
@@ -625,6 +617,7 @@ extern "C" int tpcg_setup(const tpcg_geometry* geo, int degree, int n, int dtype
     a.w_rowptr = hp.w_rowptr.data(); a.w_col = hp.w_col.data(); a.w_val = hp.w_val.data();
     a.v2u2 = hp.v2u2.empty() ? nullptr : hp.v2u2.data();
     a.omega = hp.omega.data(); a.alpha = hp.alpha.data(); a.lambda_min = hp.lambda_min;
+    a.k0 = hp.k0; a.k1 = hp.k1;
     return tpcg_problem_create(&a, out);
 }
 
@@ -637,6 +630,8 @@ extern "C" int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* o) {
     o->MP = pb->lambda_max / pb->lambda_min;
     o->norm_f = pb->norm_f;
     o->w_nnz = (int)pb->w_val.size();
+    o->k0 = pb->k0;
+    o->k1 = pb->k1;
     return TPCG_OK;
 }
 

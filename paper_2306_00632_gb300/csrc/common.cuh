@@ -189,6 +189,7 @@ struct ChirpInfo {
 
 struct tpcg_problem_s {
     int n, p, R, RP, n1, n2, dtype;
+    int k0, k1;          // Neumann flags of the two ends (App. B's sine variant)
     int rf[3];
     double lambda_min, lambda_max, norm_f;
     // host copies (double)

@@ -1,14 +1,16 @@
 // Sine transforms of the fast-diagonalization preconditioner (Alg. 4 with the eigenvector basis of App. B)
 // by FFTs: O(n1 log n1) per column instead of the dense n1 x n1 product.
 //
-// App. B writes the eigenvector block as U_dft[l, j] = sqrt2 sin(j pi x_l) on the interpolation points: DST-I
-// (x_l = l / (n1 + 1)) for odd degree and DST-II (x_l = (l - 1/2) / n1) for even degree; Alg. 4 applies
-// U_dft^T (forward) and U_dft (inverse, DST-III for even degree).  With 0-based indices q (input) and o
-// (output) every one of them is
+// App. B writes the eigenvector block as U_dft[l, j] = sqrt2 sin(omega_j x_l + k0 pi/2) on the interpolation
+// points, omega_j = (j - k0/2 - k1/2) pi with the Neumann flags k0, k1 of the two ends: for two Dirichlet ends
+// DST-I (odd degree) or DST-II (even degree), with a Neumann end the half-shifted sine and cosine variants.
+// Alg. 4 applies U_dft^T (forward) and U_dft (inverse).  On the integer grid of sine_grid (kernels.cuh), with
+// 0-based indices q (input) and o (output), every one of them is
 //     y_o = sqrt2 Im( sum_q x_q exp(i pi (4 q o + a q + b o + g) / (4 D)) ),
-// D = n1 + 1 and (a, b, g) = (4, 4, 4) for DST-I; D = n1 and (4, 2, 2) forward, (2, 4, 2) inverse for even
-// degree.  Any length n1 (126 = 2 3^2 7 or 510 = 2 3 5 17 in the benchmark sizes) is handled by Bluestein's
-// chirp-z identity 2 q o = q^2 + o^2 - (o - q)^2:
+// (a, b) = (2e, 2c) forward and (2c, 2e) inverse, g = e c + 2 k0 D (for two Dirichlet ends: D = n1 + 1 and
+// (4, 4, 4) for odd degree; D = n1 and (4, 2, 2) forward, (2, 4, 2) inverse for even degree).  Any length n1
+// (126 = 2 3^2 7 or 510 = 2 3 5 17 in the benchmark sizes) is handled by Bluestein's chirp-z identity
+// 2 q o = q^2 + o^2 - (o - q)^2:
 //     y_o = Im( post_o  sum_q (x_q pre_q) h_(o - q) ),   pre_q = e(a q + 2 q^2), post_o = sqrt2 e(b o + g + 2 o^2),
 //     h_k = e(-2 k^2),  e(m) = exp(i pi m / (4 D)),
 // a linear convolution evaluated with power-of-two FFTs of size Mf >= 2 n1 - 1 in shared memory: a
@@ -32,8 +34,18 @@ static int bit_reverse(int i, int bits) {
     return r;
 }
 
+SineGrid sine_grid(int n1, int p, int k0, int k1) {
+    SineGrid g;
+    const bool odd = (p % 2) == 1;
+    g.D = odd ? n1 + 1 - k0 - k1 : n1;   // n_el
+    g.e = 2 - k0 - k1;
+    g.c = odd ? 2 - 2 * k0 : 1;
+    g.g = 2 * k0 * g.D;
+    return g;
+}
+
 // host tables in complex double pairs: [tw (Mf/2)] [pre_0 (L)] [post_0 (L)] [hs_0 (Mf)] [pre_1] [post_1] [hs_1]
-int chirp_tables(int n1, int p, ChirpInfo* info, std::vector<double>* out) {
+int chirp_tables(int n1, int p, int k0, int k1, ChirpInfo* info, std::vector<double>* out) {
     if (n1 < 1 || n1 > 4096) {
         set_error("chirp_tables: n1 out of range");
         return TPCG_E_INVALID;
@@ -42,8 +54,8 @@ int chirp_tables(int n1, int p, ChirpInfo* info, std::vector<double>* out) {
     int Mf = 1, logm = 0;
     while (Mf < 2 * L - 1) { Mf *= 2; ++logm; }
     if (Mf < 2) { Mf = 2; logm = 1; }
-    const bool odd = (p % 2) == 1;
-    const long long D = odd ? n1 + 1 : n1;
+    const SineGrid sg = sine_grid(n1, p, k0, k1);
+    const long long D = sg.D;
     const long long per = 8 * D;
     auto phase = [&](long long m, double* re, double* im) {
         long long r = m % per;
@@ -65,10 +77,9 @@ int chirp_tables(int n1, int p, ChirpInfo* info, std::vector<double>* out) {
     }
     size_t off = (size_t)Mf / 2;
     for (int kind = 0; kind < 2; ++kind) {
-        long long a4 = 4, b4 = 4, g4 = 4;
-        if (!odd) {
-            if (kind == 0) { a4 = 4; b4 = 2; g4 = 2; } else { a4 = 2; b4 = 4; g4 = 2; }
-        }
+        const long long a4 = kind == 0 ? 2 * sg.e : 2 * sg.c;
+        const long long b4 = kind == 0 ? 2 * sg.c : 2 * sg.e;
+        const long long g4 = sg.e * sg.c + sg.g;
         for (long long q = 0; q < L; ++q) phase(a4 * q + 2 * q * q, &o[2 * (off + q)], &o[2 * (off + q) + 1]);
         off += L;
         for (long long q = 0; q < L; ++q) {

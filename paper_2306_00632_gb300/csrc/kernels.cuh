@@ -62,7 +62,15 @@ int copy_tensor_impl(const tucker_t* src, tucker_t* dst, int n, int cap, cudaStr
 // chirp-z (Bluestein) FFT sine transforms of App. B (dst.cu): host tables for length n1 and degree p (complex
 // pairs: twiddles, then forward and inverse pre/post chirps and filter spectra), and the batched transform of
 // the columns c < mult rank_t of every mode t (kind 0: U_dft^T x, kind 1: U_dft x)
-int chirp_tables(int n1, int p, ChirpInfo* info, std::vector<double>* out);
+// Integer phase grid of App. B's sine matrix, 0-based l (point) and j (sinusoid):
+//   U_dft[l, j] = sqrt2 sin(omega_j x_l + k0 pi/2) = sqrt2 sin(pi m / (4 D)),  m = (2 j + e)(2 l + c) + g,
+// D = n_el, e = 2 - k0 - k1, c = 2 - 2 k0 (odd p: breakpoints without the Dirichlet ends) or 1 (even p: span
+// midpoints), g = 2 k0 D.
+struct SineGrid {
+    long long D, e, c, g;
+};
+SineGrid sine_grid(int n1, int p, int k0, int k1);
+int chirp_tables(int n1, int p, int k0, int k1, ChirpInfo* info, std::vector<double>* out);
 template <typename T>
 int launch_chirp(tpcg_problem pb, int kind, const TuckerDesc* sd, int mult, int rp_guard, int vcap, int maxcols,
                  const T* const* X, T* const* Y, int ldx, int ldy, cudaStream_t st);

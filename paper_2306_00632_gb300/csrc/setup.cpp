@@ -338,19 +338,22 @@ void gauss_legendre(int q, Vec* x, Vec* w) {
     }
 }
 
-// quadrature on all spans: points, weights, and the p+1 non-zero (Dirichlet-reduced) values/derivatives
+// quadrature on all spans: points, weights, and the p+1 non-zero values/derivatives.  The space drops the end
+// function of every Dirichlet end (k = 0) and keeps that of every Neumann end (k = 1): n = m - 2 + k0 + k1.
 struct Quad {
-    int q = 0, n_el = 0, p = 0, n = 0;
+    int q = 0, n_el = 0, p = 0, n = 0, k0 = 0, k1 = 0;
     Vec x, w;                     // n_el * q
     std::vector<int> first;       // reduced index of the first local function (may be -1)
     std::vector<Vec> val, der;    // [pt][0..p]
 };
 
-Quad make_quad(const Spline& sp) {
+Quad make_quad(const Spline& sp, int k0 = 0, int k1 = 0) {
     Quad Q;
     Q.p = sp.p;
     Q.n_el = sp.n_el;
-    Q.n = sp.m - 2;
+    Q.k0 = k0;
+    Q.k1 = k1;
+    Q.n = sp.m - 2 + k0 + k1;
     Q.q = sp.p + 3;
     Vec gx, gw;
     gauss_legendre(Q.q, &gx, &gw);
@@ -365,7 +368,7 @@ Quad make_quad(const Spline& sp) {
             sp.ders(s, xx, 1, &d);
             Q.val.push_back(d[0]);
             Q.der.push_back(d[1]);
-            Q.first.push_back(s - sp.p - 1);
+            Q.first.push_back(s - sp.p - 1 + k0);
         }
     return Q;
 }
@@ -433,8 +436,10 @@ void inverse_jacobian(int kind, double amp, double e1, double e2, double e3, dou
     *detJ = det;
 }
 
-// Poisson: Q = det J J^-1 J^-T and omega = det J f (App. A)
-void coefficients(int kind, double amp, double e1, double e2, double e3, double Q[3][3], double* om) {
+// Poisson: Q = det J J^-1 J^-T and omega = det J f (App. A).  The cube's f makes u = s(x) s(y) s(z) the solution,
+// s(t) = sin(w t + k0 pi/2), w = (1 - k0/2 - k1/2) pi (zero at Dirichlet faces, zero slope at Neumann faces).
+void coefficients(int kind, double amp, double e1, double e2, double e3, double Q[3][3], double* om, int k0 = 0,
+                  int k1 = 0) {
     double Ji[3][3], det;
     inverse_jacobian(kind, amp, e1, e2, e3, Ji, &det);
     for (int a = 0; a < 3; ++a)
@@ -443,9 +448,10 @@ void coefficients(int kind, double amp, double e1, double e2, double e3, double 
             for (int k = 0; k < 3; ++k) v += Ji[a][k] * Ji[b][k];
             Q[a][b] = det * v;
         }
-    if (kind == TPCG_GEOM_CUBE)
-        *om = 3 * M_PI * M_PI * sin(M_PI * e1) * sin(M_PI * e2) * sin(M_PI * e3);
-    else
+    if (kind == TPCG_GEOM_CUBE) {
+        const double w = (1.0 - 0.5 * (k0 + k1)) * M_PI, ph = 0.5 * M_PI * k0;
+        *om = 3 * w * w * sin(w * e1 + ph) * sin(w * e2 + ph) * sin(w * e3 + ph);
+    } else
         *om = det * 1.0;
 }
 
@@ -642,13 +648,21 @@ static void rhs_from_samples(const Ten& Tw, double eps_geo, const Quad& Q, int n
 
 }
 
-// App. B eigenpairs (sparse sine factorization, V2 U2, Lambda~) and the exponential sum of Prop. 1
+// App. B eigenpairs (sparse sine factorization, V2 U2, Lambda~) and the exponential sum of Prop. 1.  The ends
+// carry the conditions of Q (k = 0 Dirichlet, 1 Neumann): V_h,1 asks the even derivatives 2, 4, .. <= p - 1 to
+// vanish at a Dirichlet end and the odd ones 1, 3, .. <= p - 1 at a Neumann end; an end with c conditions
+// contributes the part of the span of its 2c end functions that meets them (c functions) to V1 and the rest
+// (c functions) to null(V1^T).  The sinusoids are sin(omega_j x + k0 pi/2), omega_j = (j - k0/2 - k1/2) pi.
 static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_prec, HostProblem& H) {
-    const int n_el = n - p + 2;
+    const int n_el = sp.n_el, k0 = Q.k0, k1 = Q.k1;
     const int bw = 2 * p + 1;
-    const int n1 = (p % 2 == 1) ? n_el - 1 : n_el;
-    const int n2 = n - n1;
-    const int nc = n2 / 2;   // conditions per end: even derivatives 2k <= p - 1
+    int nord[2] = {0, 0}, ord[2][4];
+    for (int end = 0; end < 2; ++end)
+        for (int d = ((end == 0 ? k0 : k1) == 1 ? 1 : 2); d <= p - 1; d += 2) ord[end][nord[end]++] = d;
+    const int c0 = nord[0], c1 = nord[1];
+    const int blk[2] = {2 * c0, 2 * c1};   // end functions holding the conditions
+    const int n1 = n - c0 - c1;
+    const int n2 = c0 + c1;
     H.n1 = n1;
     H.n2 = n2;
     std::vector<double> Mb((size_t)bw * n), Kb((size_t)bw * n);
@@ -657,56 +671,56 @@ static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_p
     Mat Md = band_to_dense(Mb.data(), n, p), Kd = band_to_dense(Kb.data(), n, p);
     // V1: Phi0 | Phi | Phi1
     Mat V1(n, n1);
-    Mat Z0(n2, nc), Z1(n2, nc);
-    if (n2 > 0) {
-        for (int end = 0; end < 2; ++end) {
-            const double xe = end == 0 ? 0.0 : 1.0;
-            const int s = sp.span(xe);
-            std::vector<Vec> d;
-            sp.ders(s, xe, 2 * nc, &d);
-            // D (nc x n2): rows = derivatives 2, 4, .., 2nc of the n2 end functions
-            Mat D(nc, n2);
-            const int base = end == 0 ? 0 : n1;   // reduced index of the first end function
-            for (int kk = 1; kk <= nc; ++kk) {
-                double sc = 0;
-                for (int a = 0; a <= p; ++a) {
-                    const int i = s - p - 1 + a;
-                    if (i >= base && i < base + n2) D(kk - 1, i - base) = d[2 * kk][a];
-                    sc = std::max(sc, fabs(d[2 * kk][a]));
-                }
-                for (int c = 0; c < n2; ++c) D(kk - 1, c) /= sc;
+    Mat Z[2] = {Mat(blk[0], c0), Mat(blk[1], c1)};
+    for (int end = 0; end < 2; ++end) {
+        const int c = nord[end], m = blk[end];
+        if (c == 0) continue;
+        const double xe = end == 0 ? 0.0 : 1.0;
+        const int s = sp.span(xe);
+        std::vector<Vec> d;
+        sp.ders(s, xe, ord[end][c - 1], &d);
+        // D (c x m): rows = the end's derivative orders, columns = its m end functions
+        Mat D(c, m);
+        const int base = end == 0 ? 0 : n - m;   // reduced index of the first end function
+        for (int kk = 0; kk < c; ++kk) {
+            double sc = 0;
+            for (int a = 0; a <= p; ++a) {
+                const int i = s - p - 1 + k0 + a;
+                if (i >= base && i < base + m) D(kk, i - base) = d[ord[end][kk]][a];
+                sc = std::max(sc, fabs(d[ord[end][kk]][a]));
             }
-            Vec ev;
-            Mat EV;
-            sym_eig(matmul(D, D, true, false), &ev, &EV);   // null space: the n2 - nc smallest
-            Mat& Z = end == 0 ? Z0 : Z1;
-            for (int c = 0; c < nc; ++c)
-                for (int i = 0; i < n2; ++i) Z(i, c) = EV(i, c);
+            for (int q = 0; q < m; ++q) D(kk, q) /= sc;
         }
-        for (int c = 0; c < nc; ++c)
-            for (int i = 0; i < n2; ++i) {
-                V1(i, c) = Z0(i, c);
-                V1(n1 + i, n1 - nc + c) = Z1(i, c);
-            }
+        Vec ev;
+        Mat EV;
+        sym_eig(matmul(D, D, true, false), &ev, &EV);   // null space: the m - c smallest
+        for (int q = 0; q < c; ++q)
+            for (int i = 0; i < m; ++i) Z[end](i, q) = EV(i, q);
     }
-    for (int i = n2; i < n1; ++i) V1(i, nc + (i - n2)) = 1.0;
-    // interpolation points and collocation Cint[l, i] = v_i(x_l)
+    for (int q = 0; q < c0; ++q)
+        for (int i = 0; i < blk[0]; ++i) V1(i, q) = Z[0](i, q);
+    for (int i = blk[0]; i < n - blk[1]; ++i) V1(i, c0 + (i - blk[0])) = 1.0;
+    for (int q = 0; q < c1; ++q)
+        for (int i = 0; i < blk[1]; ++i) V1(n - blk[1] + i, n1 - c1 + q) = Z[1](i, q);
+    // interpolation points (breakpoints without the Dirichlet ends, or span midpoints) and Cint[l, i] = v_i(x_l)
     Vec xi(n1);
-    for (int l = 1; l <= n1; ++l) xi[l - 1] = (p % 2 == 1) ? (double)l / n_el : (l - 0.5) / n_el;
+    for (int l = 0; l < n1; ++l) xi[l] = (p % 2 == 1) ? (double)(l + 1 - k0) / n_el : (l + 0.5) / n_el;
     Mat E(n1, n);
     for (int l = 0; l < n1; ++l) {
         const int s = sp.span(xi[l]);
         std::vector<Vec> d;
         sp.ders(s, xi[l], 0, &d);
         for (int a = 0; a <= p; ++a) {
-            const int i = s - p - 1 + a;
+            const int i = s - p - 1 + k0 + a;
             if (i >= 0 && i < n) E(l, i) = d[0][a];
         }
     }
     Mat Cint = matmul(E, V1);
+    Vec om(n1);
+    for (int j = 0; j < n1; ++j) om[j] = (j + 1 - 0.5 * (k0 + k1)) * M_PI;
     Mat Udft(n1, n1);
     for (int l = 0; l < n1; ++l)
-        for (int j = 0; j < n1; ++j) Udft(l, j) = sqrt(2.0) * sin((j + 1) * M_PI * xi[l]);
+        for (int j = 0; j < n1; ++j) Udft(l, j) = sqrt(2.0) * sin(om[j] * xi[l] + 0.5 * M_PI * k0);
     Mat U1 = Udft;
     if (!lu_solve(Cint, U1)) {
         set_error("tpcg_setup: singular collocation matrix");
@@ -715,14 +729,15 @@ static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_p
     Mat V1U1 = matmul(V1, U1);
     // mu_j: symbol of an interior B-spline sampled on the interpolation lattice
     {
-        const int i0 = (p - 1 + n_el - 2) / 2;   // an interior function: distinct local knots
-        const double c0 = 0.5 * (sp.knots[i0 + 1] + sp.knots[i0 + 1 + p + 1]);   // centre of reduced b_{i0}
+        const int f0 = (p + n_el - 1) / 2;   // full index of an interior function: distinct local knots
+        const int i0 = f0 - 1 + k0;          // its reduced index
+        const double cen = 0.5 * (sp.knots[f0] + sp.knots[f0 + p + 1]);
         H.mu.assign(n1, 0.0);
         for (int l = 0; l < n1; ++l) {
             const double v = E(l, i0);
             if (v == 0.0) continue;
-            const double off = xi[l] - c0;
-            for (int j = 0; j < n1; ++j) H.mu[j] += v * cos((j + 1) * M_PI * off);
+            const double off = xi[l] - cen;
+            for (int j = 0; j < n1; ++j) H.mu[j] += v * cos(om[j] * off);
         }
     }
     // W = V1U1 diag(mu) U_dft^{-1}  (solve U_dft^T W^T = (V1U1 diag mu)^T), then keep its sparse pattern
@@ -753,17 +768,18 @@ static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_p
     }
     // V2 = M^{-1} N with N a basis of null(V1^T); U2, Lambda2 from the projected pencil
     H.lam.assign(n, 0.0);
-    for (int j = 0; j < n1; ++j) H.lam[j] = ((j + 1) * M_PI) * ((j + 1) * M_PI);
+    for (int j = 0; j < n1; ++j) H.lam[j] = om[j] * om[j];
     H.v2u2.clear();
     if (n2 > 0) {
         Mat N(n, n2);
         for (int end = 0; end < 2; ++end) {
-            Mat& Z = end == 0 ? Z0 : Z1;
+            const int c = nord[end], m = blk[end];
+            if (c == 0) continue;
             Vec ev;
             Mat EV;
-            sym_eig(matmul(Z, Z, false, true), &ev, &EV);   // null(Z^T): eigenvectors of Z Z^T with eigenvalue 0
-            for (int c = 0; c < n2 - nc; ++c)
-                for (int i = 0; i < n2; ++i) N((end == 0 ? 0 : n1) + i, end * (n2 - nc) + c) = EV(i, c);
+            sym_eig(matmul(Z[end], Z[end], false, true), &ev, &EV);   // null(Z^T): eigenvalue-0 eigenvectors of Z Z^T
+            for (int q = 0; q < m - c; ++q)
+                for (int i = 0; i < m; ++i) N((end == 0 ? 0 : n - m) + i, end * c0 + q) = EV(i, q);
         }
         Mat V2 = N;
         if (!lu_solve(Md, V2)) {
@@ -817,16 +833,25 @@ static int fd_tables(const Spline& sp, const Quad& Q, int n, int p, double eps_p
 }
 
 int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
-    const int n_el = n - p + 2;
-    if (p < 1 || p > 5 || n_el <= p || n > 1024 || (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST)) {
-        set_error("tpcg_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024 and a known geometry");
+    const int k0 = geo.k0, k1 = geo.k1;
+    if (k0 < 0 || k0 > 1 || k1 < 0 || k1 > 1 || (k0 == 1 && k1 == 1)) {
+        set_error("tpcg_setup: boundary flags (k0, k1) must be (0,0), (0,1) or (1,0)");
+        return TPCG_E_INVALID;
+    }
+    const int n_el = n - p + 2 - k0 - k1;
+    if (p < 1 + (k0 | k1) || p > 5 || n_el <= p || n > 1024 ||
+        (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST)) {
+        set_error("tpcg_setup: need 1 <= p <= 5 (2 <= p with a Neumann end), n - p + 2 - k0 - k1 > p, n <= 1024 and "
+                  "a known geometry");
         return TPCG_E_INVALID;
     }
     const double eps_geo = geo.eps_geo > 0 ? geo.eps_geo : 1e-8;
     const double eps_prec = geo.eps_prec > 0 ? geo.eps_prec : 0.1;
     HostProblem& H = *out;
+    H.k0 = k0;
+    H.k1 = k1;
     Spline sp(p, n_el);
-    Quad Q = make_quad(sp);
+    Quad Q = make_quad(sp, k0, k1);
 
     // ---- coefficient samples on the Chebyshev grid
     Ten Tq[3][3], Tw;
@@ -841,7 +866,7 @@ int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
         for (int j = 0; j < NCHEB; ++j)
             for (int i = 0; i < NCHEB; ++i) {
                 double Qv[3][3], om;
-                coefficients(geo.kind, geo.amp, cheb_pt(i), cheb_pt(j), cheb_pt(k), Qv, &om);
+                coefficients(geo.kind, geo.amp, cheb_pt(i), cheb_pt(j), cheb_pt(k), Qv, &om, k0, k1);
                 for (int a = 0; a < 3; ++a)
                     for (int b = 0; b < 3; ++b) Tq[a][b].at(i, j, k) = Qv[a][b];
                 Tw.at(i, j, k) = om;
@@ -861,8 +886,9 @@ int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double 
                      HostProblem out[9]) {
     const int n_el = n - p + 2;
     if (p < 1 || p > 5 || n_el <= p || n > 1024 || (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST) ||
-        !(mu > 0) || !(lam >= 0)) {
-        set_error("tpcg_elast_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024, a known geometry, mu > 0, lambda >= 0");
+        !(mu > 0) || !(lam >= 0) || geo.k0 != 0 || geo.k1 != 0) {
+        set_error("tpcg_elast_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024, a known geometry, mu > 0, lambda >= 0 "
+                  "and Dirichlet faces");
         return TPCG_E_INVALID;
     }
     const double eps_geo = geo.eps_geo > 0 ? geo.eps_geo : 1e-8;

@@ -11,6 +11,7 @@ struct HostProblem {
     int R = 0;                       // Kronecker terms of A~
     int rf[3] = {0, 0, 0};           // rhs ranks
     int n1 = 0, n2 = 0, RP = 0;      // App. B splitting, exponential-sum length
+    int k0 = 0, k1 = 0;              // Neumann flags of the two ends (every direction)
     double lambda_min = 0, lambda_max = 0;
     std::vector<double> w;           // R weights
     std::vector<double> bands;       // [((j*3+t)*(2p+1)+d)*n + i] = K_t^j[i, i+d-p]

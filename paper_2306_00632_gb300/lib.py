@@ -44,7 +44,8 @@ class TuckerT(C.Structure):
 
 
 class Geometry(C.Structure):
-    _fields_ = [("kind", C.c_int), ("amp", C.c_double), ("eps_geo", C.c_double), ("eps_prec", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("amp", C.c_double), ("eps_geo", C.c_double), ("eps_prec", C.c_double),
+                ("k0", C.c_int), ("k1", C.c_int)]
 
 
 class ProblemArrays(C.Structure):
@@ -55,13 +56,14 @@ class ProblemArrays(C.Structure):
                 ("lam", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
                 ("w_rowptr", C.POINTER(C.c_int)), ("w_col", C.POINTER(C.c_int)), ("w_val", C.POINTER(C.c_double)),
                 ("v2u2", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
-                ("alpha", C.POINTER(C.c_double)), ("lambda_min", C.c_double)]
+                ("alpha", C.POINTER(C.c_double)), ("lambda_min", C.c_double), ("k0", C.c_int), ("k1", C.c_int)]
 
 
 class ProblemInfo(C.Structure):
     _fields_ = [("n", C.c_int), ("p", C.c_int), ("R", C.c_int), ("RP", C.c_int), ("n1", C.c_int),
                 ("n2", C.c_int), ("rf", C.c_int * 3), ("dtype", C.c_int), ("lambda_min", C.c_double),
-                ("lambda_max", C.c_double), ("MP", C.c_double), ("norm_f", C.c_double), ("w_nnz", C.c_int)]
+                ("lambda_max", C.c_double), ("MP", C.c_double), ("norm_f", C.c_double), ("w_nnz", C.c_int),
+                ("k0", C.c_int), ("k1", C.c_int)]
 
 
 class Params(C.Structure):

@@ -11,20 +11,21 @@ from oracle import fd, lowrank, tucker
 
 
 @functools.lru_cache(maxsize=None)
-def oracle_problem(kind: str, amp: float, n: int, p: int):
-    terms = lowrank.operator_terms(kind, amp, n, p)
-    f = lowrank.rhs_tucker(kind, amp, n, p)
-    P = fd.ApproxFD(n, p)
-    W, mu, _ = fd.sine_factorization(n, p)
-    n1, n2 = fd.split_dims(n - p + 2, p)
+def oracle_problem(kind: str, amp: float, n: int, p: int, bc=(0, 0)):
+    """Operator, rhs, preconditioner and its tables from the oracle; bc = (k0, k1) marks Neumann ends."""
+    terms = lowrank.operator_terms(kind, amp, n, p, bc=bc)
+    f = lowrank.rhs_tucker(kind, amp, n, p, bc=bc)
+    P = fd.ApproxFD(n, p, bc=bc)
+    W, mu, _ = fd.sine_factorization(n, p, bc)
+    n1, n2 = fd.split_dims(n - p + 2 - bc[0] - bc[1], p, bc)
     tables = {"lam": P.lam, "mu": mu, "W": W, "v2u2": P.U[:, n1:], "omega": P.omega, "alpha": P.alpha,
-              "lambda_min": P.lmin}
+              "lambda_min": P.lmin, "bc": bc}
     return terms, f, P, tables
 
 
-def gpu_problem(kind: str, amp: float, n: int, p: int, dtype=0):
+def gpu_problem(kind: str, amp: float, n: int, p: int, dtype=0, bc=(0, 0)):
     from paper_2306_00632_gb300 import api
-    terms, f, P, tables = oracle_problem(kind, amp, n, p)
+    terms, f, P, tables = oracle_problem(kind, amp, n, p, bc)
     return api.tpcg_problem_create(n, p, terms, f[0], f[1], tables, dtype=dtype)
 
 
