@@ -152,13 +152,16 @@ __global__ void __launch_bounds__(EIG_THREADS) jacobi_eig_kernel(RoundPlan* plan
     const int Mp = (M + 1) & ~1;
     const int half = Mp / 2;
     const int P = Mp - 1;
-    // rotate only when a_pq is above both the relative threshold and the absolute floor eps trace (entries
-    // below the floor are rounding noise of the Gram itself).  The relative threshold tau need not reach
+    // rotate only when a_pq is above the relative threshold and, in FP32, the absolute floor eps trace (entries
+    // below it are rounding noise of the Gram itself).  FP64 has no absolute floor: with one, the block of
+    // eigenvalues below eps trace stayed unrotated, its diagonal entries read as energies the truncation could
+    // not discard, and the iterates of Alg. 5 kept those directions (mode ranks 43 instead of 27-33 on a
+    // 48^3 problem).  The relative threshold tau need not reach
     // machine precision: once |a_pq| <= tau sqrt(a_pp a_qq) every diagonal entry is its eigenvalue to relative
     // accuracy ~tau^2, and the truncation rule only ever uses trace - sum(kept diagonal), which is the exact
     // discarded energy of the current orthonormal basis whatever the remaining off-diagonal mass.
     const T epsr = (T)jacobi_tau<T>();
-    const T epsa = (T)((sizeof(T) == 8 ? 2.2e-16 : 1.2e-7) * s_tr);
+    const T epsa = (T)((sizeof(T) == 8 ? 0.0 : 1.2e-7) * s_tr);
     const int nblk = half * (half + 1) / 2;   // 2 x 2 blocks (a <= b) of the pair partition
     // blocks of this thread (q = tid + j nt), decoded once when there are at most 4 per thread
     constexpr int NBREG = 4;   // 2 x 2 blocks per thread decoded once (enough up to M = 180 at 1024 threads)
@@ -404,7 +407,7 @@ __global__ void __cluster_dims__(CJ_C, 1, 1) __launch_bounds__(CJ_THREADS)
     }
     __syncthreads();
     const T epsr = (T)jacobi_tau<T>();
-    const T epsa = (T)((sizeof(T) == 8 ? 2.2e-16 : 1.2e-7) * s_tr);
+    const T epsa = (T)((sizeof(T) == 8 ? 0.0 : 1.2e-7) * s_tr);   // FP64: relative threshold only (see above)
     cluster.sync();   // every CTA initialised before any remote write
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (tid == 0) s_rot = 0;
