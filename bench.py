@@ -72,6 +72,10 @@ def parse():
     ap.add_argument("--serve", type=float, default=0.0,
                     help="instead of the batch benchmark: serve a Poisson-arrival stream at this rate (requests/s)")
     ap.add_argument("--requests", type=int, default=48, help="requests in the --serve stream")
+    ap.add_argument("--serve-nmax", type=int, default=128,
+                    help="largest Poisson n of the --serve stream (sizes 32, 64, 96, 128, 192, 256, 384 up to it)")
+    ap.add_argument("--serve-setup", action="store_true",
+                    help="--serve: build each uncached operator after its request arrives, inside its latency")
     ap.add_argument("--mix-caps", default="20,60", help="--mix: range of the rank caps (lo,hi)")
     ap.add_argument("--mix", type=int, default=0,
                     help="instead of the batch benchmark: this many independent solves of uneven n, p, rank cap and "
@@ -627,11 +631,12 @@ def run_serve(args):
     from paper_2306_00632_gb300 import lib, serve
     lib.load()
     arr = synth.poisson_arrivals(args.serve, args.requests, seed=SEED)
+    sizes = tuple(v for v in (32, 64, 96, 128, 192, 256, 384) if v <= max(args.serve_nmax, 32))
     reqs = []
     for i, t in enumerate(arr):
         sd = SEED + 1000 + i
         if i % 2 == 0:
-            n = (32, 64, 96, 128)[int(synth.unit_from_seed(sd, 2) * 4)]
+            n = sizes[int(synth.unit_from_seed(sd, 2) * len(sizes))]
             p = 2 + int(synth.unit_from_seed(sd, 3) * 2)
             reqs.append(serve.Request(lib.GEOM_TWIST, synth.amp_from_seed(sd), p, n, min(n, 96), tol=TOL,
                                       dtype=lib.MIXED, arrival=float(t)))
@@ -642,8 +647,13 @@ def run_serve(args):
                                       arrival=float(t), problem="elasticity", lame_lambda=1.0, lame_mu=mu,
                                       force=(0.0, 0.1, -1.0)))
     free, _ = torch.cuda.mem_get_info()
-    srv = serve.Server(int(free * 0.6), max_slots=32)
-    srv.run(reqs[:4])   # warm-up: operators cached, contexts and graphs exercised
+    srv = serve.Server(int(free * 0.6), max_slots=32, setup_in_latency=args.serve_setup)
+    if args.serve_setup:   # warm-up on descriptions outside the stream: its operators stay uncached
+        srv.run([serve.Request(lib.GEOM_CUBE, 0.0, 2, 24, 24, tol=TOL, dtype=lib.MIXED),
+                 serve.Request(lib.GEOM_CUBE, 0.0, 2, 16, 16, tol=TOL, dtype=lib.F64, problem="elasticity",
+                               lame_lambda=1.0, lame_mu=0.5, force=(0.0, 0.1, -1.0))])
+    else:
+        srv.run(reqs[:4])   # warm-up: operators cached, contexts and graphs exercised
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
@@ -653,8 +663,14 @@ def run_serve(args):
             "rate_hz": args.serve, "requests": len(res), "converged": ok,
             "latency_s": {"p50": lat["p50"], "p99": lat["p99"]},
             "solves_per_s": len(res) / max(max(r.finished for r in res), 1e-9), "wall_s": wall,
-            "mix": "50/50 Poisson (mixed form, n 32-128) / elasticity (FP64, n 16-32), seeded twisted annuli",
+            "mix": f"50/50 Poisson (mixed form, n {sizes[0]}-{sizes[-1]}, rank cap min(n, 96)) / elasticity "
+                   "(FP64, n 16-32), seeded twisted annuli",
+            "setup_in_latency": bool(args.serve_setup),
             "max_slots": 32}
+    if args.serve_setup:
+        st = sorted(r.setup_s for r in res)
+        line["operator_cache_hit_rate"] = sum(1 for r in res if r.cache_hit) / len(res)
+        line["setup_s"] = {"p50": st[len(st) // 2], "max": st[-1]}
     by = {}
     for r in res:
         k = r.request.problem

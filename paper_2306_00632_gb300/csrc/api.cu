@@ -592,8 +592,13 @@ extern "C" int tpcg_problem_create(const tpcg_problem_arrays* a, tpcg_problem* o
     f.core = pb->d_f_store[3];
     if ((s = dmalloc(&pb->d_f_store[4], TPCG_DESC_BYTES, nullptr))) return fail(s);
     f.desc = pb->d_f_store[4];
-    if ((s = set_plain(&f, pb->rf[0], pb->rf[1], pb->rf[2], 0))) return fail(s);
-    if (cudaDeviceSynchronize() != cudaSuccess) {
+    // the descriptor kernel runs on this thread's private stream and only that stream is waited for: a
+    // device-wide synchronisation would also wait for (and, while another thread captures a CUDA graph,
+    // invalidate the capture of) the solves running concurrently
+    cudaStream_t ps = nullptr;
+    if ((s = priv_stream(&ps))) return fail(s);
+    if ((s = set_plain(&f, pb->rf[0], pb->rf[1], pb->rf[2], ps))) return fail(s);
+    if (cudaStreamSynchronize(ps) != cudaSuccess) {
         set_error("tpcg_problem_create: device error");
         return fail(TPCG_E_CUDA);
     }

@@ -95,3 +95,22 @@ def test_poisson_and_elasticity_requests_share_the_device(mods):
                 assert rel(tucker.full((b.core[i], b.factors[i])), tucker.full((a.core[i], a.factors[i]))) < 1e-13
         else:
             assert rel(tucker.full((b.core, b.factors)), tucker.full((a.core, a.factors))) < 1e-13
+
+
+def test_setup_in_latency_builds_each_operator_once_and_matches(mods):
+    # operators built after their requests arrive: one build per description, the build time inside the latency
+    # of the requests that waited for it, and the same results as with operators built beforehand
+    lib, serve = mods
+    reqs = _requests(lib, serve, lib.MIXED)
+    free, _ = torch.cuda.mem_get_info()
+    ref = serve.Server(free // 4, max_slots=8, keep_solutions=True).run(reqs)
+    srv = serve.Server(free // 4, max_slots=8, keep_solutions=True, setup_in_latency=True)
+    res = srv.run(reqs)
+    assert len(srv._problems) == 5                       # five descriptions among the ten requests
+    for a, b in zip(ref, res):
+        assert a.request == b.request and a.status == b.status == 0
+        assert (a.iters, a.outer_iters, a.rank) == (b.iters, b.outer_iters, b.rank)
+        assert rel(tucker.full((b.core, b.factors)), tucker.full((a.core, a.factors))) < 1e-13
+        assert b.admitted >= b.request.arrival + b.setup_s - 1e-3
+    assert not res[0].cache_hit and res[0].setup_s > 0.0
+    assert sum(1 for r in res if not r.cache_hit) >= 5
