@@ -278,7 +278,8 @@ int tpcg_solve_batch(int count, const tpcg_problem* pbs, const tpcg_ctx* ctxs, c
 typedef struct tpcg_elast_s* tpcg_elast;
 
 /* Host FP64 setup of all nine blocks (force: 3 host doubles, the constant body force), then upload.
- * Homogeneous Dirichlet conditions on every face: geo->k0 and geo->k1 must be 0 (else TPCG_E_INVALID). */
+ * geo->k0 / geo->k1 = 1 make the faces eta_t = 0 / eta_t = 1 of every direction traction-free (the natural
+ * condition: their end functions stay in the space of every component), 0 clamps them; (1,1) is refused. */
 int tpcg_elast_setup(const tpcg_geometry* geo, int degree, int n, double lame_lambda, double lame_mu,
                      const double* force, int dtype, tpcg_elast* out);
 /* The same from caller tables: blocks[3 i + j] describes A_ij (its rhs fields give f_i; the preconditioner

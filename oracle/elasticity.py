@@ -17,8 +17,11 @@ A_ij is a Kronecker sum.  Block vectors are lists of three Tucker tensors; produ
 truncations act block-wise (Sec. 5.3).
 
 Readings:
-  * boundary conditions: homogeneous Dirichlet on every face for every component (the paper's column test
-    mixes Dirichlet and Neumann faces on a geometry it does not give);
+  * boundary conditions: homogeneous Dirichlet on every face for every component by default; with the Neumann
+    flags bc = (k0, k1) of the Poisson spaces (the same pair in every direction) the faces eta_t = 0 (k0 = 1)
+    or eta_t = 1 (k1 = 1) are traction-free for every component (the natural condition of the bilinear form:
+    their end functions stay in the space).  The paper's column test mixes Dirichlet and Neumann faces per
+    direction on a geometry it does not give;
   * body force: a constant vector f, so component i of the rhs is f_i times the Poisson load of f = 1;
   * preconditioner block i: the parametric-cube diagonal block mu (K M M + M K M + M M K) + (lambda + mu)
     (K in direction i), i.e. fast diagonalization with direction weights c_t = mu + (lambda + mu) delta_ti,
@@ -59,12 +62,12 @@ def coefficients(kind: str, amp: float, lam: float, mu: float, e1, e2, e3):
     return C
 
 
-def _terms_of_coefficient(Ckl, n: int, p: int, eps: float):
+def _terms_of_coefficient(Ckl, n: int, p: int, eps: float, bc=(0, 0)):
     """Kronecker terms of sum_{k,l} int Ckl[k][l](eta) d_k phi d_l psi (the Poisson construction)."""
-    n_el = n - p + 2
+    n_el = bspline.n_el_of(n, p, bc)
     xs, ws = bspline.quadrature(n_el, p)
-    B0 = bspline.dirichlet_basis(n_el, p, xs, 0)
-    B1 = bspline.dirichlet_basis(n_el, p, xs, 1)
+    B0 = bspline.bc_basis(n_el, p, xs, 0, bc)
+    B1 = bspline.bc_basis(n_el, p, xs, 1, bc)
     norms = np.array([[np.linalg.norm(Ckl[..., k, l]) for l in range(3)] for k in range(3)])
     scale = max(norms.max(), 1e-300)
     terms = []
@@ -93,17 +96,18 @@ def _terms_of_coefficient(Ckl, n: int, p: int, eps: float):
     return terms
 
 
-def operator_blocks(kind: str, amp: float, n: int, p: int, lam: float, mu: float, eps: float = 1e-8):
+def operator_blocks(kind: str, amp: float, n: int, p: int, lam: float, mu: float, eps: float = 1e-8,
+                    bc=(0, 0)):
     """blocks[i][j]: Kronecker terms of A_ij (component i of the test space, j of the trial space)."""
     xc = lowrank.cheb_points()
     e1, e2, e3 = np.meshgrid(xc, xc, xc, indexing="ij")
     C = coefficients(kind, amp, lam, mu, e1, e2, e3)
-    return [[_terms_of_coefficient(C[..., i, j, :, :], n, p, eps) for j in range(3)] for i in range(3)]
+    return [[_terms_of_coefficient(C[..., i, j, :, :], n, p, eps, bc) for j in range(3)] for i in range(3)]
 
 
-def rhs(kind: str, amp: float, n: int, p: int, force, eps: float = 1e-8):
+def rhs(kind: str, amp: float, n: int, p: int, force, eps: float = 1e-8, bc=(0, 0)):
     """Component i: f_i times the load of the unit body force, int det(J) psi (Tucker, App. A)."""
-    n_el = n - p + 2
+    n_el = bspline.n_el_of(n, p, bc)
     xc = lowrank.cheb_points()
     e1, e2, e3 = np.meshgrid(xc, xc, xc, indexing="ij")
     if kind == "cube":
@@ -112,7 +116,7 @@ def rhs(kind: str, amp: float, n: int, p: int, force, eps: float = 1e-8):
         om = np.linalg.det(geometry.twist_jacobian(e1, e2, e3, amp))
     core, U = lowrank.tucker_of_samples(om, eps)
     xs, ws = bspline.quadrature(n_el, p)
-    B0 = bspline.dirichlet_basis(n_el, p, xs, 0)
+    B0 = bspline.bc_basis(n_el, p, xs, 0, bc)
     F = [(B0 * ws) @ lowrank.cheb_eval(U[t], xs) for t in range(3)]
     return [(force[i] * core, [f.copy() for f in F]) for i in range(3)]
 
@@ -180,8 +184,9 @@ class BlockFD:
     """Block-diagonal P~^-1: block i is Alg. 4 for sum_t c_t (K in direction t) with the App. B eigenpairs.
     1 / sum_t c_t lam_t ~= (1/l_i) sum_j omega_j prod_t exp(-alpha_j c_t lam_t / l_i), l_i = (sum_t c_t) lam_min."""
 
-    def __init__(self, n: int, p: int, lam: float, mu: float, base: fd.ApproxFD | None = None):
-        self.P = base if base is not None else fd.ApproxFD(n, p)
+    def __init__(self, n: int, p: int, lam: float, mu: float, base: fd.ApproxFD | None = None, bc=(0, 0)):
+        self.P = base if base is not None else fd.ApproxFD(n, p, bc=bc)
+        self.bc = tuple(bc)
         self.c = direction_weights(lam, mu)
         self.lmin1 = float(self.P.lam.min())
         self.lmin = [sum(ci) * self.lmin1 for ci in self.c]
@@ -203,7 +208,7 @@ class BlockFD:
 
     def exact_block(self, i):
         """Dense inverse of the weighted FD block with exact eigenpairs (reference for tiny n)."""
-        lamx, U = fd.exact_eig(self.P.n, self.P.p)
+        lamx, U = fd.exact_eig(self.P.n, self.P.p, self.bc)
         c = self.c[i]
         D = c[0] * lamx[:, None, None] + c[1] * lamx[None, :, None] + c[2] * lamx[None, None, :]
         return U, D

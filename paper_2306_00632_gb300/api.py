@@ -435,8 +435,11 @@ class Elast:
             pass
 
 
-def tpcg_elast_setup(kind, amp, degree, n, lame_lambda, lame_mu, force, dtype=L.F64, eps_geo=0.0, eps_prec=0.0):
-    g = L.Geometry(kind, amp, eps_geo, eps_prec)
+def tpcg_elast_setup(kind, amp, degree, n, lame_lambda, lame_mu, force, dtype=L.F64, eps_geo=0.0, eps_prec=0.0,
+                     bc=(0, 0)):
+    """bc = (k0, k1): 1 makes the faces eta_t = 0 (k0) / eta_t = 1 (k1) of every direction traction-free,
+    0 clamps them."""
+    g = L.Geometry(kind, amp, eps_geo, eps_prec, int(bc[0]), int(bc[1]))
     f = (C.c_double * 3)(*[float(v) for v in force])
     h = C.c_void_p()
     check(L.load().tpcg_elast_setup(C.byref(g), degree, n, float(lame_lambda), float(lame_mu), f, dtype, C.byref(h)),

@@ -304,6 +304,7 @@ extern "C" int tpcg_elast_setup(const tpcg_geometry* geo, int degree, int n, dou
         a[q].w_rowptr = h.w_rowptr.data(); a[q].w_col = h.w_col.data(); a[q].w_val = h.w_val.data();
         a[q].v2u2 = h.v2u2.empty() ? nullptr : h.v2u2.data();
         a[q].omega = h.omega.data(); a[q].alpha = h.alpha.data(); a[q].lambda_min = h.lambda_min;
+        a[q].k0 = h.k0; a[q].k1 = h.k1;
     }
     return tpcg_elast_create(a, lame_lambda, lame_mu, out);
 }

@@ -884,17 +884,22 @@ int host_setup(const tpcg_geometry& geo, int p, int n, HostProblem* out) {
 // (force_i times the load of a unit body force, det J) and the shared App. B / Prop. 1 tables.
 int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double mu, const double force[3],
                      HostProblem out[9]) {
-    const int n_el = n - p + 2;
-    if (p < 1 || p > 5 || n_el <= p || n > 1024 || (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST) ||
-        !(mu > 0) || !(lam >= 0) || geo.k0 != 0 || geo.k1 != 0) {
-        set_error("tpcg_elast_setup: need 1 <= p <= 5, n - p + 2 > p, n <= 1024, a known geometry, mu > 0, lambda >= 0 "
-                  "and Dirichlet faces");
+    const int k0 = geo.k0, k1 = geo.k1;
+    if (k0 < 0 || k0 > 1 || k1 < 0 || k1 > 1 || (k0 == 1 && k1 == 1)) {
+        set_error("tpcg_elast_setup: boundary flags (k0, k1) must be (0,0), (0,1) or (1,0)");
+        return TPCG_E_INVALID;
+    }
+    const int n_el = n - p + 2 - k0 - k1;
+    if (p < 1 + (k0 | k1) || p > 5 || n_el <= p || n > 1024 ||
+        (geo.kind != TPCG_GEOM_CUBE && geo.kind != TPCG_GEOM_TWIST) || !(mu > 0) || !(lam >= 0)) {
+        set_error("tpcg_elast_setup: need 1 <= p <= 5 (2 <= p with a traction-free face), n - p + 2 - k0 - k1 > p, "
+                  "n <= 1024, a known geometry, mu > 0, lambda >= 0");
         return TPCG_E_INVALID;
     }
     const double eps_geo = geo.eps_geo > 0 ? geo.eps_geo : 1e-8;
     const double eps_prec = geo.eps_prec > 0 ? geo.eps_prec : 0.1;
     Spline sp(p, n_el);
-    Quad Q = make_quad(sp);
+    Quad Q = make_quad(sp, k0, k1);
     const size_t N3 = (size_t)NCHEB * NCHEB * NCHEB;
     std::vector<Ten> Tc(81);   // [((i*3 + j)*3 + k)*3 + l]
     for (Ten& T : Tc) {
@@ -913,6 +918,8 @@ int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double 
                 Tw.at(i3, j3, k3) = det;
             }
     HostProblem fdh;
+    fdh.k0 = k0;
+    fdh.k1 = k1;
     {
         const int st = fd_tables(sp, Q, n, p, eps_prec, fdh);
         if (st != TPCG_OK) return st;

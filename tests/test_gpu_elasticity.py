@@ -29,16 +29,16 @@ def api():
 
 
 @functools.lru_cache(maxsize=None)
-def _oracle(kind, amp, n, p):
-    blocks = elasticity.operator_blocks(kind, amp, n, p, LAM, MU)
-    f = elasticity.rhs(kind, amp, n, p, FORCE)
-    tables = oracle_problem("cube", 0.0, n, p)[3]
-    P = elasticity.BlockFD(n, p, LAM, MU, base=oracle_problem("cube", 0.0, n, p)[2])
+def _oracle(kind, amp, n, p, bc=(0, 0)):
+    blocks = elasticity.operator_blocks(kind, amp, n, p, LAM, MU, bc=bc)
+    f = elasticity.rhs(kind, amp, n, p, FORCE, bc=bc)
+    tables = oracle_problem("cube", 0.0, n, p, bc)[3]
+    P = elasticity.BlockFD(n, p, LAM, MU, base=oracle_problem("cube", 0.0, n, p, bc)[2], bc=bc)
     return blocks, f, tables, P
 
 
-def _gpu(api, kind, amp, n, p, dtype=0):
-    blocks, f, tables, _ = _oracle(kind, amp, n, p)
+def _gpu(api, kind, amp, n, p, dtype=0, bc=(0, 0)):
+    blocks, f, tables, _ = _oracle(kind, amp, n, p, bc)
     return api.tpcg_elast_create(n, p, blocks, f, tables, LAM, MU, dtype=dtype)
 
 
@@ -135,3 +135,31 @@ def test_library_setup_matches_oracle_operator(api):
     # approximation tolerance of the Chebyshev step, not to rounding
     assert _brel(got, _bfull(elasticity.bmatvec(blocks, X))) < 1e-7
     assert abs(e.norm_f - elasticity.bnorm(f)) <= 1e-7 * elasticity.bnorm(f)
+
+
+@pytest.mark.parametrize("bc", [(0, 1), (1, 0)])
+def test_traction_free_faces(api, bc):
+    # Neumann flags: the faces eta_t = 1 (or 0) traction-free for every component.  The library's own setup
+    # against the oracle's operator and load, and block TPCG on oracle-built blocks against the direct solve.
+    from paper_2306_00632_gb300 import lib
+    n, p, amp = 10, 3, 0.27
+    blocks, f, _, _ = _oracle("twist", amp, n, p, bc)
+    e = api.tpcg_elast_setup(lib.GEOM_TWIST, amp, p, n, LAM, MU, FORCE, bc=bc)
+    assert e.R == [len(blocks[i][j]) for i in range(3) for j in range(3)]
+    X = [synth.random_tucker((n, n, n), (2, 2, 2), seed=80 + i) for i in range(3)]
+    x = [api.Tucker.from_numpy(c, F) for c, F in X]
+    y = [api.Tucker(n, cap=1 + sum(e.R) * 2, core_cap=1) for _ in range(3)]
+    api.elast_apply(e, x, y)
+    got = [tucker.full(yi.to_numpy(others=x)) for yi in y]
+    assert _brel(got, _bfull(elasticity.bmatvec(blocks, X))) < 1e-7
+    assert abs(e.norm_f - elasticity.bnorm(f)) <= 1e-7 * elasticity.bnorm(f)
+    n, p, amp = 8, 2, 0.21
+    blocks, f, _, P = _oracle("twist", amp, n, p, bc)
+    eg = _gpu(api, "twist", amp, n, p, bc=bc)
+    st, Xg = _solve(api, eg, n, n, tol=1e-8, max_it=300)
+    assert st.status == 0 and st.true_rel_res <= 1e-8
+    A = elasticity.assemble(blocks)
+    fv = elasticity.bvec(f)
+    import scipy.sparse.linalg as spla
+    xd = spla.spsolve(A.tocsc(), fv)
+    assert rel(elasticity.bvec(Xg), xd) < 1e-6

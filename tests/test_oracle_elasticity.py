@@ -143,3 +143,87 @@ def test_block_tpcg_matches_direct_solve():
     assert np.linalg.norm(fv - A @ xv) <= 2e-8 * np.linalg.norm(fv)
     assert np.linalg.norm(xv - xd) <= 1e-6 * np.linalg.norm(xd)
     assert info["iters"] < 100
+
+
+# ------------------------------------------------------------------------------------ Neumann faces
+def _outer(vecs):
+    return np.einsum("i,j,k->ijk", *vecs)
+
+
+def _neumann_manufactured_load(n_el, p, a, bc=(0, 1)):
+    """Load of u_i = a_i S(x) S(y) S(z), S(t) = sin(pi t / 2), on the cube clamped at the faces eta_t = 0 and
+    loaded by the traction g = sigma(u) n on the faces eta_t = 1: the body term int f . v with
+    f = -mu Lap u - (lam + mu) grad div u, plus the face terms int g . v.  Closed-form derivatives of the
+    sines and 1-D Gauss quadrature only (independent of the oracle's coefficient code)."""
+    h = 0.5 * np.pi
+    xs, ws = bspline.quadrature(n_el, p)
+    B = bspline.bc_basis(n_el, p, xs, 0, bc)
+    Ls = (B * ws) @ np.sin(h * xs)
+    Lc = (B * ws) @ np.cos(h * xs)
+    e1 = bspline.bc_basis(n_el, p, np.array([1.0]), 0, bc)[:, 0]    # test functions at eta = 1
+    F = []
+    for j in range(3):
+        t = h * h * (4 * MU + LAM) * a[j] * _outer([Ls, Ls, Ls])
+        for i in range(3):
+            if i != j:
+                v = [Ls, Ls, Ls]
+                v[i], v[j] = Lc, Lc
+                t = t - h * h * (LAM + MU) * a[i] * _outer(v)
+        for d in range(3):   # face eta_d = 1, outward normal e_d; S(1) = 1, S'(1) = 0
+            if j == d:       # normal traction lam div u = lam h sum_{k != d} a_k C(x_k) S(x_m)
+                for k in range(3):
+                    if k != d:
+                        v = [Ls, Ls, Ls]
+                        v[d], v[k] = e1, Lc
+                        t = t + LAM * h * a[k] * _outer(v)
+            else:            # shear traction mu d_j u_d = mu h a_d C(x_j) S(x_m)
+                v = [Ls, Ls, Ls]
+                v[d], v[j] = e1, Lc
+                t = t + MU * h * a[d] * _outer(v)
+        F.append(t)
+    return F
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_elasticity_with_neumann_faces_converges_at_optimal_rate(p):
+    # Neumann flags (0, 1): clamped at eta_t = 0, traction data on eta_t = 1 (the natural condition the space
+    # carries); the Galerkin error of the manufactured solution falls as h^{p+1}
+    a = (1.0, -0.5, 0.25)
+    bc = (0, 1)
+    errs = []
+    for n_el in (4, 8):
+        n = n_el + p - 1
+        blocks = elasticity.operator_blocks("cube", 0.0, n, p, LAM, MU, bc=bc)
+        A = elasticity.assemble(blocks)
+        F = _neumann_manufactured_load(n_el, p, a, bc)
+        x = spla.spsolve(A.tocsc(), np.concatenate([tucker.vec(Fj) for Fj in F]))
+        xs, ws = bspline.quadrature(n_el, p)
+        B = bspline.bc_basis(n_el, p, xs, 0, bc)
+        s = np.sin(0.5 * np.pi * xs)
+        W = _outer([ws, ws, ws])
+        e2 = 0.0
+        for j in range(3):
+            X = tucker.unvec(x[j * n ** 3:(j + 1) * n ** 3], (n, n, n))
+            uh = tucker.contract(X, [B.T, B.T, B.T])
+            e2 += np.sum(W * (uh - a[j] * _outer([s, s, s])) ** 2)
+        errs.append(np.sqrt(e2))
+    assert np.log2(errs[0] / errs[1]) > p + 1 - 0.35
+
+
+@pytest.mark.parametrize("bc", [(0, 1), (1, 0)])
+def test_neumann_faces_block_matrix_spd_and_tpcg_matches_direct_solve(bc):
+    n, p, amp = 8, 2, 0.21
+    blocks = elasticity.operator_blocks("twist", amp, n, p, LAM, MU, bc=bc)
+    A = elasticity.assemble(blocks)
+    D = A.toarray()
+    assert np.abs(D - D.T).max() <= 1e-9 * np.abs(D).max()
+    assert np.linalg.eigvalsh(0.5 * (D + D.T)).min() > 0.0     # clamped faces remove the rigid motions
+    f = elasticity.rhs("twist", amp, n, p, (0.1, 0.2, -1.0), bc=bc)
+    P = elasticity.BlockFD(n, p, LAM, MU, bc=bc)
+    x, info = elasticity.tpcg(blocks, f, P.apply, otp.Params(tol=1e-8))
+    fv = elasticity.bvec(f)
+    xd = spla.spsolve(A.tocsc(), fv)
+    xv = elasticity.bvec(x)
+    assert np.linalg.norm(fv - A @ xv) <= 2e-8 * np.linalg.norm(fv)
+    assert np.linalg.norm(xv - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert info["iters"] < 150    # 114 with traction-free faces at eta = 1: the block-diagonal FD sees no coupling
