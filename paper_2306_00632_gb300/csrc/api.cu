@@ -784,7 +784,25 @@ extern "C" int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* e
         return TPCG_E_INVALID;
     }
     return by_dtype(c->dtype, [&](auto z) {
-        return round_impl<decltype(z)>(c, y, eps, eps_dev, rank_cap, info_dev, S(stream));
+        using T = decltype(z);
+        const int rule = round_rule();
+        if constexpr (sizeof(T) == 8) {
+            if (rule == 2 && !eps_dev && eps < EPS_RESOLVED_HOST && c->max_cols >= 3 * c->rank_cap) {
+                TPCG_TRY(ensure_tensors(c, 3));
+                const int rc = (rank_cap > 0 && rank_cap < c->rank_cap) ? rank_cap : c->rank_cap;
+                TPCG_TRY(round_resolved(c, y, &c->tens[0], eps, nullptr, rc, c->scal + 143, &c->tens[1],
+                                        &c->tens[2], S(stream)));
+                int r3[3] = {0, 0, 0}, nb = 0;
+                TPCG_TRY(tucker_get_ranks(&c->tens[0], r3, &nb, S(stream)));
+                if (r3[0] > y->cap || r3[1] > y->cap || r3[2] > y->cap ||
+                    (long long)r3[0] * r3[1] * r3[2] > y->core_cap) {
+                    set_error("tucker_round: the resolved result does not fit the tensor's capacity");
+                    return TPCG_E_INVALID;
+                }
+                return copy_tensor_impl<double>(&c->tens[0], y, c->n, y->cap, S(stream));
+            }
+        }
+        return round_impl<T>(c, y, eps, eps_dev, rank_cap, info_dev, S(stream), rule == 2 ? -1 : rule);
     });
 }
 
@@ -879,7 +897,7 @@ template <typename T>
 static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucker_t* xout, tpcg_stats* st,
                       cudaStream_t s, const tucker_t* rhs = nullptr, int tbase = 0) {
     if (!rhs) rhs = &pb->f;
-    TPCG_TRY(ensure_tensors(c, std::max(10, tbase + 7)));
+    TPCG_TRY(ensure_tensors(c, std::max(10, tbase + 9)));
     const int rc = (prm->rank_cap > 0 && prm->rank_cap < c->rank_cap) ? prm->rank_cap : c->rank_cap;
     double* sc = c->scal;
     double* dprm = c->scal + 100;
@@ -898,6 +916,8 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     tucker_t* q = &c->tens[tbase + 4];
     tucker_t* big = &c->tens[tbase + 5];
     tucker_t* big2 = &c->tens[tbase + 6];
+    tucker_t* rsE = &c->tens[tbase + 7];   // scratch of the resolved rule
+    tucker_t* rsF = &c->tens[tbase + 8];
     double* eta = sc + S_ETA;
     // the FP64 rule's strict mode (reading R23) serves solves whose tolerance is below what the Gram resolves;
     // at tol >= 1e-8 Alg. 2's tolerance still falls to eps_min (about tol ||f~|| / 10), where strict mode would
@@ -926,6 +946,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
     int k = 0;
     int status = TPCG_OK;
     int trials_total = 0;
+    double eps_now = prm->eps0;   // Alg. 2 tolerance on the host (fetched with each trial decision)
     const char* tr = getenv("TPCG_TRACE");
     const bool trace = tr && tr[0] == '1';
     c->hist.clear();
@@ -973,13 +994,23 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
         TPCG_TRY(dot_cached<T>(c, p, p, sc + S_PP, s));
         TPCG_TRY(axpby_impl<T>(1.0, nullptr, x, 0.0, sc + S_OMEGA, p, big, nullptr, s));
         for (int trial = 0;; ++trial) {
-            TPCG_TRY(copy_tensor_impl<T>(big, big2, c->n, c->max_cols, s));
-            TPCG_TRY(round_cached<T>(c, big2, sc + S_EPS, rc, s, strict));
+            // below 1e-7 one FP64 Gram pass cannot resolve the budget: the resolved rule (two passes)
+            bool resolved = false;
+            if constexpr (sizeof(T) == 8)
+                resolved = strict == 0 && resolved_kind() == 1 && eps_now < EPS_RESOLVED_HOST &&
+                           c->max_cols >= 3 * rc;
+            if (resolved) {
+                if constexpr (sizeof(T) == 8)
+                    TPCG_TRY(round_resolved(c, big, big2, 0.0, sc + S_EPS, rc, sc + S_ZN2, rsE, rsF, s));
+            } else {
+                TPCG_TRY(copy_tensor_impl<T>(big, big2, c->n, c->max_cols, s));
+                TPCG_TRY(round_cached<T>(c, big2, sc + S_EPS, rc, s, strict));
+            }
             TPCG_TRY(dot_cached<T>(c, p, big2, sc + S_PXN, s));
             launch_scalar(OP_DT, sc, dprm, s);
             ++trials_total;
             double done;
-            TPCG_TRY(fetch(c, s, {{&done, sc + S_DONE, sizeof(double)}}));
+            TPCG_TRY(fetch(c, s, {{&done, sc + S_DONE, sizeof(double)}, {&eps_now, sc + S_EPS, sizeof(double)}}));
             if (done != 0.0 || trial > 64) break;
         }
         std::swap(x, big2);
@@ -1116,10 +1147,20 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
         xeps_kernel<<<1, 1, 0, s>>>(dd, xx, prm->refine_keep, xeps);
         TPCG_CHECK_LAUNCH();
         TPCG_TRY(axpby_impl<double>(1.0, nullptr, xacc, 1.0, nullptr, dco, xsum, nullptr, s));
-        // keep ||d|| to relative accuracy refine_keep: its FP32 rounding noise, at the FP64 Gram's resolution, is
-        // meant to be dropped (no strict rule)
-        TPCG_TRY(round_impl<double>(c, xsum, 0.0, xeps, rc, nullptr, s, 0));
-        std::swap(xacc, xsum);
+        // keep ||d|| to relative accuracy refine_keep: its FP32 rounding noise is meant to be dropped (no strict
+        // rule).  Once keep ||d|| / ||x + d|| is below what one FP64 Gram resolves, the resolved rule keeps d to
+        // that accuracy instead of losing it in the Gram's rounding
+        double dx[2];
+        TPCG_TRY(fetch(c, s, {{dx, dd, 2 * sizeof(double)}}));
+        const double d2 = std::max(dx[0], 0.0), x2 = std::max(dx[1], 0.0);
+        const double xeps_host = d2 + x2 > 0.0 ? prm->refine_keep * sqrt(d2 / (d2 + x2)) : 0.0;
+        if (resolved_kind() == 1 && xeps_host < EPS_RESOLVED_HOST && c->max_cols >= 3 * rc) {
+            TPCG_TRY(round_resolved(c, xsum, big, 0.0, xeps, rc, c->scal + 143, &c->tens[4], &c->tens[5], s));
+            std::swap(xacc, big);
+        } else {
+            TPCG_TRY(round_impl<double>(c, xsum, 0.0, xeps, rc, nullptr, s, 0));
+            std::swap(xacc, xsum);
+        }
     }
     TPCG_TRY(copy_tensor_impl<double>(xacc, xout, c->n, xout->cap, s));
     int rk[3] = {0, 0, 0}, nb = 0;

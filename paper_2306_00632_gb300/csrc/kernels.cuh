@@ -15,11 +15,18 @@ int round_impl(tpcg_ctx c, tucker_t* y, double eps, const double* eps_dev, int c
 // round_impl(c, y, 0, eps_dev, cap) replayed from a per-context CUDA graph (captured on first use)
 template <typename T>
 int round_cached(tpcg_ctx c, tucker_t* y, const double* eps_dev, int cap, cudaStream_t st, int strict_mode = -1);
+// FP64 Alg. 1 for eps below what one Gram resolves (two passes: the resolved part, then the remainder with the
+// absolute budget); y unchanged, result in out, E and F scratch; norm2_slot: one device double of scratch
+int round_resolved(tpcg_ctx c, const tucker_t* y, tucker_t* out, double eps, const double* eps_dev, int cap,
+                   double* norm2_slot, tucker_t* E, tucker_t* F, cudaStream_t st);
 int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, double eps, const double* eps_dev, int cap,
                 double abs_tol, double* info_dev, cudaStream_t st);
 // whether a context of this size, rank cap and dtype reduces its large Grams by Rayleigh-Ritz
 int rr_kind();      // TPCG_OPT_RR
 int gram_min_k();   // TPCG_OPT_GRAM_MIN_K
+int round_rule();   // TPCG_OPT_ROUND_RULE: rule of tucker_round (-1 automatic, 0 plain, 1 strict, 2 resolved)
+int resolved_kind();   // TPCG_OPT_RESOLVED: FP64 solves truncate x with round_resolved below its threshold
+constexpr double EPS_RESOLVED_HOST = 1e-7;   // the tolerance below which one FP64 Gram pass is not trusted
 // FP32: every context with n > RR_L (the one-CTA FP32 Jacobi for larger Grams keeps its diagonal by rotation
 // updates, whose drift spoils the trace-minus-kept rule); FP64: n > 256 (beyond the cluster eigensolver) with a
 // rank cap that leaves the basis room
@@ -82,7 +89,7 @@ int set_zero(tucker_t* t, cudaStream_t st);
 // ---- Alg. 5 scalars: slots of ctx->scal (device doubles), parameters at scal + 100, update ops
 enum {
     S_NF = 0, S_NR, S_ETA, S_RP, S_XI, S_OMEGA, S_EPS, S_EPSMIN, S_PXK, S_PXN, S_PP, S_V, S_DONE, S_ZQ, S_BETA,
-    S_STOP, S_RR, S_BAD, S_TRIALS, S_COUNT
+    S_STOP, S_RR, S_BAD, S_TRIALS, S_ZN2, S_COUNT
 };
 enum { P_TOL = 0, P_EPS0, P_EPSMIN, P_ALPHA, P_DELTA, P_BT, P_COUNT };
 enum { OP_INIT = 0, OP_OMEGA, OP_DT, OP_RES, OP_BETA, OP_XI };

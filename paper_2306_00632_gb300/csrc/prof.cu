@@ -142,6 +142,10 @@ static std::atomic<int> g_gemm_kind{2};
 int gemm_kind() { return g_gemm_kind.load(std::memory_order_relaxed); }
 static std::atomic<int> g_gram_min_k{0};
 int gram_min_k() { return g_gram_min_k.load(std::memory_order_relaxed); }
+static std::atomic<int> g_round_rule{-1};
+int round_rule() { return g_round_rule.load(std::memory_order_relaxed); }
+static std::atomic<int> g_resolved{1};
+int resolved_kind() { return g_resolved.load(std::memory_order_relaxed); }
 }  // namespace tpcg
 
 extern "C" int tpcg_set_option(int key, long long value) {
@@ -171,6 +175,14 @@ extern "C" int tpcg_set_option(int key, long long value) {
     }
     if (key == TPCG_OPT_GEMM_KIND && value >= 0 && value <= 2) {
         tpcg::g_gemm_kind.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_RESOLVED && (value == 0 || value == 1)) {
+        tpcg::g_resolved.store((int)value);
+        return TPCG_OK;
+    }
+    if (key == TPCG_OPT_ROUND_RULE && value >= -1 && value <= 2) {
+        tpcg::g_round_rule.store((int)value);
         return TPCG_OK;
     }
     if (key == TPCG_OPT_GRAM_MIN_K && value >= 0 && value <= (1 << 24)) {

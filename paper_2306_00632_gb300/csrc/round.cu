@@ -789,6 +789,44 @@ int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, doub
     return TPCG_OK;
 }
 
+// Alg. 1 at tolerances below what one FP64 Gram resolves.  A mode Gram carries rounding errors of about
+// eps_machine ||Z||^2, so for eps below ~1e-7 its smallest eigenvalues (the energies the budget
+// eps^2 ||Z||^2 / 3 is about) are noise: a single pass then both keeps noise directions and may drop more than
+// the budget.  Two passes resolve them:
+//   A. Y_A = T(Y, EPS_RESOLVED): the part the Gram resolves (relative error <= EPS_RESOLVED);
+//   B. E = Y - Y_A, rounded with the absolute budget (eps ||Y||)^2: E's own Grams resolve energies relative to
+//      ||E||^2 <= EPS_RESOLVED^2 ||Y||^2, far below the budget;
+//   Y~ = Y_A + T(E): ||Y - Y~|| = ||E - T(E)|| <= eps ||Y||, merged losslessly (QR of the joined factors, strict
+//   rule at eps 0, then the rank cap).
+// y is left unchanged; the result is written to out; E and F are scratch tensors of the context's capacity.
+constexpr double EPS_RESOLVED = EPS_RESOLVED_HOST;
+
+__global__ void save_norm2_kernel(const RoundPlan* __restrict__ plan, double* out) { *out = plan->norm2; }
+__global__ void set_abs_rel_kernel(RoundPlan* plan, const double* __restrict__ eps_dev, double eps_host,
+                                   const double* __restrict__ norm2) {
+    const double e = eps_dev ? *eps_dev : eps_host;
+    plan->abs2 = e * e * (*norm2);
+}
+
+int round_resolved(tpcg_ctx c, const tucker_t* y, tucker_t* out, double eps, const double* eps_dev, int cap,
+                   double* norm2_slot, tucker_t* E, tucker_t* F, cudaStream_t st) {
+    const int rc = (cap > 0 && cap < c->rank_cap) ? cap : c->rank_cap;
+    TPCG_TRY(copy_tensor_impl<double>(y, out, c->n, out->cap, st));
+    TPCG_TRY(round_impl<double>(c, out, EPS_RESOLVED, nullptr, rc, nullptr, st, 0));                  // A
+    save_norm2_kernel<<<1, 1, 0, st>>>(c->plan, norm2_slot);                                           // ||Y||^2
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY(axpby_impl<double>(1.0, nullptr, y, -1.0, nullptr, out, E, nullptr, st));                  // E = Y - Y_A
+    prof_begin(PK_ROUND, st);
+    TPCG_TRY(round_stage12<double>(c, E, 0.0, nullptr, rc, st, 0));                                    // B
+    set_abs_rel_kernel<<<1, 1, 0, st>>>(c->plan, eps_dev, eps, norm2_slot);
+    TPCG_CHECK_LAUNCH();
+    TPCG_TRY(round_stage34<double>(c, E, nullptr, st));
+    prof_end(PK_ROUND, st);
+    TPCG_TRY(axpby_impl<double>(1.0, nullptr, out, 1.0, nullptr, E, F, nullptr, st));                   // Y_A + T(E)
+    TPCG_TRY(round_impl<double>(c, F, 0.0, nullptr, rc, nullptr, st, 1));                              // lossless
+    return copy_tensor_impl<double>(F, out, c->n, out->cap, st);
+}
+
 // ||Z||^2 of the Z formed by round_stage12 (deterministic single-CTA reduction)
 template <typename T>
 __global__ void znorm2_kernel(const RoundPlan* __restrict__ plan, const T* __restrict__ Z, double* out) {

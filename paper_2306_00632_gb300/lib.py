@@ -34,6 +34,7 @@ SYMBOLS = [
 PROF_KINDS = {"zgemm": 0, "zblk": 1, "gram": 2, "eig": 3, "proj": 4, "qr": 5, "apply": 6, "fd": 7, "dot": 8,
               "round": 9}
 OPT_GEMM_CTAS_PER_SM, OPT_EXPSUM_BEST, OPT_EIG, OPT_DST, OPT_TC, OPT_RR, OPT_GRAM_MIN_K, OPT_GEMM_KIND = 1, 2, 3, 4, 5, 6, 7, 8   # tpcg_set_option keys
+OPT_ROUND_RULE, OPT_RESOLVED = 9, 10
 HIST_COLS = 8   # TPCG_HIST_COLS: columns of a tpcg_ctx_history row
 PROF_SWEEPS = 11   # one-CTA Jacobi: (sweeps, Grams) in the (flops, bytes) fields of this kind
 
