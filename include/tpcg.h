@@ -343,13 +343,13 @@ void tpcg_elast_destroy(tpcg_elast e);
 /*   TPCG_OPT_ROUND_RULE: the FP64 truncation rule of tucker_round (Alg. 1 step 3 on mode Grams): -1 (default)
  *   automatic, strict below eps = 1e-7 (every discarded Gram eigenvalue charged its rounding uncertainty
  *   4 eps_machine trace, so nothing the Gram cannot resolve is dropped); 0 plain (clamped eigenvalues as they
- *   are); 1 strict; 2 resolved below eps = 1e-7 (two passes: the part one Gram resolves, rounded at 1e-7, then
+ *   are); 1 strict; 2 resolved below eps = 1e-8 (two passes: the part one Gram resolves, rounded at 1e-7, then
  *   the remainder rounded with the absolute budget eps ||y||, whose own Grams resolve it; the two merged
  *   losslessly), which meets ||y - y~|| <= eps ||y|| with ranks close to those of an SVD.  tpcg_solve chooses
  *   its own rule. */
 #define TPCG_OPT_ROUND_RULE 9
 /*   TPCG_OPT_RESOLVED: 1 (default) FP64 solves (the FP64 form's Alg. 2 truncations of x, the mixed form's
- *   correction update of x) take the resolved rule whenever their tolerance is below 1e-7 and the context holds
+ *   correction update of x) take the resolved rule whenever their tolerance is below 1e-8 and the context holds
  *   3 rank_cap columns; 0 one Gram pass with the plain rule. */
 #define TPCG_OPT_RESOLVED 10
 int tpcg_set_option(int key, long long value);

@@ -787,7 +787,7 @@ extern "C" int tucker_round(tpcg_ctx c, tucker_t* y, double eps, const double* e
         using T = decltype(z);
         const int rule = round_rule();
         if constexpr (sizeof(T) == 8) {
-            if (rule == 2 && !eps_dev && eps < EPS_RESOLVED_HOST && c->max_cols >= 3 * c->rank_cap) {
+            if (rule == 2 && !eps_dev && eps < RESOLVE_BELOW && c->max_cols >= 3 * c->rank_cap) {
                 TPCG_TRY(ensure_tensors(c, 3));
                 const int rc = (rank_cap > 0 && rank_cap < c->rank_cap) ? rank_cap : c->rank_cap;
                 TPCG_TRY(round_resolved(c, y, &c->tens[0], eps, nullptr, rc, c->scal + 143, &c->tens[1],
@@ -997,7 +997,7 @@ static int solve_impl(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tucke
             // below 1e-7 one FP64 Gram pass cannot resolve the budget: the resolved rule (two passes)
             bool resolved = false;
             if constexpr (sizeof(T) == 8)
-                resolved = strict == 0 && resolved_kind() == 1 && eps_now < EPS_RESOLVED_HOST &&
+                resolved = strict == 0 && resolved_kind() == 1 && eps_now < RESOLVE_BELOW &&
                            c->max_cols >= 3 * rc;
             if (resolved) {
                 if constexpr (sizeof(T) == 8)
@@ -1154,7 +1154,7 @@ static int solve_mixed(tpcg_problem pb, tpcg_ctx c, const tpcg_params* prm, tuck
         TPCG_TRY(fetch(c, s, {{dx, dd, 2 * sizeof(double)}}));
         const double d2 = std::max(dx[0], 0.0), x2 = std::max(dx[1], 0.0);
         const double xeps_host = d2 + x2 > 0.0 ? prm->refine_keep * sqrt(d2 / (d2 + x2)) : 0.0;
-        if (resolved_kind() == 1 && xeps_host < EPS_RESOLVED_HOST && c->max_cols >= 3 * rc) {
+        if (resolved_kind() == 1 && xeps_host < RESOLVE_BELOW && c->max_cols >= 3 * rc) {
             TPCG_TRY(round_resolved(c, xsum, big, 0.0, xeps, rc, c->scal + 143, &c->tens[4], &c->tens[5], s));
             std::swap(xacc, big);
         } else {

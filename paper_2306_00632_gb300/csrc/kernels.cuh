@@ -26,7 +26,11 @@ int rr_kind();      // TPCG_OPT_RR
 int gram_min_k();   // TPCG_OPT_GRAM_MIN_K
 int round_rule();   // TPCG_OPT_ROUND_RULE: rule of tucker_round (-1 automatic, 0 plain, 1 strict, 2 resolved)
 int resolved_kind();   // TPCG_OPT_RESOLVED: FP64 solves truncate x with round_resolved below its threshold
-constexpr double EPS_RESOLVED_HOST = 1e-7;   // the tolerance below which one FP64 Gram pass is not trusted
+// The first pass of round_resolved rounds at EPS_RESOLVED_PASS, which one FP64 Gram pass resolves; solves take the
+// resolved rule below RESOLVE_BELOW (one pass met the bound at 1e-7 on Alg. 5 iterates and broke it, 1.24 eps,
+// at 6e-9)
+constexpr double EPS_RESOLVED_PASS = 1e-7;
+constexpr double RESOLVE_BELOW = 1e-8;
 // FP32: every context with n > RR_L (the one-CTA FP32 Jacobi for larger Grams keeps its diagonal by rotation
 // updates, whose drift spoils the trace-minus-kept rule); FP64: n > 256 (beyond the cluster eigensolver) with a
 // rank cap that leaves the basis room

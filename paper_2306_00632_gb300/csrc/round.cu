@@ -799,7 +799,7 @@ int round_mixed(tpcg_ctx c64, tpcg_ctx c32, tucker_t* y64, tucker_t* out32, doub
 //   Y~ = Y_A + T(E): ||Y - Y~|| = ||E - T(E)|| <= eps ||Y||, merged losslessly (QR of the joined factors, strict
 //   rule at eps 0, then the rank cap).
 // y is left unchanged; the result is written to out; E and F are scratch tensors of the context's capacity.
-constexpr double EPS_RESOLVED = EPS_RESOLVED_HOST;
+constexpr double EPS_RESOLVED = EPS_RESOLVED_PASS;
 
 __global__ void save_norm2_kernel(const RoundPlan* __restrict__ plan, double* out) { *out = plan->norm2; }
 __global__ void set_abs_rel_kernel(RoundPlan* plan, const double* __restrict__ eps_dev, double eps_host,
