@@ -175,3 +175,20 @@ def test_setup_refuses_neumann_everywhere(api):
     from paper_2306_00632_gb300 import lib
     with pytest.raises(RuntimeError):
         api.tpcg_setup(lib.GEOM_CUBE, 0.0, 3, 20, lib.F64, bc=(1, 1))
+
+
+def test_fp64_and_mixed_converge_at_n48_with_neumann_faces(api):
+    # at n = 48 the late Alg. 2 tolerances (about 6e-9) are below what one FP64 mode Gram resolves; with the
+    # resolved truncation the FP64 form takes the oracle's 29 iterations (a single Gram pass stalled at 1.4e-6)
+    from paper_2306_00632_gb300 import lib
+    n, p, bc = 48, 3, (0, 1)
+    amp = synth.amp_from_seed(9)
+    for dt, rc in ((lib.F64, 40), (lib.MIXED, 48)):
+        pb = api.tpcg_setup(lib.GEOM_TWIST, amp, p, n, dt, bc=bc)
+        ctx = api.Ctx(n, api.max_cols_for(pb.info, rc, dt), rc, dt)
+        x = api.Tucker(n, cap=rc, core_cap=rc ** 3, dtype=dt)
+        st = api.tpcg_solve(pb, ctx, x, tol=1e-6, rank_cap=rc, max_it=120)
+        torch.cuda.synchronize()
+        assert st.status == 0 and st.true_rel_res <= 1e-6, (dt, st.status, st.true_rel_res)
+        if dt == lib.F64:
+            assert st.iters <= 32
