@@ -183,29 +183,30 @@ def oracle_iterations(max_it: int, setup=None):
     return t0, [r["t"] for r in rec], info
 
 
-def oracle_sample(sample_iters=20):
-    """Time the first `sample_iters` iterations of the oracle's Alg. 5 on the same workload (setup excluded)
-    and scale to solves/sec with the oracle's own iteration count to convergence (stored)."""
+def oracle_sample():
+    """Time one whole solve of the oracle's Alg. 5 on the same workload (its stored iteration count to
+    convergence, setup excluded): solves/sec from the time per iteration over all of them."""
     iters = oracle_reference()["iters"]
-    t0, stamps, info = oracle_iterations(sample_iters)
+    t0, stamps, info = oracle_iterations(iters)
     dt = stamps[-1] - t0
     per_iter = dt / max(len(stamps), 1)
     return {"value": 1.0 / (per_iter * iters), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"the first {len(stamps)} TPCG iterations of the {N_DOF}^3 p={DEGREE} twisted-annulus solve "
-                      f"in {dt:.1f}s (setup excluded), scaled to the oracle's {iters}-iteration solve"}
+            "sample": f"{len(stamps)} TPCG iterations of the {N_DOF}^3 p={DEGREE} twisted-annulus solve (the "
+                      f"oracle's whole {iters}-iteration solve) in {dt:.1f}s, setup excluded"}
 
 
 def run_reference(args):
     """The oracle on the host cores: Alg. 5 runs on the workload timed in steps of CHUNK consecutive
-    iterations (a run that converges is restarted until K steps are timed; W untimed warm-up iterations
-    first).  value = 1 / (mean time per iteration x the oracle's iteration count to convergence);
-    ms_per_step is the mean measured time of a step."""
+    iterations, CHUNK chosen so that the K steps cover at least one whole solve (the iterates' ranks grow along
+    a solve, so early iterations alone would flatter the CPU); a run that converges is restarted until K steps
+    are timed; W untimed warm-up iterations first.  value = 1 / (mean time per iteration x the oracle's
+    iteration count to convergence); ms_per_step is the mean measured time of a step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    CHUNK = 2
     K = max(args.steps, 1)
     iters = oracle_reference()["iters"]
+    CHUNK = max(2, -(-iters // K))
     setup = _oracle_setup()
     if args.warmup > 0:
         oracle_iterations(args.warmup, setup)
