@@ -139,6 +139,13 @@ int tpcg_problem_get_info(tpcg_problem pb, tpcg_problem_info* out);
  * sized from tpcg_problem_get_info; any pointer may be NULL to skip it).  f_U[t] gets n x rf[t]. */
 int tpcg_problem_export(tpcg_problem pb, double* w, double* bands, double* f_core, double* f_U0, double* f_U1,
                         double* f_U2, double* lam, double* mu, double* v2u2, double* omega, double* alpha);
+/* Host-only form of tpcg_setup: the same FP64 setup (App. A, App. B, Prop. 1), its tables copied into caller-owned
+ * host buffers laid out as in tpcg_problem_arrays and tpcg_problem_export, without any GPU call.  info receives
+ * the sizes (dtype and norm_f are 0); any buffer may be NULL (skipped), so a first call with NULL buffers returns
+ * the sizes.  f_Ut: n x rf[t]; w_rowptr n + 1; w_col, w_val w_nnz.  Errors as tpcg_setup. */
+int tpcg_setup_host(const tpcg_geometry* geo, int degree, int n, tpcg_problem_info* info, double* w, double* bands,
+                    double* f_core, double* f_U0, double* f_U1, double* f_U2, double* lam, double* mu, double* v2u2,
+                    double* omega, double* alpha, int* w_rowptr, int* w_col, double* w_val);
 /* W of the sine factorisation in CSR (rowptr n+1, col/val w_nnz); NULL pointers are skipped. */
 int tpcg_problem_export_w(tpcg_problem pb, int* rowptr, int* col, double* val);
 void tpcg_problem_destroy(tpcg_problem pb);

@@ -338,6 +338,37 @@ def max_cols_for(info, rank_cap: int, dtype: int) -> int:
     return max(info.R * rank_cap + rhs, info.RP * rank_cap, 2 * rank_cap)
 
 
+def setup_host(kind: int, amp: float, degree: int, n: int, eps_geo=0.0, eps_prec=0.0, bc=(0, 0)):
+    """tpcg_setup_host: the library's FP64 setup tables on the host (no GPU call), as numpy arrays in the
+    layout of tpcg_problem_arrays: w, bands (R, 3, 2p+1, n), f_core (rf, Fortran order), f_U[t] (n x rf_t),
+    lam, mu, v2u2 (n x n2), omega, alpha, W in CSR (w_rowptr, w_col, w_val), and the info struct."""
+    g = L.Geometry(kind, amp, eps_geo, eps_prec, int(bc[0]), int(bc[1]))
+    info = L.ProblemInfo()
+    lib = L.load()
+    nul = C.POINTER(C.c_double)()
+    inul = C.POINTER(C.c_int)()
+    check(lib.tpcg_setup_host(C.byref(g), degree, n, C.byref(info), *([nul] * 11), inul, inul, nul),
+          "tpcg_setup_host")
+    p, R, rf, n1, n2 = degree, info.R, tuple(info.rf), info.n1, info.n2
+    out = {"w": np.zeros(R), "bands": np.zeros(R * 3 * (2 * p + 1) * n), "f_core": np.zeros(int(np.prod(rf))),
+           "f_U0": np.zeros(n * rf[0]), "f_U1": np.zeros(n * rf[1]), "f_U2": np.zeros(n * rf[2]), "lam": np.zeros(n),
+           "mu": np.zeros(n1), "v2u2": np.zeros(max(n * n2, 1)), "omega": np.zeros(info.RP),
+           "alpha": np.zeros(info.RP), "w_rowptr": np.zeros(n + 1, np.int32),
+           "w_col": np.zeros(max(info.w_nnz, 1), np.int32), "w_val": np.zeros(max(info.w_nnz, 1))}
+    dp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+    ip = lambda a: a.ctypes.data_as(C.POINTER(C.c_int))
+    check(lib.tpcg_setup_host(C.byref(g), degree, n, C.byref(info), dp(out["w"]), dp(out["bands"]),
+                              dp(out["f_core"]), dp(out["f_U0"]), dp(out["f_U1"]), dp(out["f_U2"]), dp(out["lam"]),
+                              dp(out["mu"]), dp(out["v2u2"]), dp(out["omega"]), dp(out["alpha"]), ip(out["w_rowptr"]),
+                              ip(out["w_col"]), dp(out["w_val"])), "tpcg_setup_host")
+    out["bands"] = out["bands"].reshape(R, 3, 2 * p + 1, n)
+    out["f_core"] = out["f_core"].reshape(rf, order="F")
+    out["f_U"] = [out.pop(f"f_U{t}").reshape((n, rf[t]), order="F") for t in range(3)]
+    out["v2u2"] = out["v2u2"][:n * n2].reshape((n, n2), order="F")
+    out["info"] = info
+    return out
+
+
 def expsum_best(M: float, eps_prec: float = 0.1, rmax: int = 60):
     """tpcg_expsum_best: the best exponential sum for 1/lambda on [1, M] with the fewest terms meeting
     E_R(M) <= eps_prec / M (Prop. 1, eq. estimate_prec_rel).  Host computation.  Returns (omega, alpha, E)."""

@@ -939,3 +939,49 @@ int host_elast_setup(const tpcg_geometry& geo, int p, int n, double lam, double 
 }
 
 }  // namespace tpcg
+
+// Host-only form of tpcg_setup: the same FP64 setup, its tables copied to caller-owned host buffers (no GPU call)
+extern "C" int tpcg_setup_host(const tpcg_geometry* geo, int degree, int n, tpcg_problem_info* info, double* w,
+                               double* bands, double* f_core, double* f_U0, double* f_U1, double* f_U2, double* lam,
+                               double* mu, double* v2u2, double* omega, double* alpha, int* w_rowptr, int* w_col,
+                               double* w_val) {
+    if (!geo || !info) {
+        tpcg::set_error("tpcg_setup_host: null geometry or info");
+        return TPCG_E_INVALID;
+    }
+    tpcg::HostProblem H;
+    const int s = tpcg::host_setup(*geo, degree, n, &H);
+    if (s != TPCG_OK) return s;
+    *info = tpcg_problem_info{};
+    info->n = n;
+    info->p = degree;
+    info->R = H.R;
+    info->RP = H.RP;
+    info->n1 = H.n1;
+    info->n2 = H.n2;
+    for (int t = 0; t < 3; ++t) info->rf[t] = H.rf[t];
+    info->lambda_min = H.lambda_min;
+    info->lambda_max = H.lambda_max;
+    info->MP = H.lambda_max / H.lambda_min;
+    info->w_nnz = (int)H.w_val.size();
+    info->k0 = H.k0;
+    info->k1 = H.k1;
+    auto cp = [](double* dst, const std::vector<double>& v) {
+        if (dst && !v.empty()) std::copy(v.begin(), v.end(), dst);
+    };
+    cp(w, H.w);
+    cp(bands, H.bands);
+    cp(f_core, H.f_core);
+    cp(f_U0, H.f_U[0]);
+    cp(f_U1, H.f_U[1]);
+    cp(f_U2, H.f_U[2]);
+    cp(lam, H.lam);
+    cp(mu, H.mu);
+    cp(v2u2, H.v2u2);
+    cp(omega, H.omega);
+    cp(alpha, H.alpha);
+    cp(w_val, H.w_val);
+    if (w_rowptr) std::copy(H.w_rowptr.begin(), H.w_rowptr.end(), w_rowptr);
+    if (w_col && !H.w_col.empty()) std::copy(H.w_col.begin(), H.w_col.end(), w_col);
+    return TPCG_OK;
+}

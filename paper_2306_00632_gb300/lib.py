@@ -27,7 +27,7 @@ SYMBOLS = [
     "tucker_apply", "tucker_residual", "tucker_axpby", "tucker_dot", "tucker_dot_static", "tucker_round", "fd_precond_apply",
     "tpcg_params_default", "tpcg_solve", "tpcg_ctx_history", "tpcg_solve_batch", "tpcg_ctx_stream", "tpcg_last_error", "tpcg_version",
     "tpcg_profile_enable", "tpcg_profile_reset", "tpcg_profile_get", "tpcg_launch_count", "tpcg_set_option",
-    "tpcg_expsum_best",
+    "tpcg_expsum_best", "tpcg_setup_host",
     "tpcg_elast_setup", "tpcg_elast_create", "tpcg_elast_get_info", "tpcg_elast_apply", "tpcg_elast_residual",
     "tpcg_elast_precond", "tpcg_elast_solve", "tpcg_elast_destroy",
 ]
@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
         "tpcg_launch_count": (C.c_longlong, []),
         "tpcg_set_option": (i, [i, C.c_longlong]),
         "tpcg_expsum_best": (i, [d, d, i, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_int), C.POINTER(d)]),
+        "tpcg_setup_host": (i, [C.POINTER(Geometry), i, i, C.POINTER(ProblemInfo)] + [C.POINTER(d)] * 11
+                            + [C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(d)]),
         "tpcg_version": (C.c_char_p, []),
         "tpcg_elast_setup": (i, [C.POINTER(Geometry), i, i, d, d, C.POINTER(d), i, C.POINTER(vp)]),
         "tpcg_elast_create": (i, [C.POINTER(ProblemArrays), d, d, C.POINTER(vp)]),
